@@ -1,0 +1,517 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+None of these compare the oracle with itself: each check uses an independent
+quantity (closed-form Gaussian moments, brute-force quadrature written here,
+numerical integration in mpmath, exact solutions of limiting equations, or
+exact algebraic invariants of the scheme)."""
+import math
+
+import mpmath
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2606_15720_gb300 import inputs as I
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+# ----------------------------------------------------------------------------
+# independent helpers written for the tests
+# ----------------------------------------------------------------------------
+
+def gh_nodes(n):
+    x, w = np.polynomial.hermite.hermgauss(n)
+    return x, w
+
+
+def full_shakhov_xi_integrals(D, Kxi, Pr, rho, U, T, q, u):
+    """int f+ dxi and int xi^2 f+ dxi by Gauss-Hermite quadrature over xi in R^Kxi,
+    with f+ written straight from Eq. 3-5 (|c|^2 includes xi^2, R = 1/2)."""
+    R = 0.5
+    lam = 1.0 / (2 * R * T)
+    p = rho * R * T
+    c = np.asarray(u, float) - np.asarray(U, float)
+    x, w = gh_nodes(24)
+    # xi_j = x / sqrt(lam) per internal direction; weight exp(-x^2)
+    grids = np.meshgrid(*([x] * Kxi), indexing="ij")
+    wgs = np.meshgrid(*([w] * Kxi), indexing="ij")
+    xi2 = sum((g / math.sqrt(lam)) ** 2 for g in grids)
+    wt = np.prod(wgs, axis=0) / lam ** (Kxi / 2.0)
+    c2 = float(c @ c) + xi2
+    g = rho * (lam / math.pi) ** ((D + Kxi) / 2.0) * np.exp(-lam * float(c @ c))  # times exp(-lam xi^2) in weights
+    fplus = g * (1.0 + (1 - Pr) * float(c @ np.asarray(q, float)) / (5 * p * R * T) * (c2 / (R * T) - 5.0))
+    return float(np.sum(wt * fplus)), float(np.sum(wt * xi2 * fplus))
+
+
+def maxwell_h(D, rho, U, T, u):
+    lam = 1.0 / T
+    c = u - np.asarray(U)[None, :D]
+    return rho * (lam / math.pi) ** (D / 2.0) * np.exp(-lam * np.sum(c * c, axis=1))
+
+
+# ----------------------------------------------------------------------------
+# Maxwellian, reduced distributions and Shakhov corrections (Eq. 3, 10, 13, 16-19)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("D,K", [(1, 0), (2, 0), (3, 0), (2, 2)])
+def test_discrete_maxwellian_moments_match_closed_form(D, K):
+    rng = np.random.default_rng(10 + D)
+    g = I.midpoint_grid({1: 400, 2: 90, 3: 40}[D], -10.0, 10.0, D)
+    Kxi = K + 3 - D
+    for _ in range(3):
+        rho = rng.uniform(0.5, 2.0)
+        U = rng.uniform(-1, 1, 3)
+        T = rng.uniform(0.6, 1.6)
+        out = np.array([O.reduced_equilibrium(D, K, 1.0, rho, U[:D], 1.0 / T, [0, 0, 0], uk) for uk in g.u])
+        H, B = out[:, 0], out[:, 1]
+        w = g.weight
+        mass = w @ H
+        mom = (w * H) @ g.u
+        energy = 0.5 * (w @ (np.sum(g.u ** 2, axis=1) * H + B))
+        # closed form: rho, rho U, rho |U|^2/2 + (K+3) rho T / 4   (R = 1/2)
+        assert mass == pytest.approx(rho, rel=1e-10)
+        np.testing.assert_allclose(mom, rho * U[:D], rtol=1e-10, atol=1e-10)
+        assert energy == pytest.approx(0.5 * rho * U[:D] @ U[:D] + (K + 3) * rho * T / 4.0, rel=1e-10)
+        if K == 0 or True:
+            # B = Kxi/(2 lambda) H: internal energy Kxi rho T/4 carried by b
+            assert 0.5 * (w @ B) == pytest.approx(Kxi * rho * T / 4.0, rel=1e-10, abs=1e-14)
+
+
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_reduced_shakhov_terms_match_xi_quadrature_of_eq3(D):
+    """H+ and B+ (Eq. 18-19) equal the xi-integrals of g+ from Eq. 3 (K = 0)."""
+    Kxi = 3 - D
+    rng = np.random.default_rng(20 + D)
+    for _ in range(5):
+        rho = rng.uniform(0.5, 2.0)
+        U = rng.uniform(-1, 1, D)
+        T = rng.uniform(0.6, 1.6)
+        q = rng.uniform(-0.3, 0.3, D)
+        Pr = 2.0 / 3.0
+        u = rng.uniform(-3, 3, D)
+        H, B, Hp, Bp = O.reduced_equilibrium(D, 0, Pr, rho, U, 1.0 / T, q, u)
+        if Kxi == 0:
+            lam = 1.0 / T
+            c = u - U
+            ref_h = rho * (lam / math.pi) ** (D / 2) * math.exp(-lam * c @ c) * (
+                1 + (1 - Pr) * (c @ q) / (5 * (rho * T / 2) * (T / 2)) * ((c @ c) / (T / 2) - 5))
+            assert H + Hp == pytest.approx(ref_h, rel=1e-12)
+            assert B == 0.0 and Bp == 0.0
+        else:
+            ih, ib = full_shakhov_xi_integrals(D, Kxi, Pr, rho, U, T, q, u)
+            assert H + Hp == pytest.approx(ih, rel=1e-11, abs=1e-15)
+            assert B + Bp == pytest.approx(ib, rel=1e-11, abs=1e-15)
+
+
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_shakhov_correction_has_zero_conserved_moments_and_heat_flux_1_minus_Pr(D):
+    g = I.midpoint_grid({1: 400, 2: 90, 3: 40}[D], -10.0, 10.0, D)
+    rng = np.random.default_rng(30 + D)
+    rho, T, Pr = 1.3, 1.2, 2.0 / 3.0
+    U = rng.uniform(-0.5, 0.5, D)
+    q = rng.uniform(-0.2, 0.2, D)
+    out = np.array([O.reduced_equilibrium(D, 0, Pr, rho, U, 1.0 / T, q, uk) for uk in g.u])
+    Hp, Bp = out[:, 2], out[:, 3]
+    w = g.weight
+    assert abs(w @ Hp) < 1e-10
+    np.testing.assert_allclose((w * Hp) @ g.u, 0.0, atol=1e-10)
+    assert abs(0.5 * (w @ (np.sum(g.u ** 2, 1) * Hp + Bp))) < 1e-10
+    # heat flux of the Shakhov correction (Eq. 13) is (1 - Pr) q
+    c = g.u - U[None, :]
+    qq = 0.5 * ((w * (np.sum(c * c, 1) * Hp + Bp)) @ c)
+    np.testing.assert_allclose(qq, (1 - Pr) * q, rtol=1e-9, atol=1e-12)
+    # and the oracle's Eq. 13 quadrature reproduces it for a Shakhov state
+    H = out[:, 0] + Hp
+    Bt = out[:, 1] + Bp
+    W = np.concatenate([[rho], rho * U, [0.5 * rho * U @ U + 3 * rho * T / 4]])
+    np.testing.assert_allclose(O.heat_flux(D, 0, g, H, Bt if 3 - D > 0 else None, W), (1 - Pr) * q,
+                               rtol=1e-9, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# Time-integration coefficients (Eq. 33-35)
+# ----------------------------------------------------------------------------
+
+def _mp_coeffs(dt, tau):
+    mpmath.mp.dps = 40
+    dt = mpmath.mpf(dt)
+    tau = mpmath.mpf(tau)
+    c = [lambda t: mpmath.e ** (-t / tau),
+         lambda t: -t * mpmath.e ** (-t / tau),
+         lambda t: 1 - mpmath.e ** (-t / tau),
+         lambda t: t * mpmath.e ** (-t / tau) - tau * (1 - mpmath.e ** (-t / tau)),
+         lambda t: t - tau * (1 - mpmath.e ** (-t / tau))]
+    return [float(mpmath.quad(ci, [0, dt])) for ci in c]
+
+
+@pytest.mark.parametrize("x", [1e-8, 1e-5, 1e-3, 0.1, 0.3, 0.4999, 0.5, 0.5001, 1.0, 3.0, 30.0, 1e3, 1e4])
+def test_time_coefficients_match_numerical_integration(x):
+    dt = 2.5e-3
+    tau = dt / x
+    G = O.time_coefficients(dt, tau)
+    ref = _mp_coeffs(dt, tau)
+    for g, r in zip(G, ref):
+        assert g == pytest.approx(r, rel=1e-13, abs=1e-300)
+
+
+def test_time_coefficient_limits():
+    dt = 0.01
+    G = O.time_coefficients(dt, 1e30)      # free transport
+    np.testing.assert_allclose(G, [dt, -dt * dt / 2, 0, 0, 0], atol=1e-25)
+    tau = 1e-9                              # continuum
+    G = O.time_coefficients(dt, tau)
+    np.testing.assert_allclose(G, [tau, -tau * tau, dt - tau, 2 * tau * tau - tau * dt,
+                                   dt * dt / 2 - tau * dt + tau * tau], rtol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# Interface state and slopes (Eq. 32; readings R6, R8)
+# ----------------------------------------------------------------------------
+
+def _cons(D, K, rho, U, T):
+    U = np.asarray(U, float)[:D]
+    return np.concatenate([[rho], rho * U, [0.5 * rho * U @ U + (K + 3) * rho * T / 4]])
+
+
+@pytest.mark.parametrize("D,K", [(1, 0), (2, 0), (3, 0), (2, 2)])
+def test_interface_W0_is_half_range_quadrature(D, K):
+    rng = np.random.default_rng(40 + D)
+    n = rng.normal(size=D)
+    n /= np.linalg.norm(n)
+    Wl = _cons(D, K, 1.2, rng.uniform(-1, 1, D), 1.1)
+    Wr = _cons(D, K, 0.7, rng.uniform(-1, 1, D), 0.8)
+    W0 = O.interface_W0(D, K, Wl, Wr, n)
+    # brute force in the face frame: Gauss-Legendre over u.n in [0, 14] (or [-14, 0])
+    # and over each tangential coordinate in [-14, 14]
+    basis = [n]
+    for e in np.eye(D):
+        v = e - sum((e @ b) * b for b in basis)
+        if np.linalg.norm(v) > 1e-8 and len(basis) < D:
+            basis.append(v / np.linalg.norm(v))
+    xg, wg = np.polynomial.legendre.leggauss({1: 400, 2: 200, 3: 90}[D])
+    Kxi = K + 3 - D
+    acc = np.zeros(D + 2)
+    for W, side in ((Wl, 1.0), (Wr, -1.0)):
+        rho = W[0]
+        U = W[1:1 + D] / rho
+        T = 4 * (W[-1] - 0.5 * rho * U @ U) / ((K + 3) * rho)
+        axes = [(side * 7.0 * (xg + 1.0), 7.0 * wg)] + [(14.0 * xg, 14.0 * wg)] * (D - 1)
+        grids = np.meshgrid(*[a for a, _ in axes], indexing="ij")
+        wts = np.prod(np.meshgrid(*[w for _, w in axes], indexing="ij"), axis=0).reshape(-1)
+        coords = np.stack([g.reshape(-1) for g in grids], axis=1)
+        u = coords @ np.stack(basis)
+        h = maxwell_h(D, rho, U, T, u) * wts
+        acc[0] += h.sum()
+        acc[1:1 + D] += h @ u
+        acc[-1] += 0.5 * (h @ np.sum(u ** 2, 1) + Kxi * T / 2 * h.sum())
+    np.testing.assert_allclose(W0, acc, rtol=1e-10, atol=1e-12)
+    # equal sides reproduce the state exactly
+    np.testing.assert_allclose(O.interface_W0(D, K, Wl, Wl, n), Wl, rtol=1e-14)
+
+
+def _ln_g(D, K, W, u, xi2):
+    rho = W[0]
+    U = W[1:1 + D] / rho
+    lam = (K + 3) * rho / (4 * (W[-1] - 0.5 * rho * U @ U))
+    Kxi = K + 3 - D
+    return math.log(rho) + (D + Kxi) / 2 * math.log(lam / math.pi) - lam * (np.sum((u - U) ** 2) + xi2)
+
+
+@pytest.mark.parametrize("D,K", [(1, 0), (2, 0), (3, 0), (2, 2)])
+def test_micro_slope_is_log_derivative_of_maxwellian(D, K):
+    """grad g = g (a . psi): a . psi must equal d/dx ln g(W0 + x dW) at x = 0."""
+    rng = np.random.default_rng(50 + D)
+    W0 = _cons(D, K, 1.1, rng.uniform(-0.5, 0.5, D), 1.3)
+    dW = rng.normal(size=D + 2) * 0.1
+    a = O.micro_slope(D, K, W0, dW)
+    eps = 1e-6
+    for _ in range(6):
+        u = rng.uniform(-3, 3, D)
+        xi2 = rng.uniform(0, 2) if K + 3 - D > 0 else 0.0
+        psi = np.concatenate([[1.0], u, [0.5 * (u @ u + xi2)]])
+        ref = (_ln_g(D, K, W0 + eps * dW, u, xi2) - _ln_g(D, K, W0 - eps * dW, u, xi2)) / (2 * eps)
+        assert a @ psi == pytest.approx(ref, rel=1e-7, abs=1e-8)
+
+
+def test_time_slope_reproduces_euler_flux_divergence_1d():
+    """Compatibility (Eq. 7) at first order: rho <psi psi> A = -d/dx F_Euler(W)."""
+    D, K = 1, 0
+    rng = np.random.default_rng(60)
+    W0 = _cons(D, K, 1.1, [0.3], 1.2)
+    dW = rng.normal(size=3) * 0.2
+    a = O.micro_slope(D, K, W0, dW)
+    A = O.time_slope(D, K, W0, a)
+
+    def euler_flux(W):
+        rho, m, E = W
+        U = m / rho
+        p = (E - 0.5 * rho * U * U) * 2.0 / (K + 3)    # p = rho T / 2, rho e = (K+3) p / 2
+        return np.array([m, m * U + p, U * (E + p)])
+
+    eps = 1e-6
+    dF = (euler_flux(W0 + eps * dW) - euler_flux(W0 - eps * dW)) / (2 * eps)
+    # rho <psi psi^T> A by Gauss-Hermite quadrature (u and the 2 internal xi)
+    rho = W0[0]
+    U = W0[1] / rho
+    T = 4 * (W0[2] - 0.5 * rho * U * U) / (3 * rho)
+    lam = 1 / T
+    x, w = gh_nodes(30)
+    u = U + x / math.sqrt(lam)
+    wu = w / math.sqrt(math.pi)
+    xi2_mean = 2 / (2 * lam)   # K_xi = 2
+    xi4_mean = 2 * 4 / (4 * lam * lam)
+    M = np.zeros((3, 3))
+    for ui, wi in zip(u, wu):
+        # expectation over xi done analytically per moment order
+        psi0 = np.array([1.0, ui, 0.5 * ui * ui])
+        M += wi * rho * np.array([
+            [1, ui, 0.5 * (ui * ui + xi2_mean)],
+            [ui, ui * ui, 0.5 * ui * (ui * ui + xi2_mean)],
+            [0.5 * (ui * ui + xi2_mean), 0.5 * ui * (ui * ui + xi2_mean),
+             0.25 * (ui ** 4 + 2 * ui * ui * xi2_mean + xi4_mean)]])
+        del psi0
+    np.testing.assert_allclose(M @ A, -dF, rtol=1e-6, atol=1e-8)
+
+
+# ----------------------------------------------------------------------------
+# Whole-step invariants and limits
+# ----------------------------------------------------------------------------
+
+def _setup(mesh, grid, gas, prim):
+    W = I.prim_to_conservative(prim, mesh.dim, gas.K)
+    f = O.initial_f(mesh, grid, W, gas.K)
+    return W, f
+
+
+@pytest.mark.parametrize("model", ["bgk", "shakhov"])
+def test_uniform_maxwellian_is_preserved(model):
+    mesh = I.periodic_box((10, 7))
+    grid = I.midpoint_grid(20, -5, 5, 2)
+    gas = I.Gas(model=model, Pr=1.0 if model == "bgk" else 2 / 3, mu_ref=0.01)
+    W, f = _setup(mesh, grid, gas, I.uniform_primitives(mesh, 1.3, (0.4, -0.25, 0), 0.9))
+    W1, f1, _, _ = O.run(mesh, grid, gas, W, f, 8)
+    np.testing.assert_allclose(W1, W, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(f1, f, rtol=0, atol=1e-7 if model == "shakhov" else 1e-14)
+
+
+@pytest.mark.parametrize("model,shape", [("bgk", (12, 9)), ("shakhov", (12, 9)), ("shakhov", (5, 4, 3))])
+def test_periodic_conservation(model, shape):
+    mesh = I.periodic_box(shape)
+    D = len(shape)
+    grid = I.midpoint_grid({2: 16, 3: 10}[D], -5, 5, D)
+    gas = I.Gas(model=model, Pr=1.0 if model == "bgk" else 2 / 3, mu_ref=0.02)
+    prim = I.smooth_random_primitives(mesh, seed=7, amp=0.2)
+    W, f = _setup(mesh, grid, gas, prim)
+    tot0 = mesh.cell_volume @ W
+    W1, f1, _, _ = O.run(mesh, grid, gas, W, f, 10)
+    tot1 = mesh.cell_volume @ W1
+    np.testing.assert_allclose(tot1, tot0, rtol=1e-13, atol=1e-14)
+    assert np.abs(W1 - W).max() > 1e-6   # the state did change
+
+
+def test_homogeneous_bgk_relaxation_is_exact():
+    """Uniform W, f = H + delta with zero conserved moments: the two-stage update
+    (Eq. 41-42) multiplies delta by (1 - beta)/(1 + beta), beta = dt/(2 tau)."""
+    mesh = I.periodic_box((4, 3))
+    grid = I.midpoint_grid(16, -5, 5, 2)
+    gas = I.Gas(model="bgk", mu_ref=0.003, dt=0.01)
+    prim = I.uniform_primitives(mesh, 1.0, (0.2, 0, 0), 1.0)
+    W, f = _setup(mesh, grid, gas, prim)
+    rng = np.random.default_rng(3)
+    d = rng.normal(size=grid.n_v) * 1e-3 * f[0, 0]
+    psi = np.stack([np.ones(grid.n_v), grid.u[:, 0], grid.u[:, 1], 0.5 * np.sum(grid.u ** 2, 1)])
+    wpsi = psi * grid.weight
+    d -= psi.T @ np.linalg.solve(wpsi @ psi.T, wpsi @ d)        # remove conserved moments (h part)
+    f2 = f.copy()
+    f2[0] += d[None, :]
+    n = 6
+    W1, f1, dt, _ = O.run(mesh, grid, gas, W, f2, n)
+    T = 1.0
+    tau = gas.mu_ref * T ** gas.omega / (W[0, 0] * T / 2)
+    beta = dt / (2 * tau)
+    r = (1 - beta) / (1 + beta)
+    np.testing.assert_allclose(f1[0] - f[0], np.broadcast_to((r ** n) * d, f[0].shape), rtol=1e-9, atol=4e-16)
+    np.testing.assert_allclose(W1, W, atol=1e-14)
+
+
+def _free_transport_error(n):
+    L = 1.0
+    mesh = I.cartesian_mesh((n,), (0,), (L,), {"x-": "periodic", "x+": "periodic"}, [])
+    grid = I.midpoint_grid(8, -2, 2, 1)
+    gas = I.Gas(model="bgk", mu_ref=1e14, limiter="none", cfl=0.5)
+    x = mesh.cell_centroid[:, 0]
+    eps = 0.1
+    prim = I.uniform_primitives(mesh)
+    prim[:, 0] = 1 + eps * np.sin(2 * np.pi * x)
+    W, f = _setup(mesh, grid, gas, prim)
+    dt_cfl = O.time_step(mesh, grid, 0.5)
+    t_end = 0.25
+    nsteps = int(math.ceil(t_end / dt_cfl))
+    dt = t_end / nsteps
+    W1, f1, _, _ = O.run(mesh, grid, gas, W, f, nsteps, dt=dt)
+    # exact free transport of each discrete velocity: f_k(x, t) = f0_k(x - u_k t)
+    err = 0.0
+    for k, uk in enumerate(grid.u[:, 0]):
+        xs = x - uk * t_end
+        rho = 1 + eps * np.sin(2 * np.pi * xs)
+        exact = rho * (1 / math.pi) ** 0.5 * math.exp(-uk * uk)   # T = 1, U = 0
+        err = max(err, np.max(np.abs(f1[0, :, k] - exact)))
+    return err
+
+
+def test_free_molecular_limit_converges_second_order():
+    e = [_free_transport_error(n) for n in (32, 64, 128)]
+    orders = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert orders[0] > 1.8 and orders[1] > 1.9, (e, orders)
+
+
+def _exact_sod(x, t, gamma=5 / 3, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1), x0=0.5):
+    """Exact Euler Riemann solution (Newton iteration on the star pressure)."""
+    rl, ul, pl = left
+    rr, ur, pr = right
+    cl, cr = math.sqrt(gamma * pl / rl), math.sqrt(gamma * pr / rr)
+
+    def fk(p, r, pk, ck):
+        if p > pk:
+            A = 2 / ((gamma + 1) * r)
+            B = (gamma - 1) / (gamma + 1) * pk
+            return (p - pk) * math.sqrt(A / (p + B)), math.sqrt(A / (B + p)) * (1 - (p - pk) / (2 * (B + p)))
+        return (2 * ck / (gamma - 1) * ((p / pk) ** ((gamma - 1) / (2 * gamma)) - 1),
+                1 / (r * ck) * (p / pk) ** (-(gamma + 1) / (2 * gamma)))
+
+    p = 0.5 * (pl + pr)
+    for _ in range(100):
+        f1, d1 = fk(p, rl, pl, cl)
+        f2, d2 = fk(p, rr, pr, cr)
+        pn = p - (f1 + f2 + ur - ul) / (d1 + d2)
+        if abs(pn - p) < 1e-14 * p:
+            p = pn
+            break
+        p = max(pn, 1e-12)
+    us = 0.5 * (ul + ur) + 0.5 * (fk(p, rr, pr, cr)[0] - fk(p, rl, pl, cl)[0])
+    rho = np.zeros_like(x)
+    for i, xi in enumerate(x):
+        s = (xi - x0) / t
+        if s < us:
+            if p > pl:
+                raise NotImplementedError
+            shl = ul - cl
+            cml = cl * (p / pl) ** ((gamma - 1) / (2 * gamma))
+            stl = us - cml
+            if s < shl:
+                rho[i] = rl
+            elif s > stl:
+                rho[i] = rl * (p / pl) ** (1 / gamma)
+            else:
+                rho[i] = rl * (2 / (gamma + 1) + (gamma - 1) / ((gamma + 1) * cl) * (ul - s)) ** (2 / (gamma - 1))
+        else:
+            if p > pr:
+                sr = ur + cr * math.sqrt((gamma + 1) / (2 * gamma) * p / pr + (gamma - 1) / (2 * gamma))
+                rho[i] = rr if s > sr else rr * ((p / pr + (gamma - 1) / (gamma + 1)) /
+                                                 ((gamma - 1) / (gamma + 1) * p / pr + 1))
+            else:
+                raise NotImplementedError
+    return rho
+
+
+def _sod_l1(n):
+    mesh = I.cartesian_mesh((n,), (0,), (1,), {"x-": 0, "x+": 0}, [I.BC(I.BC_OUTFLOW)])
+    grid = I.midpoint_grid(64, -8, 8, 1)
+    gas = I.Gas(model="bgk", mu_ref=1e-6, omega=0.5, cfl=0.8, shock_tau_fix=True)
+    x = mesh.cell_centroid[:, 0]
+    prim = I.uniform_primitives(mesh)
+    left = x < 0.5
+    # p = rho T / 2: (rho, p) = (1, 1) and (0.125, 0.1)
+    prim[:, 0] = np.where(left, 1.0, 0.125)
+    prim[:, -1] = np.where(left, 2.0, 1.6)
+    W, f = _setup(mesh, grid, gas, prim)
+    t_end = 0.15
+    dt0 = O.time_step(mesh, grid, 0.8)
+    nsteps = int(math.ceil(t_end / dt0))
+    W1, _, _, _ = O.run(mesh, grid, gas, W, f, nsteps, dt=t_end / nsteps)
+    exact = _exact_sod(x, t_end)
+    return float(np.mean(np.abs(W1[:, 0] - exact)))
+
+
+@pytest.mark.slow
+def test_small_tau_shock_tube_matches_exact_riemann_solution():
+    e100, e400 = _sod_l1(100), _sod_l1(400)
+    assert e400 < 2e-2, e400
+    assert e400 < 0.6 * e100, (e100, e400)
+
+
+def _shear_wave_decay(model, Pr):
+    n = 64
+    mesh = I.cartesian_mesh((n, 2), (0, 0), (1, 2.0 / n),
+                            {"x-": "periodic", "x+": "periodic", "y-": "periodic", "y+": "periodic"}, [])
+    grid = I.midpoint_grid(28, -6, 6, 2)
+    mu = 0.004   # mean free path ~ tau sqrt(T) = 0.008 << wavelength 1 (Navier-Stokes regime)
+    gas = I.Gas(model=model, Pr=Pr, mu_ref=mu, omega=0.5, cfl=0.8)
+    x = mesh.cell_centroid[:, 0]
+    eps = 1e-3
+    prim = I.uniform_primitives(mesh)
+    prim[:, 2] = eps * np.sin(2 * np.pi * x)          # shear wave U_y(x)
+    prim[:, 0] = 1 + eps * np.cos(2 * np.pi * x)       # entropy wave: rho and T at constant p
+    prim[:, -1] = 1 / prim[:, 0]
+    W, f = _setup(mesh, grid, gas, prim)
+    t_end = 1.0
+    dt0 = O.time_step(mesh, grid, 0.8)
+    nsteps = int(math.ceil(t_end / dt0))
+    W1, _, _, _ = O.run(mesh, grid, gas, W, f, nsteps, dt=t_end / nsteps)
+    k = 2 * np.pi
+    amp_u = 2 * np.mean(W1[:, 2] / W1[:, 0] * np.sin(k * x))
+    # entropy variable dp/p - gamma drho/rho: acoustic modes are isentropic, so this
+    # isolates the thermal mode from the sound waves that heat conduction launches
+    rho = W1[:, 0]
+    p = (W1[:, -1] - 0.5 * (W1[:, 1] ** 2 + W1[:, 2] ** 2) / rho) * 2.0 / 3.0
+    s = (p / 0.5 - 1.0) - 5.0 / 3.0 * (rho - 1.0)
+    amp_s = 2 * np.mean(s * np.cos(k * x)) / (-5.0 / 3.0)
+    # linearised Navier-Stokes: shear decays at nu k^2, the thermal mode at mu k^2 / (Pr rho)
+    return amp_u / eps, math.exp(-mu * k * k * t_end), amp_s / eps, math.exp(-mu * k * k / Pr * t_end)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("model,Pr", [("bgk", 1.0), ("shakhov", 2 / 3)])
+def test_navier_stokes_limit_decay_rates(model, Pr):
+    """Viscous shear-wave and entropy-wave decay recover mu and mu/Pr."""
+    got_u, ref_u, got_T, ref_T = _shear_wave_decay(model, Pr)
+    assert got_u == pytest.approx(ref_u, rel=0.005)
+    assert got_T == pytest.approx(ref_T, rel=0.005)
+
+
+def test_velocity_block_and_partition_order_is_invariant():
+    """Eq. 63-64: blocked and rank-partitioned velocity sums give the same W."""
+    mesh = I.cavity_mesh(8)
+    grid = I.midpoint_grid(12, -4.5, 4.5, 2)
+    gas = I.Gas(model="shakhov", Pr=2 / 3, mu_ref=I.mu_ref_from_kn(0.075, 0.81))
+    W, f = _setup(mesh, grid, gas, I.uniform_primitives(mesh))
+    ref, fref, _, _ = O.run(mesh, grid, gas, W, f, 5)
+    for bv, pv in ((1, 1), (7, 1), (32, 3), (grid.n_v, 8), (5, 4)):
+        Wb, fb, _, _ = O.run(mesh, grid, gas, W, f, 5, block_v=bv, p_v=pv)
+        np.testing.assert_allclose(Wb, ref, rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(fb, fref, rtol=1e-12, atol=1e-16)
+
+
+def test_wall_non_penetration_and_resting_gas():
+    mesh = I.cavity_mesh(10, lid_speed=0.0)
+    grid = I.midpoint_grid(16, -4.5, 4.5, 2)
+    gas = I.Gas(model="bgk", mu_ref=0.05)
+    W, f = _setup(mesh, grid, gas, I.uniform_primitives(mesh))
+    W1, f1, _, diag = O.run(mesh, grid, gas, W, f, 6)
+    assert diag[:, -1].max() < 1e-16        # Eq. 38 holds to round-off
+    np.testing.assert_allclose(W1, W, atol=1e-14)
+    np.testing.assert_allclose(f1, f, atol=1e-14)
+    # moving lid: still zero wall mass flux, total mass conserved
+    mesh = I.cavity_mesh(10)
+    W1, f1, _, diag = O.run(mesh, grid, gas, W, f, 6)
+    assert diag[:, -1].max() < 1e-16
+    assert mesh.cell_volume @ W1[:, 0] == pytest.approx(mesh.cell_volume @ W[:, 0], rel=1e-14)
+    assert W1[:, 1].max() > 1e-4            # the lid drives the gas
+
+
+def test_time_step_reading_on_uniform_quads():
+    mesh = I.cavity_mesh(32)
+    grid = I.midpoint_grid(24, -4.5, 4.5, 2)
+    # sum_f S max(u.n, 0) = dx (|u_x| + |u_y|) on a square cell: dt = CFL dx / max(|u_x| + |u_y|)
+    assert O.time_step(mesh, grid, 0.8) == pytest.approx(0.8 * (1 / 32) / (2 * 4.3125), rel=1e-14)
