@@ -740,7 +740,13 @@ int orc_step(const orc_mesh *m, int64_t nv, const double *u, const double *w, co
     prim_from_W(D, K, W0, &fc->p0);
     for (int d = 0; d < D; ++d) fc->q0[d] = 0.5 * (q[i * MAXD + d] + qr[d]);
     for (int d = 0; d < D; ++d) orc_micro_slope(D, K, W0, dW0[d], fc->a[d]);
-    orc_time_slope(D, K, W0, &fc->a[0][0], fc->A);
+    {
+      /* orc_time_slope takes the D slope vectors packed with stride D + 2 */
+      double apack[MAXD * NW];
+      for (int d = 0; d < D; ++d)
+        for (int t = 0; t < nw; ++t) apack[d * nw + t] = fc->a[d][t];
+      orc_time_slope(D, K, W0, apack, fc->A);
+    }
     double tau0 = tau_of(p, &fc->p0);
     if (p->shock_tau_fix) {
       prim_t pl, pr;
