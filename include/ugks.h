@@ -1,0 +1,181 @@
+/*
+ * ugks.h -- C ABI of the GB300 UGKS velocity-block sweep.
+ *
+ * The library advances the reduced distributions h, b and the conservative
+ * variables W of the unified gas-kinetic scheme (UGKS) on an unstructured
+ * face-list mesh with a discrete velocity grid, one GPU, one CUDA stream.
+ * Method: arXiv 2606.15720, Sec. 2.1 (discretisation) and Algorithm 5 (one
+ * time step); the velocity-block sweep of Sec. 2.2.2 and Algorithms 1 and 4
+ * is the device execution unit.
+ *
+ * Conventions for every entry point:
+ *   * Pointers passed in are HOST pointers unless stated otherwise; the
+ *     library copies what it needs at create time and never keeps a caller
+ *     pointer.  Output buffers are caller-allocated host memory.
+ *   * Every call returns a ugks_status.  On failure the message of the last
+ *     error is available from ugks_last_error(ctx) (or ugks_last_error(NULL)
+ *     for failures before a context exists).  After UGKS_ERR_CUDA a context
+ *     is unusable except for ugks_destroy.
+ *   * ugks_step is asynchronous on the context's stream; calls that return
+ *     data (moments, residual, get_f, state) synchronise that stream.
+ *     Non-finite or non-physical states detected on the device latch into a
+ *     status word that the next ugks_moments or ugks_residual reports as
+ *     UGKS_ERR_NONFINITE; ugks_get_f and ugks_get_state return the raw state
+ *     regardless, so that it can be inspected.
+ *   * A context is not thread-safe; distinct contexts are independent.
+ *   * Units: R = 1/2 (so lambda = 1/T, p = rho T / 2), velocities in
+ *     sqrt(2 R T_ref), lengths in the mesh's unit.
+ */
+#ifndef UGKS_H
+#define UGKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ugks_ctx ugks_ctx; /* opaque; owned by the library */
+
+typedef enum {
+  UGKS_OK = 0,
+  UGKS_ERR_INVALID_ARGUMENT = 1, /* NULL pointer, bad size or parameter */
+  UGKS_ERR_MESH = 2,             /* inconsistent mesh (indices, areas, volumes, normals) */
+  UGKS_ERR_VGRID = 3,            /* empty grid, negative or non-finite weights */
+  UGKS_ERR_OUT_OF_MEMORY = 4,    /* device or host allocation failed */
+  UGKS_ERR_CUDA = 5,             /* a CUDA runtime call failed */
+  UGKS_ERR_NONFINITE = 6,        /* NaN/Inf or non-positive density / temperature */
+  UGKS_ERR_TIMEOUT = 7,          /* reserved for bounded device waits */
+  UGKS_ERR_UNSUPPORTED = 8       /* valid request this build does not implement */
+} ugks_status;
+
+enum { UGKS_BC_WALL = 1, UGKS_BC_FARFIELD = 2, UGKS_BC_OUTFLOW = 3 };
+enum { UGKS_MODEL_BGK = 0, UGKS_MODEL_SHAKHOV = 1 };
+enum { UGKS_LIMITER_NONE = 0, UGKS_LIMITER_VENKATAKRISHNAN = 1, UGKS_LIMITER_BARTH_JESPERSEN = 2 };
+enum { UGKS_STORAGE_F64 = 0, UGKS_STORAGE_F32 = 1, UGKS_STORAGE_F16 = 2, UGKS_STORAGE_BF16 = 3 };
+
+/* Boundary condition of the faces whose neighbour is -(index+1).
+ * WALL: diffuse isothermal wall (Sec. 2.1, Eq. 36-38) with wall velocity u
+ *       (tangential) and temperature T; rho is ignored (the wall density
+ *       follows from the non-penetration condition, Eq. 38).
+ * FARFIELD: ghost cell holds the Maxwellian of (rho, u, T).
+ * OUTFLOW: ghost cell holds the Maxwellian of the interior cell's W. */
+typedef struct {
+  int32_t type;
+  double rho;
+  double u[3];
+  double T;
+} ugks_bc;
+
+/* Face-list mesh (Sec. 2.1, Eq. 20, 24).  Cells are 0..n_cells-1.
+ *   cell_volume[n_cells] > 0, cell_centroid[n_cells][dim]
+ *   face_owner[n_faces] in [0, n_cells)
+ *   face_neighbor[n_faces]: >= 0 interior cell (different from the owner), or
+ *       -(b+1) for boundary condition bc[b]
+ *   face_area[n_faces] > 0; face_normal[n_faces][dim] unit, owner -> neighbour
+ *   face_centroid[n_faces][dim] in the owner's frame
+ *   face_shift[n_faces][dim] or NULL: translation added to the neighbour
+ *       centroid across this face (periodic faces); NULL means zero.
+ * At most 32 faces per cell. */
+typedef struct {
+  int32_t dim; /* 1, 2 or 3 */
+  int64_t n_cells, n_faces;
+  const double *cell_volume;
+  const double *cell_centroid;
+  const int64_t *face_owner;
+  const int64_t *face_neighbor;
+  const double *face_area;
+  const double *face_normal;
+  const double *face_centroid;
+  const double *face_shift;
+  int32_t n_bc;
+  const ugks_bc *bc;
+} ugks_mesh;
+
+/* Discrete velocity grid (Sec. 2.1, Eq. 21-22): u[n_v][dim], weight[n_v] >= 0
+ * (the velocity-cell volumes omega_k).  The library pads it to a multiple of
+ * the velocity block (Sec. 2.2.2, Eq. 47) with zero-weight points. */
+typedef struct {
+  int64_t n_v;
+  const double *u;
+  const double *weight;
+} ugks_vgrid;
+
+/* Gas and scheme parameters.
+ *   model: BGK (Pr must be 1) or Shakhov (Sec. 2.1, Eq. 3; K must be 0)
+ *   K: internal degrees of freedom (K_xi = K + 3 - dim, Eq. 2)
+ *   mu = mu_ref T^omega, tau = mu / p
+ *   dt: dt_override if > 0, else cfl * min_i |Omega_i| / max_k sum_f S_f max(u_k . n_f, 0)
+ *   limiter: slope limiter of the least-squares reconstruction, venkat_K its constant
+ *   shock_tau_fix: add dt |p_l - p_r| / (p_l + p_r) to the interface relaxation time
+ *   storage: precision of the stored distribution (F64, F32 supported)
+ *   tile_cells: cells per device tile, 0 = automatic */
+typedef struct {
+  int32_t model;
+  int32_t K;
+  double Pr, omega, mu_ref;
+  double cfl, dt_override;
+  int32_t limiter;
+  double venkat_K;
+  int32_t shock_tau_fix;
+  int32_t storage;
+  int32_t tile_cells;
+} ugks_params;
+
+/* Creates a solver context.  Copies mesh, grid and W_init (host,
+ * [n_cells][dim+2] conservative (rho, rho U, rho E); NULL = the state of
+ * bc[0]) to the device, renumbers cells for locality, precomputes geometry
+ * and the time step, and sets h, b to the discrete Maxwellians of W_init.
+ * cuda_stream: a cudaStream_t to run on, or NULL for a library-owned stream.
+ * Errors: INVALID_ARGUMENT, MESH, VGRID, UNSUPPORTED, OUT_OF_MEMORY, CUDA. */
+ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ugks_params *params,
+                        const double *W_init, void *cuda_stream, ugks_ctx **out);
+
+/* Advances n_steps >= 0 UGKS time steps (Algorithm 5), asynchronously. */
+ugks_status ugks_step(ugks_ctx *ctx, int32_t n_steps);
+
+/* Copies W (host, [n_cells][dim+2], original cell order) and, if q_out is not
+ * NULL, the heat flux of the current distribution ([n_cells][dim], Eq. 13). */
+ugks_status ugks_moments(ugks_ctx *ctx, double *W_out, double *q_out);
+
+/* Copies the residual of the last step, res_out[dim+2]:
+ * R_m = sqrt(sum_i (W_im^{n+1} - W_im^n)^2 / n_cells).  Zero before any step. */
+ugks_status ugks_residual(ugks_ctx *ctx, double *res_out);
+
+/* Time step in use. */
+ugks_status ugks_dt(const ugks_ctx *ctx, double *dt_out);
+
+/* Number of reduced distributions (2 when K_xi > 0, else 1) and padded grid size. */
+ugks_status ugks_sizes(const ugks_ctx *ctx, int32_t *n_reduced, int64_t *n_v_padded);
+
+/* Copies the distribution of selected cells (original indices) as FP64:
+ * out[n][n_reduced][n_v] (h then b). */
+ugks_status ugks_get_f(ugks_ctx *ctx, const int64_t *cells, int64_t n, double *out);
+
+/* Checkpoint / restart: full state as FP64, W[n_cells][dim+2] and
+ * f[n_reduced][n_cells][n_v], original cell order; the step counter. */
+ugks_status ugks_get_state(ugks_ctx *ctx, double *W, double *f, int64_t *step);
+ugks_status ugks_set_state(ugks_ctx *ctx, const double *W, const double *f, int64_t step);
+
+/* Per-kernel device time accumulated since the last reset (CUDA events on the
+ * context stream, recorded only while enabled).  names/ms/count arrays of
+ * length cap; returns the number of kernels in *n. */
+ugks_status ugks_stats_enable(ugks_ctx *ctx, int32_t on);
+ugks_status ugks_stats(ugks_ctx *ctx, int32_t cap, const char **names, double *ms, int64_t *count, int32_t *n);
+
+/* One-shot solve with host buffers: create, n_steps steps, copy W_out
+ * ([n_cells][dim+2]) and res_out ([dim+2]), destroy. */
+ugks_status ugks_solve(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ugks_params *params,
+                       const double *W_init, int32_t n_steps, double *W_out, double *res_out);
+
+ugks_status ugks_destroy(ugks_ctx *ctx);
+
+/* Message of the last error of ctx, or of the calling thread when ctx is NULL. */
+const char *ugks_last_error(const ugks_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UGKS_H */

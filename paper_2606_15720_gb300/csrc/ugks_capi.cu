@@ -1,0 +1,974 @@
+// C ABI of the GB300 UGKS library (declared in include/ugks.h): validation,
+// locality renumbering of cells, least-squares geometry, tiling of the
+// velocity-block sweep, device memory, and the per-step launch sequence of
+// Algorithm 5 (cell stage -> face stage -> persistent sweep).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "ugks.h"
+#include "ugks_internal.cuh"
+#include "ugks_kernels.cuh"
+
+using namespace ugks;
+
+namespace {
+
+thread_local std::string g_thread_err;
+
+struct KernelTiming {
+  int id;
+  cudaEvent_t start, stop;
+};
+
+const char* const kKernelNames[] = {"cell_stage", "face_stage", "velocity_block_sweep", "residual"};
+constexpr int kNumKernels = 4;
+
+}  // namespace
+
+struct ugks_ctx {
+  int D = 0, K = 0, NR = 1, storage = UGKS_STORAGE_F32;
+  int64_t Nc = 0, Nf = 0, nv = 0, M = 0;
+  double dt = 0.0;
+  Gas gas{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<int64_t> new_of_old, old_of_new;
+  std::vector<void*> allocs;
+  // cells
+  double *d_vol = nullptr, *d_xc = nullptr, *d_W[2] = {nullptr, nullptr}, *d_q[2] = {nullptr, nullptr};
+  double *d_gW = nullptr, *d_res_acc = nullptr, *d_res = nullptr;
+  int* d_status = nullptr;
+  CellPrim *d_cp[2] = {nullptr, nullptr};
+  int64_t* d_cf_off = nullptr;
+  CellFace* d_cf = nullptr;
+  void* d_cfT = nullptr;
+  void* d_eps2 = nullptr;
+  // faces
+  int64_t *d_fown = nullptr, *d_fnei = nullptr;
+  double *d_fnormal = nullptr, *d_fcent = nullptr, *d_fshift = nullptr;
+  void* d_fg = nullptr;
+  void* d_fr = nullptr;
+  BCDev* d_bcs = nullptr;
+  // velocities
+  double *d_u = nullptr, *d_wgt = nullptr, *d_ux = nullptr, *d_uy = nullptr, *d_uz = nullptr, *d_wp = nullptr;
+  void *d_uxT = nullptr, *d_uyT = nullptr, *d_uzT = nullptr, *d_wT = nullptr;
+  // distributions
+  void* d_f[2] = {nullptr, nullptr};
+  // tiles and scratch
+  int ntiles = 0, threads = 512;
+  int64_t *d_tile_begin = nullptr, *d_gset_off = nullptr, *d_gset = nullptr, *d_tf_off = nullptr;
+  TileFace* d_tf = nullptr;
+  int32_t* d_tcf = nullptr;
+  void *d_G = nullptr, *d_Phi = nullptr;
+  double* d_Facc = nullptr;
+  int64_t G_stride = 0, Phi_stride = 0, Facc_stride = 0;
+  int cur = 0;
+  int64_t step = 0;
+  bool stats_on = false;
+  std::vector<KernelTiming> timings;
+  double stat_ms[kNumKernels] = {0, 0, 0, 0};
+  int64_t stat_count[kNumKernels] = {0, 0, 0, 0};
+  std::string err;
+};
+
+namespace {
+
+ugks_status fail(ugks_ctx* ctx, ugks_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  g_thread_err = buf;
+  return st;
+}
+
+#define CUDA_TRY(ctx, call)                                                                       \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) {                                                                      \
+      if (e_ == cudaErrorMemoryAllocation)                                                        \
+        return fail(ctx, UGKS_ERR_OUT_OF_MEMORY, "%s: %s", #call, cudaGetErrorString(e_));        \
+      return fail(ctx, UGKS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));            \
+    }                                                                                             \
+  } while (0)
+
+template <typename P>
+cudaError_t dalloc(ugks_ctx* ctx, P** ptr, size_t bytes) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  ctx->allocs.push_back(p);
+  *ptr = static_cast<P*>(p);
+  return cudaSuccess;
+}
+
+template <typename P>
+cudaError_t upload(ugks_ctx* ctx, P** ptr, const void* host, size_t bytes) {
+  cudaError_t e = dalloc(ctx, ptr, bytes);
+  if (e != cudaSuccess) return e;
+  if (bytes) e = cudaMemcpyAsync(*ptr, host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(ctx->stream);
+}
+
+void release(ugks_ctx* ctx) {
+  for (auto& t : ctx->timings) {
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
+  }
+  ctx->timings.clear();
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  ctx->stream = nullptr;
+}
+
+// Spread the low 21 bits of x so that two zero bits follow each bit.
+uint64_t spread3(uint64_t x) {
+  x &= 0x1fffff;
+  x = (x | x << 32) & 0x1f00000000ffffULL;
+  x = (x | x << 16) & 0x1f0000ff0000ffULL;
+  x = (x | x << 8) & 0x100f00f00f00f00fULL;
+  x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+  x = (x | x << 2) & 0x1249249249249249ULL;
+  return x;
+}
+
+// Least-squares weights M^-1 d (M = sum d d^T); M is singular (zero gradient)
+// when det M <= 1e-12 (tr M / D)^D.
+bool lsq_inverse(int D, const double* M, double* Minv) {
+  double tr = 0.0;
+  for (int d = 0; d < D; ++d) tr += M[d * D + d];
+  tr /= D;
+  if (!(tr > 0.0)) return false;
+  if (D == 1) {
+    if (!(M[0] > 1e-12 * tr)) return false;
+    Minv[0] = 1.0 / M[0];
+    return true;
+  }
+  if (D == 2) {
+    double det = M[0] * M[3] - M[1] * M[2];
+    if (!(det > 1e-12 * tr * tr)) return false;
+    Minv[0] = M[3] / det;
+    Minv[1] = -M[1] / det;
+    Minv[2] = -M[2] / det;
+    Minv[3] = M[0] / det;
+    return true;
+  }
+  double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8], c02 = M[3] * M[7] - M[4] * M[6];
+  double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
+  if (!(det > 1e-12 * tr * tr * tr)) return false;
+  double inv[9] = {c00, M[2] * M[7] - M[1] * M[8], M[1] * M[5] - M[2] * M[4],
+                   c01, M[0] * M[8] - M[2] * M[6], M[2] * M[3] - M[0] * M[5],
+                   c02, M[1] * M[6] - M[0] * M[7], M[0] * M[4] - M[1] * M[3]};
+  for (int t = 0; t < 9; ++t) Minv[t] = inv[t] / det;
+  return true;
+}
+
+ugks_status validate(const ugks_mesh* m, const ugks_vgrid* v, const ugks_params* p) {
+  if (!m || !v || !p) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "mesh, vgrid and params must not be NULL");
+  if (m->dim < 1 || m->dim > 3) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "dim must be 1, 2 or 3");
+  if (m->n_cells <= 0 || m->n_faces <= 0) return fail(nullptr, UGKS_ERR_MESH, "mesh needs cells and faces");
+  if (!m->cell_volume || !m->cell_centroid || !m->face_owner || !m->face_neighbor || !m->face_area ||
+      !m->face_normal || !m->face_centroid)
+    return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "mesh arrays must not be NULL");
+  if (m->n_bc < 0 || (m->n_bc > 0 && !m->bc)) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "bad bc list");
+  const int D = m->dim;
+  for (int b = 0; b < m->n_bc; ++b) {
+    const ugks_bc& bc = m->bc[b];
+    if (bc.type < UGKS_BC_WALL || bc.type > UGKS_BC_OUTFLOW)
+      return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "bc %d has unknown type %d", b, bc.type);
+    if (!(bc.T > 0.0) || !std::isfinite(bc.T)) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "bc %d: T <= 0", b);
+    if (bc.type == UGKS_BC_FARFIELD && !(bc.rho > 0.0))
+      return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "bc %d: rho <= 0", b);
+  }
+  for (int64_t i = 0; i < m->n_cells; ++i)
+    if (!(m->cell_volume[i] > 0.0) || !std::isfinite(m->cell_volume[i]))
+      return fail(nullptr, UGKS_ERR_MESH, "cell %lld has non-positive volume", (long long)i);
+  std::vector<int> nfaces(m->n_cells, 0);
+  for (int64_t f = 0; f < m->n_faces; ++f) {
+    int64_t o = m->face_owner[f], n = m->face_neighbor[f];
+    if (o < 0 || o >= m->n_cells) return fail(nullptr, UGKS_ERR_MESH, "face %lld: owner out of range", (long long)f);
+    if (n >= m->n_cells || n == o || (n < 0 && -n - 1 >= m->n_bc))
+      return fail(nullptr, UGKS_ERR_MESH, "face %lld: bad neighbour %lld", (long long)f, (long long)n);
+    if (!(m->face_area[f] > 0.0)) return fail(nullptr, UGKS_ERR_MESH, "face %lld: non-positive area", (long long)f);
+    double nn = 0.0;
+    for (int d = 0; d < D; ++d) nn += m->face_normal[f * D + d] * m->face_normal[f * D + d];
+    if (std::fabs(nn - 1.0) > 1e-8) return fail(nullptr, UGKS_ERR_MESH, "face %lld: normal not unit", (long long)f);
+    if (++nfaces[o] > MAXF || (n >= 0 && ++nfaces[n] > MAXF))
+      return fail(nullptr, UGKS_ERR_MESH, "more than %d faces on a cell", MAXF);
+  }
+  if (v->n_v <= 0 || !v->u || !v->weight) return fail(nullptr, UGKS_ERR_VGRID, "empty velocity grid");
+  for (int64_t k = 0; k < v->n_v; ++k) {
+    if (!(v->weight[k] >= 0.0) || !std::isfinite(v->weight[k]))
+      return fail(nullptr, UGKS_ERR_VGRID, "velocity %lld: bad weight", (long long)k);
+    for (int d = 0; d < D; ++d)
+      if (!std::isfinite(v->u[k * D + d])) return fail(nullptr, UGKS_ERR_VGRID, "velocity %lld: non-finite", (long long)k);
+  }
+  if (p->model != UGKS_MODEL_BGK && p->model != UGKS_MODEL_SHAKHOV)
+    return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "unknown model");
+  if (p->K < 0) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "K must be >= 0");
+  if (p->model == UGKS_MODEL_SHAKHOV && p->K != 0)
+    return fail(nullptr, UGKS_ERR_UNSUPPORTED, "the reduced Shakhov terms (Eq. 18-19) hold for K = 0 only");
+  if (p->model == UGKS_MODEL_BGK && p->Pr != 1.0)
+    return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "BGK has Pr = 1");
+  if (!(p->Pr > 0.0) || !(p->mu_ref > 0.0)) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "Pr, mu_ref must be > 0");
+  if (!(p->dt_override > 0.0) && !(p->cfl > 0.0))
+    return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "need cfl > 0 or dt_override > 0");
+  if (p->limiter < 0 || p->limiter > 2) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "unknown limiter");
+  if (p->storage != UGKS_STORAGE_F64 && p->storage != UGKS_STORAGE_F32)
+    return fail(nullptr, UGKS_ERR_UNSUPPORTED, "storage precision %d not implemented", p->storage);
+  if (p->tile_cells < 0) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "tile_cells must be >= 0");
+  return UGKS_OK;
+}
+
+template <typename T>
+size_t tsize() {
+  return sizeof(T);
+}
+
+void record_start(ugks_ctx* ctx, int id, cudaEvent_t* ev) {
+  *ev = nullptr;
+  if (!ctx->stats_on) return;
+  cudaEventCreate(ev);
+  cudaEventRecord(*ev, ctx->stream);
+  (void)id;
+}
+
+void record_stop(ugks_ctx* ctx, int id, cudaEvent_t start) {
+  if (!ctx->stats_on || !start) return;
+  cudaEvent_t stop;
+  cudaEventCreate(&stop);
+  cudaEventRecord(stop, ctx->stream);
+  ctx->timings.push_back({id, start, stop});
+}
+
+template <typename T>
+ugks_status build_typed(ugks_ctx* ctx, const std::vector<CellFace>& cf, const std::vector<double>& eps2,
+                        const std::vector<FaceGeom<double>>& fg64, const double* ux, const double* uy,
+                        const double* uz, const double* wp) {
+  std::vector<CellFaceT<T>> cft(cf.size());
+  for (size_t e = 0; e < cf.size(); ++e) {
+    for (int d = 0; d < 3; ++d) {
+      cft[e].w[d] = T(cf[e].w[d]);
+      cft[e].r[d] = T(cf[e].r[d]);
+    }
+    cft[e].area = T(cf[e].area);
+    cft[e].other = cf[e].other;
+    cft[e].bc = cf[e].other < 0 ? int32_t(-cf[e].other - 1) : -1;
+    cft[e].flags = cf[e].bc_type == UGKS_BC_WALL ? 1 : 0;
+  }
+  std::vector<T> e2(eps2.begin(), eps2.end());
+  std::vector<FaceGeom<T>> fg(fg64.size());
+  for (size_t f = 0; f < fg64.size(); ++f) {
+    for (int d = 0; d < 3; ++d) {
+      fg[f].n[d] = T(fg64[f].n[d]);
+      fg[f].rl[d] = T(fg64[f].rl[d]);
+      fg[f].rr[d] = T(fg64[f].rr[d]);
+    }
+    fg[f].area = T(fg64[f].area);
+    fg[f].own = fg64[f].own;
+    fg[f].nei = fg64[f].nei;
+    fg[f].bc_type = fg64[f].bc_type;
+    fg[f].pad = 0;
+  }
+  const size_t Mp = size_t(ctx->M) * BV;
+  std::vector<T> tux(Mp), tuy(Mp), tuz(Mp), tw(Mp);
+  for (size_t k = 0; k < Mp; ++k) {
+    tux[k] = T(ux[k]);
+    tuy[k] = T(uy[k]);
+    tuz[k] = T(uz[k]);
+    tw[k] = T(wp[k]);
+  }
+  T *cfT, *ep, *fgp, *a, *b, *c, *w;
+  CUDA_TRY(ctx, upload(ctx, reinterpret_cast<CellFaceT<T>**>(&cfT), cft.data(), cft.size() * sizeof(CellFaceT<T>)));
+  ctx->d_cfT = cfT;
+  CUDA_TRY(ctx, upload(ctx, &ep, e2.data(), e2.size() * sizeof(T)));
+  ctx->d_eps2 = ep;
+  CUDA_TRY(ctx, upload(ctx, reinterpret_cast<FaceGeom<T>**>(&fgp), fg.data(), fg.size() * sizeof(FaceGeom<T>)));
+  ctx->d_fg = fgp;
+  CUDA_TRY(ctx, upload(ctx, &a, tux.data(), Mp * sizeof(T)));
+  CUDA_TRY(ctx, upload(ctx, &b, tuy.data(), Mp * sizeof(T)));
+  CUDA_TRY(ctx, upload(ctx, &c, tuz.data(), Mp * sizeof(T)));
+  CUDA_TRY(ctx, upload(ctx, &w, tw.data(), Mp * sizeof(T)));
+  ctx->d_uxT = a;
+  ctx->d_uyT = b;
+  ctx->d_uzT = c;
+  ctx->d_wT = w;
+  FaceRec<T>* fr;
+  CUDA_TRY(ctx, dalloc(ctx, &fr, size_t(ctx->Nf) * sizeof(FaceRec<T>)));
+  ctx->d_fr = fr;
+  const size_t fsz = size_t(ctx->NR) * ctx->M * ctx->Nc * BV * sizeof(T);
+  for (int s = 0; s < 2; ++s) {
+    T* f;
+    CUDA_TRY(ctx, dalloc(ctx, &f, fsz));
+    ctx->d_f[s] = f;
+  }
+  T *G, *Phi;
+  CUDA_TRY(ctx, dalloc(ctx, &G, size_t(ctx->ntiles) * ctx->G_stride * sizeof(T)));
+  CUDA_TRY(ctx, dalloc(ctx, &Phi, size_t(ctx->ntiles) * ctx->Phi_stride * sizeof(T)));
+  ctx->d_G = G;
+  ctx->d_Phi = Phi;
+  return UGKS_OK;
+}
+
+template <typename T>
+ugks_status init_state_typed(ugks_ctx* ctx) {
+  launch_init_f<T>(ctx->stream, ctx->Nc, ctx->M, ctx->nv, ctx->gas, ctx->d_W[0], ctx->d_ux, ctx->d_uy, ctx->d_uz,
+                   static_cast<T*>(ctx->d_f[0]));
+  CUDA_TRY(ctx, cudaGetLastError());
+  launch_moments<T>(ctx->stream, ctx->Nc, ctx->M, ctx->gas, static_cast<const T*>(ctx->d_f[0]), ctx->d_W[0],
+                    ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp, ctx->d_q[0], nullptr);
+  CUDA_TRY(ctx, cudaGetLastError());
+  return UGKS_OK;
+}
+
+template <typename T>
+ugks_status step_typed(ugks_ctx* ctx) {
+  const int cur = ctx->cur, nxt = 1 - cur;
+  cudaEvent_t ev;
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_res_acc, 0, NWP * sizeof(double), ctx->stream));
+  record_start(ctx, 0, &ev);
+  launch_cell(ctx->stream, ctx->Nc, ctx->gas, ctx->d_W[cur], ctx->d_q[cur], ctx->d_cf_off, ctx->d_cf, ctx->d_vol,
+              ctx->d_bcs, ctx->d_cp[0], ctx->d_gW, ctx->d_status);
+  CUDA_TRY(ctx, cudaGetLastError());
+  record_stop(ctx, 0, ev);
+  record_start(ctx, 1, &ev);
+  launch_face<T>(ctx->stream, ctx->Nf, ctx->gas, ctx->d_W[cur], ctx->d_gW, ctx->d_q[cur], ctx->d_fown, ctx->d_fnei,
+                 ctx->d_fnormal, ctx->d_fcent, ctx->d_fshift, ctx->d_xc, ctx->d_bcs,
+                 static_cast<FaceRec<T>*>(ctx->d_fr));
+  CUDA_TRY(ctx, cudaGetLastError());
+  record_stop(ctx, 1, ev);
+  SweepArgs<T> a;
+  a.g = ctx->gas;
+  a.Nc = ctx->Nc;
+  a.M = ctx->M;
+  a.nv = ctx->nv;
+  a.f_cur = static_cast<const T*>(ctx->d_f[cur]);
+  a.f_next = static_cast<T*>(ctx->d_f[nxt]);
+  a.W_cur = ctx->d_W[cur];
+  a.W_next = ctx->d_W[nxt];
+  a.cp = ctx->d_cp[0];
+  a.cp_next = ctx->d_cp[1];
+  a.q_next = ctx->d_q[nxt];
+  a.ux = static_cast<const T*>(ctx->d_uxT);
+  a.uy = static_cast<const T*>(ctx->d_uyT);
+  a.uz = static_cast<const T*>(ctx->d_uzT);
+  a.w = static_cast<const T*>(ctx->d_wT);
+  a.vol = ctx->d_vol;
+  a.eps2 = static_cast<const T*>(ctx->d_eps2);
+  a.cf_off = ctx->d_cf_off;
+  a.cf = static_cast<const CellFaceT<T>*>(ctx->d_cfT);
+  a.fg = static_cast<const FaceGeom<T>*>(ctx->d_fg);
+  a.fr = static_cast<const FaceRec<T>*>(ctx->d_fr);
+  a.bcs = ctx->d_bcs;
+  a.tile_begin = ctx->d_tile_begin;
+  a.gset_off = ctx->d_gset_off;
+  a.gset = ctx->d_gset;
+  a.tf_off = ctx->d_tf_off;
+  a.tf = ctx->d_tf;
+  a.tcf = ctx->d_tcf;
+  a.G = static_cast<T*>(ctx->d_G);
+  a.Phi = static_cast<T*>(ctx->d_Phi);
+  a.Facc = ctx->d_Facc;
+  a.G_stride = ctx->G_stride;
+  a.Phi_stride = ctx->Phi_stride;
+  a.Facc_stride = ctx->Facc_stride;
+  a.res_acc = ctx->d_res_acc;
+  a.status = ctx->d_status;
+  record_start(ctx, 2, &ev);
+  CUDA_TRY(ctx, launch_sweep<T>(ctx->stream, a, ctx->ntiles, ctx->threads));
+  record_stop(ctx, 2, ev);
+  record_start(ctx, 3, &ev);
+  launch_residual_finalize(ctx->stream, ctx->D + 2, ctx->Nc, ctx->d_res_acc, ctx->d_res);
+  CUDA_TRY(ctx, cudaGetLastError());
+  record_stop(ctx, 3, ev);
+  ctx->cur = nxt;
+  ctx->step++;
+  return UGKS_OK;
+}
+
+ugks_status check_status(ugks_ctx* ctx) {
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  int st = 0;
+  CUDA_TRY(ctx, cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) return fail(ctx, UGKS_ERR_NONFINITE, "non-physical state (rho <= 0, T <= 0 or NaN) was produced");
+  return UGKS_OK;
+}
+
+ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_params* p, const double* W_init,
+                        void* stream, ugks_ctx* ctx) {
+  const int D = m->dim;
+  ctx->D = D;
+  ctx->K = p->K;
+  const int Kxi = p->K + 3 - D;
+  ctx->NR = Kxi > 0 ? 2 : 1;
+  ctx->storage = p->storage;
+  ctx->Nc = m->n_cells;
+  ctx->Nf = m->n_faces;
+  ctx->nv = v->n_v;
+  ctx->M = (v->n_v + BV - 1) / BV;
+  if (stream) {
+    ctx->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    ctx->own_stream = true;
+  }
+  const int64_t Nc = ctx->Nc, Nf = ctx->Nf;
+
+  // ---- locality renumbering: Morton order of the cell centroids ----
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t i = 0; i < Nc; ++i)
+    for (int d = 0; d < D; ++d) {
+      lo[d] = std::min(lo[d], m->cell_centroid[i * D + d]);
+      hi[d] = std::max(hi[d], m->cell_centroid[i * D + d]);
+    }
+  std::vector<uint64_t> key(Nc);
+  for (int64_t i = 0; i < Nc; ++i) {
+    uint64_t kk = 0;
+    for (int d = 0; d < D; ++d) {
+      double span = hi[d] > lo[d] ? hi[d] - lo[d] : 1.0;
+      uint64_t q = uint64_t(std::min(2097151.0, std::max(0.0, (m->cell_centroid[i * D + d] - lo[d]) / span * 2097151.0)));
+      kk |= spread3(q) << d;
+    }
+    key[i] = kk;
+  }
+  ctx->old_of_new.resize(Nc);
+  std::iota(ctx->old_of_new.begin(), ctx->old_of_new.end(), 0);
+  std::stable_sort(ctx->old_of_new.begin(), ctx->old_of_new.end(),
+                   [&](int64_t a, int64_t b) { return key[a] < key[b]; });
+  ctx->new_of_old.resize(Nc);
+  for (int64_t i = 0; i < Nc; ++i) ctx->new_of_old[ctx->old_of_new[i]] = i;
+  const auto& n_of_o = ctx->new_of_old;
+  const auto& o_of_n = ctx->old_of_new;
+
+  // ---- cell geometry in the new order ----
+  std::vector<double> vol(Nc), xc(Nc * 3, 0.0);
+  for (int64_t i = 0; i < Nc; ++i) {
+    int64_t o = o_of_n[i];
+    vol[i] = m->cell_volume[o];
+    for (int d = 0; d < D; ++d) xc[i * 3 + d] = m->cell_centroid[o * D + d];
+  }
+  // ---- face geometry ----
+  std::vector<int64_t> fown(Nf), fnei(Nf);
+  std::vector<double> fnormal(Nf * 3, 0.0), fcent(Nf * 3, 0.0), fshift(Nf * 3, 0.0);
+  std::vector<FaceGeom<double>> fg(Nf);
+  for (int64_t f = 0; f < Nf; ++f) {
+    fown[f] = n_of_o[m->face_owner[f]];
+    int64_t nb = m->face_neighbor[f];
+    fnei[f] = nb >= 0 ? n_of_o[nb] : nb;
+    for (int d = 0; d < D; ++d) {
+      fnormal[f * 3 + d] = m->face_normal[f * D + d];
+      fcent[f * 3 + d] = m->face_centroid[f * D + d];
+      fshift[f * 3 + d] = m->face_shift ? m->face_shift[f * D + d] : 0.0;
+    }
+    FaceGeom<double>& g = fg[f];
+    for (int d = 0; d < 3; ++d) {
+      g.n[d] = fnormal[f * 3 + d];
+      g.rl[d] = d < D ? fcent[f * 3 + d] - xc[fown[f] * 3 + d] : 0.0;
+      g.rr[d] = (d < D && fnei[f] >= 0) ? fcent[f * 3 + d] - fshift[f * 3 + d] - xc[fnei[f] * 3 + d] : 0.0;
+    }
+    g.area = m->face_area[f];
+    g.own = fown[f];
+    g.nei = fnei[f];
+    g.bc_type = nb >= 0 ? 0 : m->bc[-nb - 1].type;
+    g.pad = 0;
+  }
+  // ---- incidence CSR with least-squares weights ----
+  std::vector<int64_t> cf_off(Nc + 1, 0);
+  for (int64_t f = 0; f < Nf; ++f) {
+    cf_off[fown[f] + 1]++;
+    if (fnei[f] >= 0) cf_off[fnei[f] + 1]++;
+  }
+  for (int64_t i = 0; i < Nc; ++i) cf_off[i + 1] += cf_off[i];
+  std::vector<CellFace> cf(cf_off[Nc]);
+  {
+    std::vector<int64_t> fill(cf_off.begin(), cf_off.end() - 1);
+    for (int64_t f = 0; f < Nf; ++f) {
+      for (int side = 0; side < 2; ++side) {
+        int64_t c = side == 0 ? fown[f] : fnei[f];
+        if (c < 0) continue;
+        CellFace e{};
+        e.face = f;
+        e.sign = side == 0 ? 1 : -1;
+        e.other = side == 0 ? fnei[f] : fown[f];
+        e.bc_type = fnei[f] >= 0 ? 0 : m->bc[-fnei[f] - 1].type;
+        e.area = m->face_area[f];
+        for (int d = 0; d < D; ++d) e.r[d] = fcent[f * 3 + d] - (side == 0 ? 0.0 : fshift[f * 3 + d]) - xc[c * 3 + d];
+        cf[fill[c]++] = e;
+      }
+    }
+  }
+  std::vector<double> eps2(Nc);
+  for (int64_t i = 0; i < Nc; ++i) {
+    double M3[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double dx[MAXF][3];
+    for (int64_t e = cf_off[i]; e < cf_off[i + 1]; ++e) {
+      CellFace& s = cf[e];
+      double* d_ = dx[e - cf_off[i]];
+      for (int d = 0; d < 3; ++d) d_[d] = 0.0;
+      if (s.bc_type == UGKS_BC_WALL) continue;
+      const double* n = &fnormal[s.face * 3];
+      if (s.other >= 0) {
+        double sh = s.sign > 0 ? 1.0 : -1.0;
+        for (int d = 0; d < D; ++d) d_[d] = xc[s.other * 3 + d] + sh * fshift[s.face * 3 + d] - xc[i * 3 + d];
+      } else {
+        double dn = 0.0;
+        for (int d = 0; d < D; ++d) dn += s.r[d] * n[d];
+        for (int d = 0; d < D; ++d) d_[d] = 2.0 * dn * n[d];
+      }
+      for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) M3[a * D + b] += d_[a] * d_[b];
+    }
+    double Minv[9];
+    bool ok = lsq_inverse(D, M3, Minv);
+    for (int64_t e = cf_off[i]; e < cf_off[i + 1]; ++e) {
+      CellFace& s = cf[e];
+      const double* d_ = dx[e - cf_off[i]];
+      for (int a = 0; a < 3; ++a) {
+        double w = 0.0;
+        if (ok && a < D && s.bc_type != UGKS_BC_WALL)
+          for (int b = 0; b < D; ++b) w += Minv[a * D + b] * d_[b];
+        s.w[a] = w;
+      }
+    }
+    eps2[i] = std::pow(p->venkat_K * std::pow(vol[i], 1.0 / D), 3.0);
+  }
+
+  // ---- padded velocity grid (zero weight, zero velocity beyond n_v) ----
+  const int64_t Mp = ctx->M * BV;
+  std::vector<double> ux(Mp, 0.0), uy(Mp, 0.0), uz(Mp, 0.0), wp(Mp, 0.0);
+  for (int64_t k = 0; k < v->n_v; ++k) {
+    ux[k] = v->u[k * D];
+    if (D > 1) uy[k] = v->u[k * D + 1];
+    if (D > 2) uz[k] = v->u[k * D + 2];
+    wp[k] = v->weight[k];
+  }
+
+  // ---- tiles of the sweep ----
+  ctx->threads = 512;
+  int dev = 0, nsm = 1;
+  CUDA_TRY(ctx, cudaGetDevice(&dev));
+  CUDA_TRY(ctx, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int occ = ctx->storage == UGKS_STORAGE_F64 ? sweep_occupancy<double>(D, ctx->NR, ctx->threads)
+                                             : sweep_occupancy<float>(D, ctx->NR, ctx->threads);
+  CUDA_TRY(ctx, cudaGetLastError());
+  if (occ < 1) occ = 1;
+  int64_t ntiles = int64_t(nsm) * occ;
+  if (p->tile_cells > 0) ntiles = (Nc + p->tile_cells - 1) / p->tile_cells;
+  ntiles = std::max<int64_t>(1, std::min<int64_t>(ntiles, std::max<int64_t>(1, Nc / 16)));
+  ctx->ntiles = int(ntiles);
+  std::vector<int64_t> tile_begin(ntiles + 1);
+  for (int64_t t = 0; t <= ntiles; ++t) tile_begin[t] = (Nc * t) / ntiles;
+  std::vector<int64_t> gset_off(ntiles + 1, 0), gset, tf_off(ntiles + 1, 0);
+  std::vector<TileFace> tfl;
+  std::vector<int32_t> tcf(cf.size(), 0);
+  std::vector<int64_t> cell_mark(Nc, -1), cell_local(Nc, -1), face_mark(Nf, -1), face_local(Nf, -1);
+  int64_t max_ng = 1, max_nf = 1;
+  for (int64_t t = 0; t < ntiles; ++t) {
+    int64_t ng = 0;
+    for (int64_t c = tile_begin[t]; c < tile_begin[t + 1]; ++c) {
+      cell_mark[c] = t;
+      cell_local[c] = ng++;
+      gset.push_back(c);
+    }
+    for (int64_t c = tile_begin[t]; c < tile_begin[t + 1]; ++c)
+      for (int64_t e = cf_off[c]; e < cf_off[c + 1]; ++e) {
+        int64_t o = cf[e].other;
+        if (o >= 0 && cell_mark[o] != t) {
+          cell_mark[o] = t;
+          cell_local[o] = ng++;
+          gset.push_back(o);
+        }
+      }
+    int64_t nfl = 0;
+    for (int64_t c = tile_begin[t]; c < tile_begin[t + 1]; ++c)
+      for (int64_t e = cf_off[c]; e < cf_off[c + 1]; ++e) {
+        int64_t f = cf[e].face;
+        if (face_mark[f] != t) {
+          face_mark[f] = t;
+          face_local[f] = nfl++;
+          TileFace tfe;
+          tfe.face = f;
+          tfe.lo = int32_t(cell_local[fown[f]]);
+          tfe.ln = fnei[f] >= 0 ? int32_t(cell_local[fnei[f]]) : -1;
+          tfl.push_back(tfe);
+        }
+        tcf[e] = int32_t(face_local[f] << 1) | (cf[e].sign < 0 ? 1 : 0);
+      }
+    gset_off[t + 1] = gset_off[t] + ng;
+    tf_off[t + 1] = tf_off[t] + nfl;
+    max_ng = std::max(max_ng, ng);
+    max_nf = std::max(max_nf, nfl);
+  }
+  ctx->G_stride = max_ng * ctx->NR * D * BV;
+  ctx->Phi_stride = max_nf * ctx->NR * BV;
+  ctx->Facc_stride = max_nf * FACC_W;
+
+  // ---- gas ----
+  Gas& g = ctx->gas;
+  g.D = D;
+  g.K = p->K;
+  g.Kxi = Kxi;
+  g.NR = ctx->NR;
+  g.shakhov = p->model == UGKS_MODEL_SHAKHOV;
+  g.limiter = p->limiter;
+  g.shock_fix = p->shock_tau_fix;
+  g.Pr = p->Pr;
+  g.omega = p->omega;
+  g.mu_ref = p->mu_ref;
+  g.venkat_K = p->venkat_K;
+
+  // ---- device uploads ----
+  std::vector<BCDev> bcs(std::max(1, m->n_bc));
+  for (int b = 0; b < m->n_bc; ++b) {
+    bcs[b].type = m->bc[b].type;
+    bcs[b].pad = 0;
+    bcs[b].rho = m->bc[b].rho;
+    for (int d = 0; d < 3; ++d) bcs[b].u[d] = m->bc[b].u[d];
+    bcs[b].T = m->bc[b].T;
+  }
+  std::vector<double> W0(Nc * NWP, 0.0);
+  for (int64_t i = 0; i < Nc; ++i) {
+    int64_t o = o_of_n[i];
+    if (W_init) {
+      for (int t = 0; t < D + 2; ++t) W0[i * NWP + t] = W_init[o * (D + 2) + t];
+    } else {
+      if (m->n_bc < 1) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "W_init is NULL and the mesh has no bc");
+      const ugks_bc& b = m->bc[0];
+      double u2 = 0.0;
+      W0[i * NWP] = b.rho;
+      for (int d = 0; d < D; ++d) {
+        W0[i * NWP + 1 + d] = b.rho * b.u[d];
+        u2 += b.u[d] * b.u[d];
+      }
+      W0[i * NWP + D + 1] = 0.5 * b.rho * u2 + (p->K + 3) * b.rho * b.T / 4.0;
+    }
+  }
+  for (int64_t i = 0; i < Nc; ++i) {
+    const double* Wi = &W0[i * NWP];
+    double u2 = 0.0;
+    for (int d = 0; d < D; ++d) u2 += (Wi[1 + d] / Wi[0]) * (Wi[1 + d] / Wi[0]);
+    if (!(Wi[0] > 0.0) || !(Wi[D + 1] - 0.5 * Wi[0] * u2 > 0.0) || !std::isfinite(Wi[D + 1]))
+      return fail(ctx, UGKS_ERR_NONFINITE, "W_init of cell %lld is not a physical state", (long long)o_of_n[i]);
+  }
+  std::vector<double> uflat(v->n_v * D);
+  std::copy(v->u, v->u + v->n_v * D, uflat.begin());
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_vol, vol.data(), Nc * sizeof(double)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_xc, xc.data(), Nc * 3 * sizeof(double)));
+  for (int s = 0; s < 2; ++s) {
+    CUDA_TRY(ctx, dalloc(ctx, &ctx->d_W[s], Nc * NWP * sizeof(double)));
+    CUDA_TRY(ctx, dalloc(ctx, &ctx->d_q[s], Nc * 3 * sizeof(double)));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_q[s], 0, Nc * 3 * sizeof(double), ctx->stream));
+    CUDA_TRY(ctx, dalloc(ctx, &ctx->d_cp[s], Nc * sizeof(CellPrim)));
+  }
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_W[0], W0.data(), Nc * NWP * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, dalloc(ctx, &ctx->d_gW, Nc * NWP * 3 * sizeof(double)));
+  CUDA_TRY(ctx, dalloc(ctx, &ctx->d_res_acc, NWP * sizeof(double)));
+  CUDA_TRY(ctx, dalloc(ctx, &ctx->d_res, NWP * sizeof(double)));
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_res, 0, NWP * sizeof(double), ctx->stream));
+  CUDA_TRY(ctx, dalloc(ctx, &ctx->d_status, sizeof(int)));
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_cf_off, cf_off.data(), cf_off.size() * sizeof(int64_t)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_cf, cf.data(), cf.size() * sizeof(CellFace)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_fown, fown.data(), Nf * sizeof(int64_t)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_fnei, fnei.data(), Nf * sizeof(int64_t)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_fnormal, fnormal.data(), Nf * 3 * sizeof(double)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_fcent, fcent.data(), Nf * 3 * sizeof(double)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_fshift, fshift.data(), Nf * 3 * sizeof(double)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_bcs, bcs.data(), bcs.size() * sizeof(BCDev)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_u, uflat.data(), uflat.size() * sizeof(double)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_wgt, v->weight, v->n_v * sizeof(double)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_ux, ux.data(), Mp * sizeof(double)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_uy, uy.data(), Mp * sizeof(double)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_uz, uz.data(), Mp * sizeof(double)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_wp, wp.data(), Mp * sizeof(double)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_tile_begin, tile_begin.data(), tile_begin.size() * sizeof(int64_t)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_gset_off, gset_off.data(), gset_off.size() * sizeof(int64_t)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_gset, gset.data(), gset.size() * sizeof(int64_t)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_tf_off, tf_off.data(), tf_off.size() * sizeof(int64_t)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_tf, tfl.data(), tfl.size() * sizeof(TileFace)));
+  CUDA_TRY(ctx, upload(ctx, &ctx->d_tcf, tcf.data(), tcf.size() * sizeof(int32_t)));
+  CUDA_TRY(ctx, dalloc(ctx, &ctx->d_Facc, size_t(ntiles) * ctx->Facc_stride * sizeof(double)));
+
+  // ---- time step ----
+  if (p->dt_override > 0.0) {
+    ctx->dt = p->dt_override;
+  } else {
+    unsigned long long* bits;
+    CUDA_TRY(ctx, dalloc(ctx, &bits, sizeof(unsigned long long)));
+    unsigned long long init = 0x7ff0000000000000ULL;  // +inf
+    CUDA_TRY(ctx, cudaMemcpyAsync(bits, &init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+    launch_time_step(ctx->stream, Nc, D, ctx->d_cf_off, ctx->d_cf, ctx->d_fnormal, ctx->d_vol, ctx->d_u, ctx->d_wgt,
+                     v->n_v, bits);
+    CUDA_TRY(ctx, cudaGetLastError());
+    unsigned long long out = 0;
+    CUDA_TRY(ctx, cudaMemcpyAsync(&out, bits, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    double dmin;
+    std::memcpy(&dmin, &out, sizeof(dmin));
+    if (!std::isfinite(dmin)) return fail(ctx, UGKS_ERR_VGRID, "no velocity with positive weight moves");
+    ctx->dt = p->cfl * dmin;
+  }
+  g.dt = ctx->dt;
+
+  ugks_status st = ctx->storage == UGKS_STORAGE_F64
+                       ? build_typed<double>(ctx, cf, eps2, fg, ux.data(), uy.data(), uz.data(), wp.data())
+                       : build_typed<float>(ctx, cf, eps2, fg, ux.data(), uy.data(), uz.data(), wp.data());
+  if (st != UGKS_OK) return st;
+  st = ctx->storage == UGKS_STORAGE_F64 ? init_state_typed<double>(ctx) : init_state_typed<float>(ctx);
+  if (st != UGKS_OK) return st;
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return UGKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ugks_status ugks_create(const ugks_mesh* mesh, const ugks_vgrid* vgrid, const ugks_params* params,
+                        const double* W_init, void* cuda_stream, ugks_ctx** out) {
+  if (!out) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "out must not be NULL");
+  *out = nullptr;
+  ugks_status st = validate(mesh, vgrid, params);
+  if (st != UGKS_OK) return st;
+  if (vgrid->n_v > 0 && mesh->n_cells > 0) {
+    // (NR * M * Nc * BV) elements must be addressable
+    double elems = 2.0 * double((vgrid->n_v + BV - 1) / BV) * BV * double(mesh->n_cells);
+    if (elems > 9.0e18) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "problem too large");
+  }
+  ugks_ctx* ctx = new (std::nothrow) ugks_ctx();
+  if (!ctx) return fail(nullptr, UGKS_ERR_OUT_OF_MEMORY, "host allocation failed");
+  st = create_impl(mesh, vgrid, params, W_init, cuda_stream, ctx);
+  if (st != UGKS_OK) {
+    g_thread_err = ctx->err;
+    release(ctx);
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return UGKS_OK;
+}
+
+ugks_status ugks_step(ugks_ctx* ctx, int32_t n_steps) {
+  if (!ctx) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL context");
+  if (n_steps < 0) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "n_steps must be >= 0");
+  for (int32_t s = 0; s < n_steps; ++s) {
+    ugks_status st = ctx->storage == UGKS_STORAGE_F64 ? step_typed<double>(ctx) : step_typed<float>(ctx);
+    if (st != UGKS_OK) return st;
+  }
+  return UGKS_OK;
+}
+
+ugks_status ugks_moments(ugks_ctx* ctx, double* W_out, double* q_out) {
+  if (!ctx || !W_out) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "NULL argument");
+  ugks_status st = check_status(ctx);
+  if (st != UGKS_OK) return st;
+  const int D = ctx->D;
+  std::vector<double> W(ctx->Nc * NWP), q(ctx->Nc * 3);
+  CUDA_TRY(ctx, cudaMemcpy(W.data(), ctx->d_W[ctx->cur], W.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  if (q_out) CUDA_TRY(ctx, cudaMemcpy(q.data(), ctx->d_q[ctx->cur], q.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < ctx->Nc; ++i) {
+    int64_t o = ctx->old_of_new[i];
+    for (int t = 0; t < D + 2; ++t) W_out[o * (D + 2) + t] = W[i * NWP + t];
+    if (q_out)
+      for (int d = 0; d < D; ++d) q_out[o * D + d] = q[i * 3 + d];
+  }
+  return UGKS_OK;
+}
+
+ugks_status ugks_residual(ugks_ctx* ctx, double* res_out) {
+  if (!ctx || !res_out) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "NULL argument");
+  ugks_status st = check_status(ctx);
+  if (st != UGKS_OK) return st;
+  CUDA_TRY(ctx, cudaMemcpy(res_out, ctx->d_res, (ctx->D + 2) * sizeof(double), cudaMemcpyDeviceToHost));
+  return UGKS_OK;
+}
+
+ugks_status ugks_dt(const ugks_ctx* ctx, double* dt_out) {
+  if (!ctx || !dt_out) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL argument");
+  *dt_out = ctx->dt;
+  return UGKS_OK;
+}
+
+ugks_status ugks_sizes(const ugks_ctx* ctx, int32_t* n_reduced, int64_t* n_v_padded) {
+  if (!ctx) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL context");
+  if (n_reduced) *n_reduced = ctx->NR;
+  if (n_v_padded) *n_v_padded = ctx->M * BV;
+  return UGKS_OK;
+}
+
+ugks_status ugks_get_f(ugks_ctx* ctx, const int64_t* cells, int64_t n, double* out) {
+  if (!ctx || (n > 0 && (!cells || !out)) || n < 0) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "bad arguments");
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (n == 0) return UGKS_OK;
+  std::vector<int64_t> sel(n);
+  for (int64_t s = 0; s < n; ++s) {
+    if (cells[s] < 0 || cells[s] >= ctx->Nc) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "cell index out of range");
+    sel[s] = ctx->new_of_old[cells[s]];
+  }
+  int64_t *d_sel = nullptr;
+  double* d_out = nullptr;
+  const size_t nout = size_t(n) * ctx->NR * ctx->nv;
+  CUDA_TRY(ctx, cudaMalloc(&d_sel, n * sizeof(int64_t)));
+  cudaError_t e = cudaMalloc(&d_out, nout * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_sel, sel.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) {
+    if (ctx->storage == UGKS_STORAGE_F64)
+      launch_gather_f<double>(ctx->stream, ctx->Nc, ctx->M, ctx->NR, ctx->nv,
+                              static_cast<const double*>(ctx->d_f[ctx->cur]), d_sel, n, d_out);
+    else
+      launch_gather_f<float>(ctx->stream, ctx->Nc, ctx->M, ctx->NR, ctx->nv,
+                             static_cast<const float*>(ctx->d_f[ctx->cur]), d_sel, n, d_out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, nout * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d_sel);
+  if (d_out) cudaFree(d_out);
+  if (e != cudaSuccess) return fail(ctx, UGKS_ERR_CUDA, "ugks_get_f: %s", cudaGetErrorString(e));
+  return UGKS_OK;
+}
+
+ugks_status ugks_get_state(ugks_ctx* ctx, double* W, double* f, int64_t* step) {
+  if (!ctx || !W) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "NULL argument");
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  {
+    const int D = ctx->D;
+    std::vector<double> Wd(ctx->Nc * NWP);
+    CUDA_TRY(ctx, cudaMemcpy(Wd.data(), ctx->d_W[ctx->cur], Wd.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < ctx->Nc; ++i)
+      for (int t = 0; t < D + 2; ++t) W[ctx->old_of_new[i] * (D + 2) + t] = Wd[i * NWP + t];
+  }
+  ugks_status st = UGKS_OK;
+  if (step) *step = ctx->step;
+  if (!f) return UGKS_OK;
+  std::vector<int64_t> all(ctx->Nc);
+  std::iota(all.begin(), all.end(), 0);
+  // gather in original order: out[cell][r][k] -> f[r][cell][k]
+  std::vector<double> tmp(size_t(ctx->Nc) * ctx->NR * ctx->nv);
+  st = ugks_get_f(ctx, all.data(), ctx->Nc, tmp.data());
+  if (st != UGKS_OK) return st;
+  for (int64_t c = 0; c < ctx->Nc; ++c)
+    for (int r = 0; r < ctx->NR; ++r)
+      std::memcpy(f + (size_t(r) * ctx->Nc + c) * ctx->nv, &tmp[(size_t(c) * ctx->NR + r) * ctx->nv],
+                  ctx->nv * sizeof(double));
+  return UGKS_OK;
+}
+
+ugks_status ugks_set_state(ugks_ctx* ctx, const double* W, const double* f, int64_t step) {
+  if (!ctx || !W || !f) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "NULL argument");
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  const int D = ctx->D;
+  std::vector<double> Wn(ctx->Nc * NWP, 0.0);
+  for (int64_t i = 0; i < ctx->Nc; ++i)
+    for (int t = 0; t < D + 2; ++t) Wn[i * NWP + t] = W[ctx->old_of_new[i] * (D + 2) + t];
+  const int c = ctx->cur;
+  CUDA_TRY(ctx, cudaMemcpy(ctx->d_W[c], Wn.data(), Wn.size() * sizeof(double), cudaMemcpyHostToDevice));
+  double* d_in = nullptr;
+  int64_t* d_map = nullptr;
+  const size_t nin = size_t(ctx->NR) * ctx->Nc * ctx->nv;
+  CUDA_TRY(ctx, cudaMalloc(&d_in, nin * sizeof(double)));
+  cudaError_t e = cudaMalloc(&d_map, ctx->Nc * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMemcpy(d_in, f, nin * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_map, ctx->old_of_new.data(), ctx->Nc * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    if (ctx->storage == UGKS_STORAGE_F64)
+      launch_scatter_f<double>(ctx->stream, ctx->Nc, ctx->M, ctx->NR, ctx->nv, d_in, d_map,
+                               static_cast<double*>(ctx->d_f[c]));
+    else
+      launch_scatter_f<float>(ctx->stream, ctx->Nc, ctx->M, ctx->NR, ctx->nv, d_in, d_map,
+                              static_cast<float*>(ctx->d_f[c]));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    if (ctx->storage == UGKS_STORAGE_F64)
+      launch_moments<double>(ctx->stream, ctx->Nc, ctx->M, ctx->gas, static_cast<const double*>(ctx->d_f[c]),
+                             ctx->d_W[c], ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp, ctx->d_q[c], nullptr);
+    else
+      launch_moments<float>(ctx->stream, ctx->Nc, ctx->M, ctx->gas, static_cast<const float*>(ctx->d_f[c]),
+                            ctx->d_W[c], ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp, ctx->d_q[c], nullptr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d_in);
+  if (d_map) cudaFree(d_map);
+  if (e != cudaSuccess) return fail(ctx, UGKS_ERR_CUDA, "ugks_set_state: %s", cudaGetErrorString(e));
+  ctx->step = step;
+  return UGKS_OK;
+}
+
+ugks_status ugks_stats_enable(ugks_ctx* ctx, int32_t on) {
+  if (!ctx) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL context");
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  for (auto& t : ctx->timings) {
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
+  }
+  ctx->timings.clear();
+  for (int i = 0; i < kNumKernels; ++i) {
+    ctx->stat_ms[i] = 0.0;
+    ctx->stat_count[i] = 0;
+  }
+  ctx->stats_on = on != 0;
+  return UGKS_OK;
+}
+
+ugks_status ugks_stats(ugks_ctx* ctx, int32_t cap, const char** names, double* ms, int64_t* count, int32_t* n) {
+  if (!ctx) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL context");
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  for (auto& t : ctx->timings) {
+    float e = 0.0f;
+    CUDA_TRY(ctx, cudaEventElapsedTime(&e, t.start, t.stop));
+    ctx->stat_ms[t.id] += e;
+    ctx->stat_count[t.id]++;
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
+  }
+  ctx->timings.clear();
+  for (int i = 0; i < kNumKernels && i < cap; ++i) {
+    if (names) names[i] = kKernelNames[i];
+    if (ms) ms[i] = ctx->stat_ms[i];
+    if (count) count[i] = ctx->stat_count[i];
+  }
+  if (n) *n = kNumKernels;
+  return UGKS_OK;
+}
+
+ugks_status ugks_solve(const ugks_mesh* mesh, const ugks_vgrid* vgrid, const ugks_params* params,
+                       const double* W_init, int32_t n_steps, double* W_out, double* res_out) {
+  ugks_ctx* ctx = nullptr;
+  ugks_status st = ugks_create(mesh, vgrid, params, W_init, nullptr, &ctx);
+  if (st != UGKS_OK) return st;
+  st = ugks_step(ctx, n_steps);
+  if (st == UGKS_OK && W_out) st = ugks_moments(ctx, W_out, nullptr);
+  if (st == UGKS_OK && res_out) st = ugks_residual(ctx, res_out);
+  if (st != UGKS_OK) g_thread_err = ctx->err;
+  ugks_destroy(ctx);
+  return st;
+}
+
+ugks_status ugks_destroy(ugks_ctx* ctx) {
+  if (!ctx) return UGKS_OK;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  release(ctx);
+  delete ctx;
+  return UGKS_OK;
+}
+
+const char* ugks_last_error(const ugks_ctx* ctx) {
+  if (ctx) return ctx->err.c_str();
+  return g_thread_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// Internal device data layout of the GB300 UGKS library.
+//
+// Distribution storage (Sec. 2.2.2, Eq. 47-48): the padded velocity set is
+// split into blocks of BV = 32 points, one warp lane per velocity, and each
+// reduced distribution r (h, then b) is stored block-major with the velocity
+// innermost:  f[r][m][cell][lane], so that one (r, m, cell) row is a single
+// contiguous 32-element segment (128 B in FP32, 256 B in FP64).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ugks {
+
+constexpr int BV = 32;      // velocity block = warp width
+constexpr int NWP = 5;      // stride of conservative vectors (dim + 2 <= 5)
+constexpr int MAXF = 32;    // faces per cell
+constexpr int FACC_W = 12;  // per-face accumulator: [0,5) flux, [5,10) wall unit-outflow moments, 10 rho_w
+
+// Per-cell primitive record, FP64 (computed each step from W).
+struct CellPrim {
+  double rho, U[3], lam, tau;
+  double q[3];
+  double pad;
+};
+
+// Per-cell incidence entry (CSR over cells): one per face of the cell.
+struct CellFace {
+  int64_t face;    // global face index
+  int64_t other;   // neighbour cell (renumbered) or -(bc+1)
+  double w[3];     // least-squares weight M^-1 d (zero for walls)
+  double r[3];     // face centroid minus cell centroid (cell's frame)
+  double area;
+  int32_t sign;    // +1 owner, -1 neighbour
+  int32_t bc_type; // 0 interior, else UGKS_BC_*
+};
+
+// Same entry in the storage/compute precision of the sweep kernel.
+template <typename T>
+struct CellFaceT {
+  T w[3];
+  T r[3];
+  T area;
+  int64_t other;
+  int32_t bc;      // -1 interior, else bc index
+  int32_t flags;   // bit 0: wall
+};
+
+// Constant per-face geometry in the sweep precision.
+template <typename T>
+struct FaceGeom {
+  T n[3];          // unit normal owner -> neighbour
+  T rl[3];         // face centroid - owner centroid
+  T rr[3];         // face centroid - neighbour centroid (neighbour's frame), or 0
+  T area;
+  int64_t own, nei;   // renumbered cells; nei < 0: -(bc+1)
+  int32_t bc_type;    // 0 interior
+  int32_t pad;
+};
+
+// Per-step interface coefficients in the sweep precision (Eq. 32-35).
+// Interior / far-field / outflow faces: interface Maxwellian g0 and its
+// slopes.  Wall faces: the unit-density wall Maxwellian (rho_pref, U, lam,
+// kappa) and zero elsewhere.
+template <typename T>
+struct FaceRec {
+  T G[5];          // integrals of c1..c5 over [0, dt]
+  T rho_pref;      // rho0 (lambda0/pi)^(D/2)
+  T lam;           // lambda0
+  T U[3];
+  T sq;            // Shakhov prefactor 4 (1-Pr) lambda0^2 / (5 rho0), 0 for BGK
+  T q[3];          // interface heat flux
+  T a[3][5];       // spatial slopes per direction
+  T A[5];          // time slope
+  T kappa;         // K_xi / (2 lambda0)
+  T xi4;           // <xi^4> = K_xi (K_xi + 2) / (4 lambda0^2)
+  T pad[2];
+};
+
+struct BCDev {
+  int32_t type;
+  int32_t pad;
+  double rho, u[3], T;
+};
+
+// Tile face entry: global face index and the local gradient-set indices of
+// the two sides (-1 for a ghost side).
+struct TileFace {
+  int64_t face;
+  int32_t lo, ln;
+};
+
+struct Gas {
+  int D, K, Kxi, NR, shakhov, limiter, shock_fix;
+  double Pr, omega, mu_ref, venkat_K, dt;
+};
+
+}  // namespace ugks

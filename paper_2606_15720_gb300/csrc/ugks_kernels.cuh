@@ -1,0 +1,85 @@
+// Host-side launchers of the UGKS kernels (implemented in ugks_prep.cu and
+// ugks_sweep.cu), called by the C ABI in ugks_capi.cu.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ugks_internal.cuh"
+
+namespace ugks {
+
+void launch_time_step(cudaStream_t s, int64_t Nc, int D, const int64_t* cf_off, const CellFace* cf,
+                      const double* fnormal, const double* vol, const double* u, const double* w, int64_t nv,
+                      unsigned long long* out_bits);
+
+template <typename T>
+void launch_init_f(cudaStream_t s, int64_t Nc, int64_t M, int64_t nv, const Gas& g, const double* W,
+                   const double* ux, const double* uy, const double* uz, T* f);
+
+void launch_cell(cudaStream_t s, int64_t Nc, const Gas& g, const double* W, const double* q, const int64_t* cf_off,
+                 const CellFace* cf, const double* vol, const BCDev* bcs, CellPrim* cp, double* gW, int* status);
+
+template <typename T>
+void launch_face(cudaStream_t s, int64_t Nf, const Gas& g, const double* W, const double* gW, const double* q,
+                 const int64_t* fown, const int64_t* fnei, const double* fnormal, const double* fcent,
+                 const double* fshift, const double* xc, const BCDev* bcs, FaceRec<T>* rec);
+
+template <typename T>
+void launch_moments(cudaStream_t s, int64_t Nc, int64_t M, const Gas& g, const T* f, const double* W,
+                    const double* ux, const double* uy, const double* uz, const double* w, double* q_out,
+                    double* Wf_out);
+
+template <typename T>
+void launch_gather_f(cudaStream_t s, int64_t Nc, int64_t M, int NR, int64_t nv, const T* f, const int64_t* sel,
+                     int64_t n, double* out);
+
+template <typename T>
+void launch_scatter_f(cudaStream_t s, int64_t Nc, int64_t M, int NR, int64_t nv, const double* in,
+                      const int64_t* old_of_new, T* f);
+
+void launch_residual_finalize(cudaStream_t s, int nw, int64_t Nc, const double* acc, double* res);
+
+// Arguments of the persistent velocity-block sweep (ugks_sweep.cu).
+template <typename T>
+struct SweepArgs {
+  Gas g;
+  int64_t Nc, M, nv;
+  const T* f_cur;        // f^n        [NR][M][Nc][BV]
+  T* f_next;             // f~ then f^{n+1}
+  const double* W_cur;   // [Nc][NWP]
+  double* W_next;
+  const CellPrim* cp;    // primitive record of W^n (with q^n)
+  CellPrim* cp_next;     // primitive record of W^{n+1} (written for tile cells)
+  double* q_next;        // [Nc][3] heat flux of f^{n+1}
+  const T* ux;           // [M*BV] velocity components and weights (padded)
+  const T* uy;
+  const T* uz;
+  const T* w;
+  const double* vol;
+  const T* eps2;                 // limiter constant (K_v |Omega|^(1/D))^3 per cell
+  const int64_t* cf_off;         // per cell incidence CSR
+  const CellFaceT<T>* cf;
+  const FaceGeom<T>* fg;
+  const FaceRec<T>* fr;
+  const BCDev* bcs;
+  const int64_t* tile_begin;     // [ntiles+1] cell ranges
+  const int64_t* gset_off;       // [ntiles+1]
+  const int64_t* gset;           // gradient-set cells per tile (tile cells first)
+  const int64_t* tf_off;         // [ntiles+1]
+  const TileFace* tf;            // tile faces
+  const int32_t* tcf;            // per cell incidence as local tile-face index << 1 | (sign < 0)
+  T* G;                          // per-tile scratch: gradients [gmax][NR][D][BV]
+  T* Phi;                        // per-tile scratch: micro fluxes [fmax][NR][BV]
+  double* Facc;                  // per-tile scratch: face accumulators [fmax][FACC_W]
+  int64_t G_stride, Phi_stride, Facc_stride;
+  double* res_acc;               // [NWP] sum of squared W increments
+  int* status;
+};
+
+template <typename T>
+cudaError_t launch_sweep(cudaStream_t s, const SweepArgs<T>& a, int ntiles, int threads);
+
+template <typename T>
+int sweep_occupancy(int D, int NR, int threads);
+
+}  // namespace ugks

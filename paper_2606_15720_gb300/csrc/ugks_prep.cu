@@ -1,0 +1,690 @@
+// Per-cell and per-face FP64 kernels of one UGKS step (Algorithm 5, the
+// stages before the velocity-block sweep), plus set-up and data-movement
+// kernels.  GB300 executes FP64 at a small fraction of its FP32 rate, so FP64
+// is confined to O(N_cells + N_faces) work here: primitive variables, the
+// limited least-squares gradient of W, and the interface coefficients whose
+// exp(-dt/tau) terms cancel at small dt/tau (Eq. 34-35).
+#include <cmath>
+#include <cstdint>
+
+#include "ugks_internal.cuh"
+#include "ugks_kernels.cuh"
+
+namespace ugks {
+
+namespace {
+
+// Small fixed-size vectors passed by value, so that with D a template
+// parameter every loop unrolls and all of them live in registers.
+struct Vec5 {
+  double v[NWP];
+};
+
+struct Prim {
+  double rho, U[3], lam;
+};
+
+// lambda = (K+3) rho / (4 (rho E - rho |U|^2 / 2)), R = 1/2 (Eq. 6, 10).
+template <int D>
+__device__ __forceinline__ Prim prim_of(const Vec5& W, int K, bool& ok) {
+  Prim p;
+  p.rho = W.v[0];
+  double u2 = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) p.U[d] = d < D ? W.v[1 + (d < D ? d : 0)] / W.v[0] : 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) u2 += p.U[d] * p.U[d];
+  const double ein = W.v[D + 1] - 0.5 * W.v[0] * u2;
+  p.lam = (K + 3) * W.v[0] / (4.0 * ein);
+  ok = (p.rho > 0.0) && (ein > 0.0) && isfinite(p.lam) && isfinite(u2);
+  return p;
+}
+
+template <int D>
+__device__ __forceinline__ Vec5 cons_of(const Prim& p, int K) {
+  Vec5 W;
+  double u2 = 0.0;
+#pragma unroll
+  for (int t = 0; t < NWP; ++t) W.v[t] = 0.0;
+  W.v[0] = p.rho;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    W.v[1 + d] = p.rho * p.U[d];
+    u2 += p.U[d] * p.U[d];
+  }
+  W.v[D + 1] = 0.5 * p.rho * u2 + (K + 3) * p.rho / (4.0 * p.lam);
+  return W;
+}
+
+template <int D>
+__device__ __forceinline__ Vec5 load5(const double* W) {
+  Vec5 r;
+#pragma unroll
+  for (int t = 0; t < NWP; ++t) r.v[t] = t < D + 2 ? W[t] : 0.0;
+  return r;
+}
+
+// tau = mu / p with mu = mu_ref T^omega and p = rho / (2 lambda).
+__device__ __forceinline__ double tau_of(const Prim& p, const Gas& g) {
+  const double T = 1.0 / p.lam;
+  return g.mu_ref * pow(T, g.omega) * 2.0 * p.lam / p.rho;
+}
+
+// Ghost conservative state of an artificial boundary (Sec. 2.1).
+template <int D>
+__device__ __forceinline__ Vec5 ghost_state(const BCDev& bc, const Vec5& Wi, int K) {
+  if (bc.type == 3) return Wi;
+  Prim p;
+  p.rho = bc.rho;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) p.U[d] = bc.u[d];
+  p.lam = 1.0 / bc.T;
+  return cons_of<D>(p, K);
+}
+
+// Venkatakrishnan / Barth-Jespersen limiter value for one face.
+__device__ __forceinline__ double limiter_fn(int kind, double d2, double dmax, double dmin, double eps2) {
+  if (kind == 0 || d2 == 0.0) return 1.0;
+  const double dp = d2 > 0.0 ? dmax : dmin;
+  if (kind == 2) return fmin(1.0, dp / d2);
+  const double num = dp * dp + eps2 + 2.0 * d2 * dp;
+  const double den = dp * dp + 2.0 * d2 * d2 + dp * d2 + eps2;
+  return den != 0.0 ? num / den : 1.0;
+}
+
+// Solves rho <psi psi^T> x = rhs for a Maxwellian with N = K + 3 degrees of
+// freedom, in closed form through the peculiar velocity: with a.psi written
+// as b0 + b.c + aE (c^2 + xi^2)/2, the mass, momentum and energy moments give
+//   b0 + aE N/(4 lam) = dr,  b = 2 lam (dm - U dr),
+//   b0 N/(4 lam) + aE N(N+2)/(16 lam^2) = dE - |U|^2 dr/2 - U.b/(2 lam).
+template <int D>
+__device__ __forceinline__ Vec5 maxwell_solve(const Prim& p, int K, const Vec5& rhs) {
+  const double N = K + 3.0, lam = p.lam;
+  const double dr = rhs.v[0] / p.rho, dE = rhs.v[D + 1] / p.rho;
+  double b[3] = {0.0, 0.0, 0.0}, u2 = 0.0, ub = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    b[d] = 2.0 * lam * (rhs.v[1 + d] / p.rho - p.U[d] * dr);
+    u2 += p.U[d] * p.U[d];
+    ub += p.U[d] * b[d];
+  }
+  const double R = dE - 0.5 * u2 * dr - ub / (2.0 * lam);
+  const double aE = (R - dr * N / (4.0 * lam)) * 8.0 * lam * lam / N;
+  const double b0 = dr - aE * N / (4.0 * lam);
+  Vec5 x;
+#pragma unroll
+  for (int t = 0; t < NWP; ++t) x.v[t] = 0.0;
+  double a0 = b0 - 0.5 * aE * u2;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double au = b[d] - aE * p.U[d];
+    x.v[1 + d] = au;
+    a0 -= au * p.U[d];
+  }
+  x.v[0] = a0;
+  x.v[D + 1] = aE;
+  return x;
+}
+
+// Directional derivative of the Euler flux F_dir(W) along dW; equal to the
+// moment rho <psi u_dir (a.psi)> of the slope a with rho <psi psi^T> a = dW.
+template <int D>
+__device__ __forceinline__ Vec5 euler_flux_derivative(const Prim& p, int K, int dir, const Vec5& W, const Vec5& dW) {
+  const double N = K + 3.0;
+  double u2 = 0.0, Udm = 0.0, dU[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    u2 += p.U[d] * p.U[d];
+    Udm += p.U[d] * dW.v[1 + d];
+    dU[d] = (dW.v[1 + d] - p.U[d] * dW.v[0]) / p.rho;
+  }
+  const double pres = p.rho / (2.0 * p.lam);
+  const double dp = (2.0 / N) * (dW.v[D + 1] - Udm + 0.5 * u2 * dW.v[0]);
+  double Udir = 0.0, dUdir = 0.0, mdir = 0.0, dmdir = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+    if (d == dir) {
+      Udir = p.U[d];
+      dUdir = dU[d];
+      mdir = W.v[1 + d];
+      dmdir = dW.v[1 + d];
+    }
+  Vec5 out;
+#pragma unroll
+  for (int t = 0; t < NWP; ++t) out.v[t] = 0.0;
+  out.v[0] = dmdir;
+#pragma unroll
+  for (int e = 0; e < D; ++e) out.v[1 + e] = dmdir * p.U[e] + mdir * dU[e] + (e == dir ? dp : 0.0);
+  out.v[D + 1] = dUdir * (W.v[D + 1] + pres) + Udir * (dW.v[D + 1] + dp);
+  return out;
+}
+
+// rho <psi> over the half space s (u.n) > 0 of a Maxwellian.
+template <int D>
+__device__ __forceinline__ Vec5 half_space_moments(const Prim& p, int K, const double* n, double s) {
+  const int Kxi = K + 3 - D;
+  double Un = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) Un += p.U[d] * n[d];
+  const double sl = sqrt(p.lam);
+  const double e = exp(-p.lam * Un * Un) / (2.0 * sqrt(M_PI * p.lam));
+  const double m0 = 0.5 * erfc(-s * sl * Un);
+  const double m1 = Un * m0 + s * e;
+  const double m2 = Un * m1 + m0 / (2.0 * p.lam);
+  double ut2 = 0.0;
+  Vec5 out;
+#pragma unroll
+  for (int t = 0; t < NWP; ++t) out.v[t] = 0.0;
+  out.v[0] = p.rho * m0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double ut = p.U[d] - Un * n[d];
+    ut2 += ut * ut;
+    out.v[1 + d] = p.rho * (m1 * n[d] + m0 * ut);
+  }
+  out.v[D + 1] = 0.5 * p.rho * (m2 + m0 * (ut2 + (D - 1 + Kxi) / (2.0 * p.lam)));
+  return out;
+}
+
+struct G5 {
+  double g[5];
+};
+
+// Integrals over [0, dt] of c1..c5 (Eq. 34-35).  Closed forms for x = dt/tau
+// >= 0.5; below, power series in x (evaluated by Horner), because the closed
+// forms cancel:
+//   G0 = dt sum_n (-x)^n/(n+1)!            G2 = dt x sum_j (-x)^j/(j+2)!
+//   G1 = dt^2 sum_m (-1)^(m+1)(m+1) x^m/(m+2)!
+//   G3 = dt^2 x sum_j>=0 (-1)^(j+1)(j+1) x^j/(j+3)!
+//   G4 = dt^2 x sum_j>=0 (-1)^j x^j/(j+3)!
+__device__ __forceinline__ G5 time_integrals(double dt, double tau) {
+  G5 r;
+  const double x = dt / tau;
+  if (x >= 0.5) {
+    const double em = -expm1(-x);
+    const double E = exp(-x);
+    r.g[0] = tau * em;
+    r.g[1] = tau * (dt * E - tau * em);
+    r.g[2] = dt - tau * em;
+    r.g[3] = tau * (2.0 * tau * em - dt * (1.0 + E));
+    r.g[4] = 0.5 * dt * dt - tau * dt + tau * tau * em;
+    return r;
+  }
+  constexpr int NT = 24;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+  // 1/(n+1)!, 1/(n+2)!, 1/(n+3)! for n = NT-1 down to 0, built from 1/(NT+2)!
+  double f1 = 1.0, f2 = 1.0, f3 = 1.0;
+#pragma unroll
+  for (int i = 2; i <= NT; ++i) f1 /= i;        // 1/NT!
+  f2 = f1 / (NT + 1);                            // 1/(NT+1)!
+  f3 = f2 / (NT + 2);                            // 1/(NT+2)!
+#pragma unroll
+  for (int n = NT - 1; n >= 0; --n) {
+    const double sg = (n & 1) ? -1.0 : 1.0;
+    s0 = s0 * x + sg * f1;
+    s2 = s2 * x + sg * f2;
+    s1 = s1 * x - sg * (n + 1) * f2;
+    s3 = s3 * x - sg * (n + 1) * f3;
+    s4 = s4 * x + sg * f3;
+    f3 = f2;
+    f2 = f1;
+    f1 = f1 * (n + 1 > 1 ? n + 1 : 1);
+  }
+  r.g[0] = dt * s0;
+  r.g[1] = dt * dt * s1;
+  r.g[2] = dt * x * s2;
+  r.g[3] = dt * dt * x * s3;
+  r.g[4] = dt * dt * x * s4;
+  return r;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Time step: one warp per cell, lanes over velocities.  The positive double
+// dt_i is min-reduced through its bit pattern (positive doubles order like
+// their unsigned 64-bit images).
+// ---------------------------------------------------------------------------
+__global__ void k_time_step(int64_t Nc, int D, const int64_t* cf_off, const CellFace* cf, const double* fnormal,
+                            const double* vol, const double* u, const double* w, int64_t nv,
+                            unsigned long long* out_bits) {
+  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= Nc) return;
+  int64_t i = warp;
+  double worst = 0.0;
+  for (int64_t k = lane; k < nv; k += 32) {
+    if (w[k] == 0.0) continue;
+    double s = 0.0;
+    for (int64_t e = cf_off[i]; e < cf_off[i + 1]; ++e) {
+      const CellFace& c = cf[e];
+      double un = 0.0;
+      for (int d = 0; d < D; ++d) un += u[k * D + d] * fnormal[c.face * 3 + d];
+      un *= c.sign;
+      if (un > 0.0) s += c.area * un;
+    }
+    worst = fmax(worst, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  if (lane == 0 && worst > 0.0) {
+    double v = vol[i] / worst;
+    atomicMin(out_bits, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Initial distribution: discrete reduced Maxwellians of W (h = H, b = K_xi/(2 lam) H);
+// padded velocities (k >= nv) hold zero.
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__global__ void k_init_f(int64_t Nc, int64_t M, int64_t nv, Gas g, const double* W, const double* ux,
+                         const double* uy, const double* uz, T* f) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= M * Nc * BV) return;
+  const int lane = int(idx & 31);
+  const int64_t row = idx >> 5;
+  const int64_t c = row % Nc, m = row / Nc;
+  const int64_t k = m * BV + lane;
+  double H = 0.0, kap = 0.0;
+  if (k < nv) {
+    bool ok;
+    const Prim p = prim_of<D>(load5<D>(W + c * NWP), g.K, ok);
+    const double uu[3] = {ux[k], uy[k], uz[k]};
+    double c2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) c2 += (uu[d] - p.U[d]) * (uu[d] - p.U[d]);
+    H = p.rho * pow(p.lam / M_PI, 0.5 * D) * exp(-p.lam * c2);
+    kap = g.Kxi / (2.0 * p.lam);
+  }
+  const size_t plane = size_t(M) * Nc * BV;
+  f[size_t(m) * Nc * BV + size_t(c) * BV + lane] = T(H);
+  if (g.NR == 2) f[plane + size_t(m) * Nc * BV + size_t(c) * BV + lane] = T(kap * H);
+}
+
+// ---------------------------------------------------------------------------
+// Cell stage (Algorithm 5: primitive variables, relaxation time, and the
+// limited least-squares gradient of W), one thread per cell, FP64.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_cell(int64_t Nc, Gas g, const double* W, const double* q, const int64_t* cf_off,
+                       const CellFace* cf, const double* vol, const BCDev* bcs, CellPrim* cp, double* gW,
+                       int* status) {
+  constexpr int nw = D + 2;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= Nc) return;
+  const Vec5 Wi = load5<D>(W + i * NWP);
+  bool ok;
+  Prim p = prim_of<D>(Wi, g.K, ok);
+  if (!ok) {
+    atomicOr(status, 1);
+    p.rho = 1.0;
+    p.lam = 1.0;
+  }
+  CellPrim c;
+  c.rho = p.rho;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) c.U[d] = p.U[d];
+  c.lam = p.lam;
+  c.tau = tau_of(p, g);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) c.q[d] = (d < D && g.shakhov) ? q[i * 3 + d] : 0.0;
+  c.pad = 0.0;
+  cp[i] = c;
+
+  double grad[nw][D], wmax[nw], wmin[nw];
+#pragma unroll
+  for (int t = 0; t < nw; ++t) {
+    wmax[t] = wmin[t] = Wi.v[t];
+#pragma unroll
+    for (int d = 0; d < D; ++d) grad[t][d] = 0.0;
+  }
+  const int64_t e0 = cf_off[i], e1 = cf_off[i + 1];
+  for (int64_t e = e0; e < e1; ++e) {
+    const CellFace& s = cf[e];
+    if (s.bc_type == 1) continue;  // walls are not in the least-squares stencil
+    const Vec5 Wo = s.other >= 0 ? load5<D>(W + s.other * NWP) : ghost_state<D>(bcs[-s.other - 1], Wi, g.K);
+#pragma unroll
+    for (int t = 0; t < nw; ++t) {
+      const double dw = Wo.v[t] - Wi.v[t];
+#pragma unroll
+      for (int d = 0; d < D; ++d) grad[t][d] += s.w[d] * dw;
+      wmax[t] = fmax(wmax[t], Wo.v[t]);
+      wmin[t] = fmin(wmin[t], Wo.v[t]);
+    }
+  }
+  const double h = pow(vol[i], 1.0 / D), eps2 = pow(g.venkat_K * h, 3.0);
+  double phi[nw];
+#pragma unroll
+  for (int t = 0; t < nw; ++t) phi[t] = 1.0;
+  for (int64_t e = e0; e < e1; ++e) {
+    const CellFace& s = cf[e];
+#pragma unroll
+    for (int t = 0; t < nw; ++t) {
+      double d2 = 0.0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) d2 += grad[t][d] * s.r[d];
+      phi[t] = fmin(phi[t], limiter_fn(g.limiter, d2, wmax[t] - Wi.v[t], wmin[t] - Wi.v[t], eps2));
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < nw; ++t)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gW[(i * NWP + t) * 3 + d] = d < D ? fmax(phi[t], 0.0) * grad[t][d < D ? d : 0] : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Face stage (Algorithm 5: interface equilibrium, slopes, time integrals),
+// one thread per face, FP64 arithmetic, record stored in the sweep precision.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ Vec5 slope_column(const double* gW, int64_t c, int d) {
+  Vec5 r;
+#pragma unroll
+  for (int t = 0; t < NWP; ++t) r.v[t] = t < D + 2 ? gW[(c * NWP + t) * 3 + d] : 0.0;
+  return r;
+}
+
+template <int D, typename T>
+__global__ void k_face(int64_t Nf, Gas g, const double* W, const double* gW, const double* q,
+                       const int64_t* fown, const int64_t* fnei, const double* fnormal, const double* fcent,
+                       const double* fshift, const double* xc, const BCDev* bcs, FaceRec<T>* rec) {
+  constexpr int nw = D + 2;
+  const int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (f >= Nf) return;
+  const int K = g.K;
+  const int64_t o = fown[f], j = fnei[f];
+  FaceRec<T> R;
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    R.G[t] = T(0);
+    R.A[t] = T(0);
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R.U[d] = T(0);
+    R.q[d] = T(0);
+#pragma unroll
+    for (int t = 0; t < 5; ++t) R.a[d][t] = T(0);
+  }
+  R.pad[0] = R.pad[1] = T(0);
+  R.sq = T(0);
+  R.xi4 = T(0);
+  if (j < 0 && bcs[-j - 1].type == 1) {
+    // diffuse wall: unit-density wall Maxwellian (Eq. 37)
+    const BCDev& bc = bcs[-j - 1];
+    const double lam = 1.0 / bc.T;
+    R.rho_pref = T(pow(lam / M_PI, 0.5 * D));
+    R.lam = T(lam);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) R.U[d] = T(bc.u[d]);
+    R.kappa = T(g.Kxi / (2.0 * lam));
+    rec[f] = R;
+    return;
+  }
+  double n[3], rl[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    n[d] = fnormal[f * 3 + d];
+    rl[d] = fcent[f * 3 + d] - xc[o * 3 + d];
+  }
+  const Vec5 Wo = load5<D>(W + o * NWP);
+  bool ok;
+  // reconstructed conservative states on both sides (Eq. 31 for W, reading R8)
+  Vec5 Wl = Wo;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const Vec5 s = slope_column<D>(gW, o, d);
+#pragma unroll
+    for (int t = 0; t < nw; ++t) Wl.v[t] += s.v[t] * rl[d];
+  }
+  Prim pl = prim_of<D>(Wl, K, ok);
+  if (!ok) {
+    Wl = Wo;
+    pl = prim_of<D>(Wl, K, ok);
+  }
+  Vec5 Wr;
+  Vec5 dW0[D];
+  double qr[3] = {0.0, 0.0, 0.0};
+  if (j >= 0) {
+    const Vec5 Wj = load5<D>(W + j * NWP);
+    Wr = Wj;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const double rr = fcent[f * 3 + d] - fshift[f * 3 + d] - xc[j * 3 + d];
+      const Vec5 s = slope_column<D>(gW, j, d);
+#pragma unroll
+      for (int t = 0; t < nw; ++t) Wr.v[t] += s.v[t] * rr;
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const Vec5 so = slope_column<D>(gW, o, d), sj = slope_column<D>(gW, j, d);
+#pragma unroll
+      for (int t = 0; t < NWP; ++t) dW0[d].v[t] = 0.5 * (so.v[t] + sj.v[t]);
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) qr[d] = q[j * 3 + d];
+  } else {
+    Wr = ghost_state<D>(bcs[-j - 1], Wo, K);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const Vec5 so = slope_column<D>(gW, o, d);
+#pragma unroll
+      for (int t = 0; t < NWP; ++t) dW0[d].v[t] = 0.5 * so.v[t];
+    }
+  }
+  Prim pr = prim_of<D>(Wr, K, ok);
+  if (!ok && j >= 0) {
+    Wr = load5<D>(W + j * NWP);
+    pr = prim_of<D>(Wr, K, ok);
+  }
+  // interface state from the two half-range moments (reading R6)
+  const Vec5 hl = half_space_moments<D>(pl, K, n, +1.0);
+  const Vec5 hr = half_space_moments<D>(pr, K, n, -1.0);
+  Vec5 W0;
+#pragma unroll
+  for (int t = 0; t < NWP; ++t) W0.v[t] = hl.v[t] + hr.v[t];
+  const Prim p0 = prim_of<D>(W0, K, ok);
+  // spatial slopes a_d and the time slope A from compatibility (Eq. 7, 32)
+  Vec5 rhsA;
+#pragma unroll
+  for (int t = 0; t < NWP; ++t) rhsA.v[t] = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const Vec5 a = maxwell_solve<D>(p0, K, dW0[d]);
+#pragma unroll
+    for (int t = 0; t < nw; ++t) R.a[d][t] = T(a.v[t]);
+    const Vec5 dF = euler_flux_derivative<D>(p0, K, d, W0, dW0[d]);
+#pragma unroll
+    for (int t = 0; t < NWP; ++t) rhsA.v[t] -= dF.v[t];
+  }
+  const Vec5 A = maxwell_solve<D>(p0, K, rhsA);
+#pragma unroll
+  for (int t = 0; t < nw; ++t) R.A[t] = T(A.v[t]);
+  double tau0 = tau_of(p0, g);
+  if (g.shock_fix) {
+    const double PL = pl.rho / (2.0 * pl.lam), PR = pr.rho / (2.0 * pr.lam);
+    tau0 += g.dt * fabs(PL - PR) / (PL + PR);
+  }
+  const G5 G = time_integrals(g.dt, tau0);
+#pragma unroll
+  for (int t = 0; t < 5; ++t) R.G[t] = T(G.g[t]);
+  R.rho_pref = T(p0.rho * pow(p0.lam / M_PI, 0.5 * D));
+  R.lam = T(p0.lam);
+#pragma unroll
+  for (int d = 0; d < D; ++d) R.U[d] = T(p0.U[d]);
+  if (g.shakhov) {
+    R.sq = T(4.0 * (1.0 - g.Pr) * p0.lam * p0.lam / (5.0 * p0.rho));
+#pragma unroll
+    for (int d = 0; d < D; ++d) R.q[d] = T(0.5 * (q[o * 3 + d] + qr[d]));
+  }
+  R.kappa = T(g.Kxi / (2.0 * p0.lam));
+  R.xi4 = T(g.Kxi * (g.Kxi + 2.0) / (4.0 * p0.lam * p0.lam));
+  rec[f] = R;
+}
+
+// ---------------------------------------------------------------------------
+// Moments of the stored distribution: heat flux (Eq. 13) about U of W, and
+// the discrete conservative moments (Eq. 10, 21).  One warp per cell.
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__global__ void k_moments(int64_t Nc, int64_t M, Gas g, const T* f, const double* W, const double* ux,
+                          const double* uy, const double* uz, const double* w, double* q_out, double* Wf_out) {
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= Nc) return;
+  bool ok;
+  const Prim p = prim_of<D>(load5<D>(W + i * NWP), g.K, ok);
+  double qa[3] = {0.0, 0.0, 0.0}, ma[3] = {0.0, 0.0, 0.0}, m0 = 0.0, mE = 0.0;
+  const size_t plane = size_t(M) * Nc * BV;
+  for (int64_t m = 0; m < M; ++m) {
+    const int64_t k = m * BV + lane;
+    const double h = double(f[size_t(m) * Nc * BV + size_t(i) * BV + lane]);
+    const double b = g.NR == 2 ? double(f[plane + size_t(m) * Nc * BV + size_t(i) * BV + lane]) : 0.0;
+    const double uu[3] = {ux[k], uy[k], uz[k]}, wk = w[k];
+    double c2 = 0.0, u2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      c2 += (uu[d] - p.U[d]) * (uu[d] - p.U[d]);
+      u2 += uu[d] * uu[d];
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      qa[d] += 0.5 * wk * (uu[d] - p.U[d]) * (c2 * h + b);
+      ma[d] += wk * uu[d] * h;
+    }
+    m0 += wk * h;
+    mE += 0.5 * wk * (u2 * h + b);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m0 += __shfl_xor_sync(0xffffffffu, m0, o);
+    mE += __shfl_xor_sync(0xffffffffu, mE, o);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      qa[d] += __shfl_xor_sync(0xffffffffu, qa[d], o);
+      ma[d] += __shfl_xor_sync(0xffffffffu, ma[d], o);
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) q_out[i * 3 + d] = d < D ? qa[d] : 0.0;
+    if (Wf_out) {
+      Wf_out[i * NWP + 0] = m0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) Wf_out[i * NWP + 1 + d] = ma[d];
+      Wf_out[i * NWP + D + 1] = mE;
+    }
+  }
+}
+
+// Gather of selected rows as FP64: out[n][NR][nv] for cells sel[] (renumbered).
+template <typename T>
+__global__ void k_gather_f(int64_t Nc, int64_t M, int NR, int64_t nv, const T* f, const int64_t* sel, int64_t n,
+                           double* out) {
+  int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= n * NR * nv) return;
+  int64_t k = idx % nv, r = (idx / nv) % NR, s = idx / (nv * NR);
+  int64_t c = sel[s], m = k / BV, lane = k % BV;
+  out[idx] = double(f[(size_t(r) * M + m) * Nc * BV + size_t(c) * BV + lane]);
+}
+
+// Scatter of a full FP64 state in[NR][Nc_orig][nv] (original order) into f.
+template <typename T>
+__global__ void k_scatter_f(int64_t Nc, int64_t M, int NR, int64_t nv, const double* in, const int64_t* old_of_new,
+                            T* f) {
+  int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(NR) * M * Nc * BV) return;
+  int lane = int(idx & 31);
+  int64_t row = idx >> 5;
+  int64_t c = row % Nc, m = (row / Nc) % M, r = row / (Nc * M);
+  int64_t k = m * BV + lane;
+  double v = k < nv ? in[(size_t(r) * Nc + old_of_new[c]) * nv + k] : 0.0;
+  f[idx] = T(v);
+}
+
+__global__ void k_residual_finalize(int nw, int64_t Nc, const double* acc, double* res) {
+  int t = threadIdx.x;
+  if (t < nw) res[t] = sqrt(acc[t] / double(Nc));
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+static inline unsigned blocks_for(int64_t n, int threads) { return unsigned((n + threads - 1) / threads); }
+
+void launch_time_step(cudaStream_t s, int64_t Nc, int D, const int64_t* cf_off, const CellFace* cf,
+                      const double* fnormal, const double* vol, const double* u, const double* w, int64_t nv,
+                      unsigned long long* out_bits) {
+  k_time_step<<<blocks_for(Nc * 32, 256), 256, 0, s>>>(Nc, D, cf_off, cf, fnormal, vol, u, w, nv, out_bits);
+}
+
+template <typename T>
+void launch_init_f(cudaStream_t s, int64_t Nc, int64_t M, int64_t nv, const Gas& g, const double* W,
+                   const double* ux, const double* uy, const double* uz, T* f) {
+  const unsigned nb = blocks_for(M * Nc * BV, 256);
+  if (g.D == 1) k_init_f<1, T><<<nb, 256, 0, s>>>(Nc, M, nv, g, W, ux, uy, uz, f);
+  if (g.D == 2) k_init_f<2, T><<<nb, 256, 0, s>>>(Nc, M, nv, g, W, ux, uy, uz, f);
+  if (g.D == 3) k_init_f<3, T><<<nb, 256, 0, s>>>(Nc, M, nv, g, W, ux, uy, uz, f);
+}
+
+void launch_cell(cudaStream_t s, int64_t Nc, const Gas& g, const double* W, const double* q, const int64_t* cf_off,
+                 const CellFace* cf, const double* vol, const BCDev* bcs, CellPrim* cp, double* gW, int* status) {
+  const unsigned nb = blocks_for(Nc, 128);
+  if (g.D == 1) k_cell<1><<<nb, 128, 0, s>>>(Nc, g, W, q, cf_off, cf, vol, bcs, cp, gW, status);
+  if (g.D == 2) k_cell<2><<<nb, 128, 0, s>>>(Nc, g, W, q, cf_off, cf, vol, bcs, cp, gW, status);
+  if (g.D == 3) k_cell<3><<<nb, 128, 0, s>>>(Nc, g, W, q, cf_off, cf, vol, bcs, cp, gW, status);
+}
+
+template <typename T>
+void launch_face(cudaStream_t s, int64_t Nf, const Gas& g, const double* W, const double* gW, const double* q,
+                 const int64_t* fown, const int64_t* fnei, const double* fnormal, const double* fcent,
+                 const double* fshift, const double* xc, const BCDev* bcs, FaceRec<T>* rec) {
+  const unsigned nb = blocks_for(Nf, 128);
+  if (g.D == 1) k_face<1, T><<<nb, 128, 0, s>>>(Nf, g, W, gW, q, fown, fnei, fnormal, fcent, fshift, xc, bcs, rec);
+  if (g.D == 2) k_face<2, T><<<nb, 128, 0, s>>>(Nf, g, W, gW, q, fown, fnei, fnormal, fcent, fshift, xc, bcs, rec);
+  if (g.D == 3) k_face<3, T><<<nb, 128, 0, s>>>(Nf, g, W, gW, q, fown, fnei, fnormal, fcent, fshift, xc, bcs, rec);
+}
+
+template <typename T>
+void launch_moments(cudaStream_t s, int64_t Nc, int64_t M, const Gas& g, const T* f, const double* W,
+                    const double* ux, const double* uy, const double* uz, const double* w, double* q_out,
+                    double* Wf_out) {
+  const unsigned nb = blocks_for(Nc * 32, 256);
+  if (g.D == 1) k_moments<1, T><<<nb, 256, 0, s>>>(Nc, M, g, f, W, ux, uy, uz, w, q_out, Wf_out);
+  if (g.D == 2) k_moments<2, T><<<nb, 256, 0, s>>>(Nc, M, g, f, W, ux, uy, uz, w, q_out, Wf_out);
+  if (g.D == 3) k_moments<3, T><<<nb, 256, 0, s>>>(Nc, M, g, f, W, ux, uy, uz, w, q_out, Wf_out);
+}
+
+template <typename T>
+void launch_gather_f(cudaStream_t s, int64_t Nc, int64_t M, int NR, int64_t nv, const T* f, const int64_t* sel,
+                     int64_t n, double* out) {
+  if (n * NR * nv == 0) return;
+  k_gather_f<T><<<blocks_for(n * NR * nv, 256), 256, 0, s>>>(Nc, M, NR, nv, f, sel, n, out);
+}
+
+template <typename T>
+void launch_scatter_f(cudaStream_t s, int64_t Nc, int64_t M, int NR, int64_t nv, const double* in,
+                      const int64_t* old_of_new, T* f) {
+  k_scatter_f<T><<<blocks_for(int64_t(NR) * M * Nc * BV, 256), 256, 0, s>>>(Nc, M, NR, nv, in, old_of_new, f);
+}
+
+void launch_residual_finalize(cudaStream_t s, int nw, int64_t Nc, const double* acc, double* res) {
+  k_residual_finalize<<<1, 32, 0, s>>>(nw, Nc, acc, res);
+}
+
+#define UGKS_INSTANTIATE(T)                                                                                      \
+  template void launch_init_f<T>(cudaStream_t, int64_t, int64_t, int64_t, const Gas&, const double*,             \
+                                 const double*, const double*, const double*, T*);                              \
+  template void launch_face<T>(cudaStream_t, int64_t, const Gas&, const double*, const double*, const double*,   \
+                               const int64_t*, const int64_t*, const double*, const double*, const double*,      \
+                               const double*, const BCDev*, FaceRec<T>*);                                        \
+  template void launch_moments<T>(cudaStream_t, int64_t, int64_t, const Gas&, const T*, const double*,           \
+                                  const double*, const double*, const double*, const double*, double*, double*); \
+  template void launch_gather_f<T>(cudaStream_t, int64_t, int64_t, int, int64_t, const T*, const int64_t*,       \
+                                   int64_t, double*);                                                            \
+  template void launch_scatter_f<T>(cudaStream_t, int64_t, int64_t, int, int64_t, const double*, const int64_t*, \
+                                    T*);
+UGKS_INSTANTIATE(float)
+UGKS_INSTANTIATE(double)
+
+}  // namespace ugks

@@ -313,6 +313,29 @@ def _assemble_simplex_mesh(points, simplices, keep, dim, classify, bcs, name):
                 face_shift=np.zeros_like(fc), bc=bcs, name=name)
 
 
+def _size_search(build, target: int, dim: int, scale0: float = 1.0, tol: float = 0.05, max_iter: int = 12):
+    """Finds the spacing scale whose mesh has target +- tol cells, using the
+    power law cells ~ scale^-dim (secant steps in log-log space from scale0)."""
+    scale = scale0
+    P, simp, keep = build(scale)
+    n = int(keep.sum())
+    expo = float(dim)
+    prev = None
+    for _ in range(max_iter):
+        if abs(n - target) <= tol * target:
+            break
+        if prev is not None and prev[1] != n and prev[0] != scale:
+            e = -math.log(n / prev[1]) / math.log(scale / prev[0])
+            if 0.5 * dim <= e <= 2.0 * dim:
+                expo = e
+        new_scale = scale * (n / target) ** (1.0 / expo)
+        prev = (scale, n)
+        scale = new_scale
+        P, simp, keep = build(scale)
+        n = int(keep.sum())
+    return P, simp, keep
+
+
 def sphere_tet_mesh(target_cells: int = 100_000, seed: int = 2, mach: float = 5.0,
                     T_wall: Optional[float] = None, gamma: float = 5.0 / 3.0) -> Mesh:
     """Tetrahedral mesh around a unit sphere in the box [-4,8] x [-5,5]^2.
@@ -367,20 +390,8 @@ def sphere_tet_mesh(target_cells: int = 100_000, seed: int = 2, mach: float = 5.
         keep &= vol > 1e-14
         return P, simp, keep
 
-    lo_s, hi_s = 0.5, 4.0
-    best = None
-    for _ in range(30):
-        mid = math.sqrt(lo_s * hi_s)
-        P, simp, keep = build(mid)
-        n = int(keep.sum())
-        best = (P, simp, keep)
-        if abs(n - target_cells) <= 0.05 * target_cells:
-            break
-        if n > target_cells:
-            lo_s = mid
-        else:
-            hi_s = mid
-    P, simp, keep = best
+    P, simp, keep = _size_search(build, target_cells, dim=3,
+                                 scale0=1.6133 * (103387.0 / target_cells) ** (1.0 / 3.0))
 
     def classify(fc):
         out = np.full(fc.shape[0], 1, dtype=np.int64)
@@ -438,20 +449,7 @@ def cylinder_tri_mesh(target_cells: int = 10_000, seed: int = 4, mach: float = 3
         keep &= vol > 1e-14
         return P, simp, keep
 
-    lo_s, hi_s = 0.2, 20.0
-    best = None
-    for _ in range(40):
-        mid = math.sqrt(lo_s * hi_s)
-        P, simp, keep = build(mid)
-        n = int(keep.sum())
-        best = (P, simp, keep)
-        if abs(n - target_cells) <= 0.05 * target_cells:
-            break
-        if n > target_cells:
-            lo_s = mid
-        else:
-            hi_s = mid
-    P, simp, keep = best
+    P, simp, keep = _size_search(build, target_cells, dim=2)
 
     def classify(fc):
         out = np.full(fc.shape[0], 1, dtype=np.int64)

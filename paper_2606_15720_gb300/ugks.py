@@ -1,0 +1,259 @@
+"""Python binding of the C ABI in include/ugks.h (argument marshalling only).
+
+Every step of the UGKS path runs in the CUDA library libugks.so built by
+``paper_2606_15720_gb300.build``; this module only converts numpy arrays and
+dataclasses into the C structs and calls the entry points of the same names.
+There is no fallback: if the library cannot be loaded, or a call fails, an
+exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+from .inputs import LIMITERS, MODELS, Gas, Mesh, VelocityGrid
+
+STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+STATUS = {0: "UGKS_OK", 1: "UGKS_ERR_INVALID_ARGUMENT", 2: "UGKS_ERR_MESH", 3: "UGKS_ERR_VGRID",
+          4: "UGKS_ERR_OUT_OF_MEMORY", 5: "UGKS_ERR_CUDA", 6: "UGKS_ERR_NONFINITE", 7: "UGKS_ERR_TIMEOUT",
+          8: "UGKS_ERR_UNSUPPORTED"}
+
+_lib = None
+
+
+class UGKSError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class ugks_bc(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("rho", ctypes.c_double), ("u", ctypes.c_double * 3),
+                ("T", ctypes.c_double)]
+
+
+class ugks_mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n_cells", ctypes.c_int64), ("n_faces", ctypes.c_int64),
+                ("cell_volume", ctypes.c_void_p), ("cell_centroid", ctypes.c_void_p),
+                ("face_owner", ctypes.c_void_p), ("face_neighbor", ctypes.c_void_p),
+                ("face_area", ctypes.c_void_p), ("face_normal", ctypes.c_void_p),
+                ("face_centroid", ctypes.c_void_p), ("face_shift", ctypes.c_void_p),
+                ("n_bc", ctypes.c_int32), ("bc", ctypes.c_void_p)]
+
+
+class ugks_vgrid(ctypes.Structure):
+    _fields_ = [("n_v", ctypes.c_int64), ("u", ctypes.c_void_p), ("weight", ctypes.c_void_p)]
+
+
+class ugks_params(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("K", ctypes.c_int32), ("Pr", ctypes.c_double),
+                ("omega", ctypes.c_double), ("mu_ref", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("dt_override", ctypes.c_double), ("limiter", ctypes.c_int32), ("venkat_K", ctypes.c_double),
+                ("shock_tau_fix", ctypes.c_int32), ("storage", ctypes.c_int32), ("tile_cells", ctypes.c_int32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libugks.so (building it first if it is missing and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB) and build_if_missing:
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "ugks_create": [P, P, P, P, P, P],
+        "ugks_step": [P, I32],
+        "ugks_moments": [P, P, P],
+        "ugks_residual": [P, P],
+        "ugks_dt": [P, P],
+        "ugks_sizes": [P, P, P],
+        "ugks_get_f": [P, P, I64, P],
+        "ugks_get_state": [P, P, P, P],
+        "ugks_set_state": [P, P, P, I64],
+        "ugks_stats_enable": [P, I32],
+        "ugks_stats": [P, I32, P, P, P, P],
+        "ugks_solve": [P, P, P, P, I32, P, P],
+        "ugks_destroy": [P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.ugks_last_error.argtypes = [P]
+    lib.ugks_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data
+
+
+class _MeshArgs:
+    """Owns contiguous copies of the mesh / grid arrays while a call runs."""
+
+    def __init__(self, mesh: Mesh, grid: VelocityGrid):
+        f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
+        i64 = lambda a: np.ascontiguousarray(a, dtype=np.int64)  # noqa: E731
+        self.arrays = [f64(mesh.cell_volume), f64(mesh.cell_centroid), i64(mesh.face_owner),
+                       i64(mesh.face_neighbor), f64(mesh.face_area), f64(mesh.face_normal),
+                       f64(mesh.face_centroid), f64(mesh.face_shift)]
+        nbc = max(1, len(mesh.bc))
+        self.bcs = (ugks_bc * nbc)()
+        for i, b in enumerate(mesh.bc):
+            self.bcs[i].type = int(b.type)
+            self.bcs[i].rho = float(b.rho)
+            for d in range(3):
+                self.bcs[i].u[d] = float(b.u[d])
+            self.bcs[i].T = float(b.T)
+        a = self.arrays
+        self.mesh = ugks_mesh(mesh.dim, mesh.n_cells, mesh.n_faces, *[_ptr(x) for x in a], len(mesh.bc),
+                              ctypes.addressof(self.bcs))
+        self.u = f64(grid.u)
+        self.w = f64(grid.weight)
+        self.grid = ugks_vgrid(grid.n_v, _ptr(self.u), _ptr(self.w))
+
+
+def make_params(gas: Gas, storage: str = "f32", tile_cells: int = 0) -> ugks_params:
+    return ugks_params(MODELS[gas.model], int(gas.K), float(gas.Pr), float(gas.omega), float(gas.mu_ref),
+                       float(gas.cfl), float(gas.dt), LIMITERS[gas.limiter], float(gas.venkat_K),
+                       int(bool(gas.shock_tau_fix)), STORAGE[storage], int(tile_cells))
+
+
+def _check(lib, status: int, ctx=None):
+    if status != 0:
+        msg = lib.ugks_last_error(ctx).decode(errors="replace")
+        raise UGKSError(status, msg)
+
+
+def current_stream_handle() -> Optional[int]:
+    """cudaStream_t of torch's current stream (torch supplies streams), or None."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover - torch missing
+        return None
+    return None
+
+
+class Solver:
+    """One ugks_ctx: ugks_create / ugks_step / ugks_moments / ugks_residual."""
+
+    def __init__(self, mesh: Mesh, grid: VelocityGrid, gas: Gas, W_init: Optional[np.ndarray] = None,
+                 storage: str = "f32", tile_cells: int = 0, stream: Optional[int] = None):
+        self._lib = load()
+        self.mesh, self.grid, self.gas = mesh, grid, gas
+        self.dim = mesh.dim
+        args = _MeshArgs(mesh, grid)
+        prm = make_params(gas, storage, tile_cells)
+        W = None if W_init is None else np.ascontiguousarray(W_init, dtype=np.float64)
+        if W is not None and W.shape != (mesh.n_cells, mesh.dim + 2):
+            raise ValueError("W_init must be [n_cells, dim+2]")
+        if stream is None:
+            stream = current_stream_handle()
+        ctx = ctypes.c_void_p()
+        st = self._lib.ugks_create(ctypes.byref(args.mesh), ctypes.byref(args.grid), ctypes.byref(prm), _ptr(W),
+                                   stream, ctypes.byref(ctx))
+        _check(self._lib, st)
+        self._ctx = ctx
+        nr = ctypes.c_int32()
+        nvp = ctypes.c_int64()
+        self._lib.ugks_sizes(self._ctx, ctypes.byref(nr), ctypes.byref(nvp))
+        self.n_reduced = nr.value
+        self.n_v_padded = nvp.value
+
+    def _c(self, st):
+        _check(self._lib, st, self._ctx)
+
+    def step(self, n: int = 1) -> None:
+        self._c(self._lib.ugks_step(self._ctx, int(n)))
+
+    def moments(self, with_q: bool = False):
+        W = np.zeros((self.mesh.n_cells, self.dim + 2))
+        q = np.zeros((self.mesh.n_cells, self.dim)) if with_q else None
+        self._c(self._lib.ugks_moments(self._ctx, _ptr(W), _ptr(q)))
+        return (W, q) if with_q else W
+
+    def residual(self) -> np.ndarray:
+        r = np.zeros(self.dim + 2)
+        self._c(self._lib.ugks_residual(self._ctx, _ptr(r)))
+        return r
+
+    @property
+    def dt(self) -> float:
+        v = ctypes.c_double()
+        self._c(self._lib.ugks_dt(self._ctx, ctypes.byref(v)))
+        return v.value
+
+    def get_f(self, cells: Sequence[int]) -> np.ndarray:
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.zeros((cells.size, self.n_reduced, self.grid.n_v))
+        self._c(self._lib.ugks_get_f(self._ctx, _ptr(cells), cells.size, _ptr(out)))
+        return out
+
+    def get_state(self):
+        W = np.zeros((self.mesh.n_cells, self.dim + 2))
+        f = np.zeros((self.n_reduced, self.mesh.n_cells, self.grid.n_v))
+        step = ctypes.c_int64()
+        self._c(self._lib.ugks_get_state(self._ctx, _ptr(W), _ptr(f), ctypes.byref(step)))
+        return W, f, step.value
+
+    def set_state(self, W: np.ndarray, f: np.ndarray, step: int = 0) -> None:
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (self.n_reduced, self.mesh.n_cells, self.grid.n_v)
+        self._c(self._lib.ugks_set_state(self._ctx, _ptr(W), _ptr(f), int(step)))
+
+    def stats_enable(self, on: bool = True) -> None:
+        self._c(self._lib.ugks_stats_enable(self._ctx, int(bool(on))))
+
+    def stats(self) -> dict:
+        cap = 8
+        names = (ctypes.c_char_p * cap)()
+        ms = np.zeros(cap)
+        cnt = np.zeros(cap, dtype=np.int64)
+        n = ctypes.c_int32()
+        self._c(self._lib.ugks_stats(self._ctx, cap, ctypes.addressof(names), _ptr(ms), _ptr(cnt), ctypes.byref(n)))
+        return {names[i].decode(): (float(ms[i]), int(cnt[i])) for i in range(n.value)}
+
+    def close(self) -> None:
+        if getattr(self, "_ctx", None):
+            self._lib.ugks_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def solve(mesh: Mesh, grid: VelocityGrid, gas: Gas, W_init: np.ndarray, n_steps: int, storage: str = "f32",
+          tile_cells: int = 0):
+    """ugks_solve: one call with host buffers (create, n steps, W and residual, destroy)."""
+    lib = load()
+    args = _MeshArgs(mesh, grid)
+    prm = make_params(gas, storage, tile_cells)
+    W = np.ascontiguousarray(W_init, dtype=np.float64)
+    Wout = np.zeros_like(W)
+    res = np.zeros(mesh.dim + 2)
+    st = lib.ugks_solve(ctypes.byref(args.mesh), ctypes.byref(args.grid), ctypes.byref(prm), _ptr(W), int(n_steps),
+                        _ptr(Wout), _ptr(res))
+    _check(lib, st)
+    return Wout, res

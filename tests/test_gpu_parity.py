@@ -1,0 +1,227 @@
+"""Parity of the CUDA path with the FP64 oracle, element by element.
+
+Every case builds seeded synthetic inputs, runs the CUDA library through the
+C ABI (ugks_create / ugks_step / ugks_moments / ugks_get_f) and the oracle on
+the same inputs, and compares W and the distributions.  Tolerances:
+  * FP64 storage: relative L-inf <= 1e-11 on W and f (round-off only);
+  * FP32 storage: relative L-inf on W <= 1e-5 after one step and <= 1e-4
+    after 100 steps; f <= 1e-5 after one step.
+Relative L-inf of a field = max_i |a_i - b_i| / max_i |b_i|, taken per
+conservative variable (per reduced distribution for f) and maximised."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2606_15720_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def U():
+    from paper_2606_15720_gb300 import ugks
+    ugks.load()
+    return ugks
+
+
+def rel_linf(a, b, axis_fields=-1):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if axis_fields is None:
+        return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+    a2 = np.moveaxis(a, axis_fields, 0).reshape(a.shape[axis_fields], -1)
+    b2 = np.moveaxis(b, axis_fields, 0).reshape(b.shape[axis_fields], -1)
+    out = 0.0
+    for x, y in zip(a2, b2):
+        scale = np.max(np.abs(y))
+        if scale == 0.0:
+            scale = 1.0
+        out = max(out, float(np.max(np.abs(x - y)) / scale))
+    return out
+
+
+def run_pair(U, mesh, grid, gas, prim, nsteps, storage, tile_cells=0):
+    W0 = I.prim_to_conservative(prim, mesh.dim, gas.K)
+    with U.Solver(mesh, grid, gas, W0, storage=storage, tile_cells=tile_cells) as s:
+        dt = s.dt
+        s.step(nsteps)
+        Wg = s.moments()
+        fg = s.get_f(np.arange(mesh.n_cells))            # [cell, r, k]
+        res = s.residual()
+    f0 = O.initial_f(mesh, grid, W0, gas.K)
+    Wo, fo, dto, diag = O.run(mesh, grid, gas, W0, f0, nsteps, dt=dt)
+    return Wg, np.transpose(fg, (1, 0, 2)), res, Wo, fo, diag, dt, dto
+
+
+# ---------------------------------------------------------------------------
+# case builders (small sizes that still span several tiles and a ragged tail)
+# ---------------------------------------------------------------------------
+
+def cavity_case(n=16, nvx=20, model="bgk"):
+    mesh = I.cavity_mesh(n)
+    grid = I.midpoint_grid(nvx, -4.5, 4.5, 2)        # 400 velocities: 12 full blocks + a ragged tail
+    gas = I.Gas(model=model, Pr=1.0 if model == "bgk" else 2 / 3, omega=0.81,
+                mu_ref=I.mu_ref_from_kn(0.075, 0.81), cfl=0.8)
+    prim = I.smooth_random_primitives(mesh, seed=11, amp=0.1)
+    return mesh, grid, gas, prim
+
+
+def periodic3d_case(model="shakhov", K=0):
+    mesh = I.periodic_box((5, 4, 3))
+    grid = I.midpoint_grid(7, -5, 5, 3)              # 343 velocities
+    gas = I.Gas(model=model, K=K, Pr=2 / 3 if model == "shakhov" else 1.0, mu_ref=0.02, omega=0.72)
+    prim = I.smooth_random_primitives(mesh, seed=5, amp=0.15, U0=(0.3, -0.1, 0.2))
+    return mesh, grid, gas, prim
+
+
+def strip1d_case():
+    mesh = I.cartesian_mesh((40,), (0,), (1,), {"x-": 0, "x+": 1},
+                            [I.BC(I.BC_FARFIELD, 1.0, (0.2, 0, 0), 1.0), I.BC(I.BC_OUTFLOW)])
+    grid = I.midpoint_grid(45, -8, 8, 1)
+    gas = I.Gas(model="shakhov", Pr=2 / 3, mu_ref=0.01, omega=0.5, shock_tau_fix=True)
+    prim = I.uniform_primitives(mesh)
+    x = mesh.cell_centroid[:, 0]
+    prim[:, 0] = np.where(x < 0.5, 1.0, 0.3)
+    prim[:, -1] = np.where(x < 0.5, 1.5, 1.0)
+    return mesh, grid, gas, prim
+
+
+def sphere_case(cells=2500, nvx=11):
+    mesh = I.sphere_tet_mesh(cells, seed=3)
+    u_inf = mesh.bc[1].u[0]
+    grid = I.midpoint_grid(nvx, -12, 12, 3)
+    gas = I.Gas(model="shakhov", Pr=2 / 3, omega=0.81, mu_ref=I.mu_ref_from_kn(0.05, 0.81), cfl=0.8)
+    prim = I.smooth_random_primitives(mesh, seed=9, amp=0.1, U0=(u_inf, 0, 0), length=(12, 10, 10))
+    return mesh, grid, gas, prim
+
+
+def cylinder_case(cells=1500, nvx=13):
+    mesh = I.cylinder_tri_mesh(cells, seed=4, mach=3.0)
+    u_inf = mesh.bc[1].u[0]
+    grid = I.midpoint_grid(nvx, -9, 9, 2)
+    gas = I.Gas(model="bgk", omega=0.81, mu_ref=I.mu_ref_from_kn(0.1, 0.81), cfl=0.8, K=2)
+    prim = I.smooth_random_primitives(mesh, seed=2, amp=0.1, U0=(u_inf, 0, 0), length=(12, 10))
+    return mesh, grid, gas, prim
+
+
+CASES = {
+    "cavity_bgk": cavity_case,
+    "cavity_shakhov": lambda: cavity_case(model="shakhov"),
+    "periodic3d_shakhov": periodic3d_case,
+    "periodic3d_bgk_K2": lambda: periodic3d_case("bgk", K=2),
+    "strip1d_farfield_outflow": strip1d_case,
+    "sphere_tet": sphere_case,
+    "cylinder_tri_K2": cylinder_case,
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_matches_oracle(U, name):
+    mesh, grid, gas, prim = CASES[name]()
+    Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 3, "f64", tile_cells=48)
+    assert rel_linf(Wg, Wo) <= 1e-11, rel_linf(Wg, Wo)
+    assert rel_linf(fg, fo, axis_fields=0) <= 1e-11
+    np.testing.assert_allclose(res, diag[-1, :mesh.dim + 2], rtol=1e-9, atol=1e-300)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp32_one_step_matches_oracle(U, name):
+    mesh, grid, gas, prim = CASES[name]()
+    Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 1, "f32", tile_cells=48)
+    assert rel_linf(Wg, Wo) <= 1e-5, rel_linf(Wg, Wo)
+    assert rel_linf(fg, fo, axis_fields=0) <= 1e-5, rel_linf(fg, fo, axis_fields=0)
+
+
+LONG_CASES = {
+    "cavity_bgk": cavity_case,
+    "periodic3d_shakhov": periodic3d_case,
+    "sphere_tet_small": lambda: sphere_case(cells=1200, nvx=9),
+}
+
+
+@pytest.mark.parametrize("name", sorted(LONG_CASES))
+def test_fp32_hundred_steps_matches_oracle(U, name):
+    mesh, grid, gas, prim = LONG_CASES[name]()
+    Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 100, "f32", tile_cells=64)
+    assert rel_linf(Wg, Wo) <= 1e-4, rel_linf(Wg, Wo)
+
+
+def test_cavity_config_200_steps_fp64(U):
+    """32x32 cavity, 24x24 grid, Kn 0.075, FP64, 200 steps (the correctness workload)."""
+    mesh = I.cavity_mesh(32)
+    grid = I.midpoint_grid(24, -4.5, 4.5, 2)
+    gas = I.Gas(model="bgk", omega=0.81, mu_ref=I.mu_ref_from_kn(0.075, 0.81), cfl=0.8)
+    prim = I.uniform_primitives(mesh)
+    Wg, fg, res, Wo, fo, diag, dt, dto = run_pair(U, mesh, grid, gas, prim, 200, "f64")
+    assert rel_linf(Wg, Wo) <= 1e-10
+    assert abs(dt - O.time_step(mesh, grid, 0.8)) <= 1e-15 * dt
+    # the lid drives the gas and the walls hold the mass
+    assert np.max(Wg[:, 1]) > 1e-3
+    assert mesh.cell_volume @ Wg[:, 0] == pytest.approx(1.0, rel=1e-12)
+
+
+def test_tiling_does_not_change_the_result(U):
+    """Faces shared by tiles are evaluated identically by both: W is bitwise
+    independent of the tile size (FP64 and FP32)."""
+    mesh, grid, gas, prim = sphere_case(cells=2000, nvx=9)
+    W0 = I.prim_to_conservative(prim, 3, 0)
+    for storage in ("f64", "f32"):
+        outs = []
+        for tc in (16, 97, 100000):
+            with U.Solver(mesh, grid, gas, W0, storage=storage, tile_cells=tc) as s:
+                s.step(4)
+                outs.append(s.moments())
+        assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_conservation_on_periodic_box_fp32(U):
+    mesh, grid, gas, prim = periodic3d_case()
+    W0 = I.prim_to_conservative(prim, 3, 0)
+    with U.Solver(mesh, grid, gas, W0, storage="f32", tile_cells=8) as s:
+        s.step(20)
+        W = s.moments()
+    tot0, tot = mesh.cell_volume @ W0, mesh.cell_volume @ W
+    np.testing.assert_allclose(tot, tot0, rtol=1e-13, atol=1e-13)
+
+
+def test_zero_steps_and_checkpoint_roundtrip(U):
+    mesh, grid, gas, prim = cavity_case(n=8, nvx=10)
+    W0 = I.prim_to_conservative(prim, 2, 0)
+    with U.Solver(mesh, grid, gas, W0, storage="f64") as s:
+        s.step(0)
+        np.testing.assert_array_equal(s.moments(), W0)
+        np.testing.assert_array_equal(s.residual(), 0.0)
+        s.step(3)
+        W3, f3, k = s.get_state()
+        assert k == 3
+        s.step(4)
+        W7 = s.moments()
+    with U.Solver(mesh, grid, gas, W0, storage="f64") as s2:
+        s2.set_state(W3, f3, 3)
+        s2.step(4)
+        assert np.array_equal(s2.moments(), W7)
+
+
+def test_solve_one_shot_with_host_buffers(U):
+    mesh, grid, gas, prim = cavity_case(n=8, nvx=10)
+    W0 = I.prim_to_conservative(prim, 2, 0)
+    Wout, res = U.solve(mesh, grid, gas, W0, 5, storage="f64")
+    f0 = O.initial_f(mesh, grid, W0, 0)
+    with U.Solver(mesh, grid, gas, W0, storage="f64") as s:
+        dt = s.dt
+    Wo, _, _, diag = O.run(mesh, grid, gas, W0, f0, 5, dt=dt)
+    assert rel_linf(Wout, Wo) <= 1e-11
+    np.testing.assert_allclose(res, diag[-1, :4], rtol=1e-9)
+
+
+def test_nonphysical_state_is_reported(U):
+    mesh, grid, gas, prim = cavity_case(n=8, nvx=10)
+    W0 = I.prim_to_conservative(prim, 2, 0)
+    with U.Solver(mesh, grid, gas, W0, storage="f64") as s:
+        Wb, fb, _ = s.get_state()
+        Wb[5, 0] = -1.0                     # negative density planted on the host
+        s.set_state(Wb, fb, 0)
+        s.step(1)
+        with pytest.raises(U.UGKSError) as e:
+            s.moments()
+        assert e.value.status == 6
