@@ -1,0 +1,318 @@
+"""Benchmark of the UGKS velocity-block sweep on the 3-D sphere workload.
+
+Workload: hypersonic flow (Ma 5, Kn 0.05, Shakhov, Pr 2/3, monatomic) around a
+unit sphere on a seeded Delaunay tetrahedral mesh of ~1e5 cells graded toward
+the body, with a 32^3 uniform velocity grid on [-12, 12]^3 (3.3e9 phase-space
+points), FP32 distribution storage with FP64 moments, W update and interface
+coefficients; diffuse isothermal wall at the stagnation temperature.  Inputs
+are synthetic (no dataset).
+
+metric: phase-space DOF updates per second = n_cells * n_v * n_reduced / step time.
+
+Arms:
+  default            the CUDA library through its C ABI; device-timed steps
+                     (CUDA events on the library's stream), plus an end-to-end
+                     number through the one-shot host-buffer call, a roofline
+                     for the sweep kernel and the oracle's CPU baseline.
+  --impl reference   the FP64 CPU oracle on a bounded sample of the workload.
+Under torchrun each rank runs an independent replica (the path does not shard
+across GPUs); rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2606_15720_gb300 import inputs as I  # noqa: E402
+
+METRIC = "phase-space DOF updates/s per UGKS step"
+UNIT = "DOF/s"
+WORKLOAD = "sphere_tet100k_v32cube_shakhov_ma5_kn0.05_fp32"
+MESH_CELLS = 100_000
+MESH_SEED = 2
+NV_AXIS = 32
+
+
+def build_workload():
+    mesh = I.sphere_tet_mesh(MESH_CELLS, seed=MESH_SEED)
+    grid = I.midpoint_grid(NV_AXIS, -12.0, 12.0, 3)
+    gas = I.Gas(model="shakhov", K=0, Pr=2.0 / 3.0, omega=0.81, mu_ref=I.mu_ref_from_kn(0.05, 0.81), cfl=0.8)
+    prim = I.uniform_primitives(mesh, 1.0, mesh.bc[1].u, 1.0)   # freestream start
+    W0 = I.prim_to_conservative(prim, 3, 0)
+    return mesh, grid, gas, W0
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def sweep_source_hash():
+    h = hashlib.sha256()
+    for fn in ("ugks_sweep.cu", "ugks_internal.cuh", "ugks_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_15720_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("source_hash") != sweep_source_hash():
+        return None
+    return d.get("bytes_per_launch_full_workload")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(mesh, grid, gas, W0, target_cells=3000, steps=2):
+    """The FP64 oracle as it stands, on a bounded sample of the workload: the
+    face-connected patch of ~target_cells cells around a body-adjacent cell,
+    all 32^3 velocities, `steps` steps."""
+    import oracle as O
+    seed = int(mesh.face_owner[np.flatnonzero(mesh.face_neighbor == -1)[0]])
+    rings, cells, pm = 1, None, None
+    while True:
+        cells, pm = I.submesh(mesh, [seed], rings)
+        if pm.n_cells >= target_cells or rings > 40:
+            break
+        rings += 1
+    W = W0[cells]
+    f = O.initial_f(pm, grid, W, gas.K)
+    dt = 1e-4
+    O.run(pm, grid, gas, W, f, 1, dt=dt)             # warm-up (page-in, thread pool)
+    t0 = time.perf_counter()
+    O.run(pm, grid, gas, W, f, steps, dt=dt)
+    el = time.perf_counter() - t0
+    dof = pm.n_cells * grid.n_v * O.n_reduced(3, gas.K)
+    return {"value": dof * steps / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{steps} steps of a {pm.n_cells}-cell patch of the workload mesh x {grid.n_v} velocities "
+                      f"({dof * steps:.3g} DOF updates, {el:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    mesh, grid, gas, W0 = build_workload()
+    import oracle as O
+    seed = int(mesh.face_owner[np.flatnonzero(mesh.face_neighbor == -1)[0]])
+    rings = 1
+    while True:
+        cells, pm = I.submesh(mesh, [seed], rings)
+        if pm.n_cells >= 1500 or rings > 40:
+            break
+        rings += 1
+    W = W0[cells]
+    f = O.initial_f(pm, grid, W, gas.K)
+    dt = 1e-4
+    dof = pm.n_cells * grid.n_v * O.n_reduced(3, gas.K)
+    for _ in range(args.warmup):
+        W, f, _, _ = O.run(pm, grid, gas, W, f, 1, dt=dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        W, f, _, _ = O.run(pm, grid, gas, W, f, 1, dt=dt)
+    el = time.perf_counter() - t0
+    value = dof * args.steps / el
+    sample = f"each step: one oracle step of a {pm.n_cells}-cell patch of the workload mesh x {grid.n_v} velocities"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_cells": pm.n_cells, "n_v": grid.n_v, "sampled_from_cells": mesh.n_cells},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CUDA library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2606_15720_gb300 import ugks as U
+
+    mesh, grid, gas, W0 = build_workload()
+    stream = torch.cuda.Stream()
+    n_reduced = 1
+    dof = mesh.n_cells * grid.n_v * n_reduced
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        solver = U.Solver(mesh, grid, gas, W0, storage="f32", stream=int(stream.cuda_stream))
+        assert solver.n_reduced == n_reduced
+        solver.step(args.warmup)
+        solver.residual()
+        solver.stats_enable(True)
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        start.record(stream)
+        solver.step(args.steps)
+        stop.record(stream)
+        stop.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop()
+        ms = start.elapsed_time(stop)
+        stats = solver.stats()
+        res = solver.residual()
+        W_end = solver.moments()
+        solver.close()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_per_step = ms_max / args.steps
+    value = dof * world / (ms_per_step * 1e-3)
+
+    # roofline of the dominant kernel (the velocity-block sweep): algorithmic
+    # bytes = stage-1 read + write of f and stage-2 read + write of f, 4 bytes each
+    sweep_ms, sweep_n = stats.get("velocity_block_sweep", (0.0, 0))
+    hbm_peak, peak_kind = load_peaks()
+    bytes_alg = 16.0 * dof
+    achieved = bytes_alg / (sweep_ms / max(sweep_n, 1) * 1e-3) / 1e9 if sweep_n else None
+    roofline = {"bound": "hbm", "kernel": "velocity_block_sweep", "achieved": achieved, "peak": hbm_peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": (achieved / hbm_peak) if achieved else None,
+                "traffic": recorded_traffic(), "algorithmic_bytes_per_launch": bytes_alg,
+                "launch_ms": sweep_ms / max(sweep_n, 1)}
+
+    # end to end through the one-shot C call with host buffers: mesh, grid and
+    # W_init copied in, n steps, W and the residual copied out
+    barrier()
+    t0 = time.perf_counter()
+    W_e2e, res_e2e = U.solve(mesh, grid, gas, W0, args.steps, storage="f32")
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    in_bytes = sum(a.nbytes for a in (mesh.cell_volume, mesh.cell_centroid, mesh.face_owner, mesh.face_neighbor,
+                                      mesh.face_area, mesh.face_normal, mesh.face_centroid, mesh.face_shift,
+                                      grid.u, grid.weight, W0))
+    out_bytes = W_e2e.nbytes + res_e2e.nbytes
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": dof * world * args.steps / float(te.item()), "unit": UNIT,
+           "h2d_bytes_per_step": int(math.ceil(in_bytes / args.steps)),
+           "d2h_bytes_per_step": int(math.ceil(out_bytes / args.steps)),
+           "includes": "ugks_solve: create from host arrays (renumbering, geometry, f init), all steps, W and residual read back"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(mesh, grid, gas, W0)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_cells": mesh.n_cells, "n_faces": mesh.n_faces, "n_v": grid.n_v,
+                       "n_reduced": n_reduced, "dof_per_step": dof, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (two 13.1 GB distribution buffers)",
+                       "state_after": {"residual": [float(x) for x in res],
+                                       "finite": bool(np.all(np.isfinite(W_end)))}},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(sum(n for _, n in stats.values())),
+            "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in stats.items()},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -12,9 +12,11 @@
  * a blocked summation order is requested (Sec. 2.2.6, Eq. 63-64), and no
  * fusion.  Where the paper is silent the following readings are used (they
  * bind the CUDA path too):
- *   R1 limiter: Venkatakrishnan, eps^2 = (K_v h)^3, h = |Omega|^(1/D), phi
- *      clipped to [0,1]; per cell, per velocity, per reduced function; also
- *      per component of W for the macroscopic reconstruction.
+ *   R1 limiter: Venkatakrishnan with eps^2 = (K_v h)^3 m^2, h = |Omega|^(1/D),
+ *      m = the largest |value| over the cell and its stencil (the limited
+ *      quantity's own scale; f spans many decades, so an absolute eps never
+ *      limits it), phi clipped to [0,1]; per cell, per velocity, per reduced
+ *      function; also per component of W for the macroscopic reconstruction.
  *   R2 gradient: unweighted least squares over face neighbours, M^-1 sum d df.
  *   R3 stencil: far-field / outflow ghosts included (ghost centroid mirrored
  *      across the face, ghost distribution = Maxwellian of the ghost state);
@@ -693,7 +695,8 @@ int orc_step(const orc_mesh *m, int64_t nv, const double *u, const double *w, co
         face_view(m, adj.face[s], i, nout, xfc, xo);
         double d2 = 0.0;
         for (int d = 0; d < D; ++d) d2 += g[t][d] * (xfc[d] - m->xc[i * D + d]);
-        double ph = limiter_phi(p->limiter, d2, wmax[t] - Wi[t], wmin[t] - Wi[t], eps2);
+        double mag = fabs(wmax[t]) > fabs(wmin[t]) ? fabs(wmax[t]) : fabs(wmin[t]);
+        double ph = limiter_phi(p->limiter, d2, wmax[t] - Wi[t], wmin[t] - Wi[t], eps2 * mag * mag);
         if (ph < phi) phi = ph;
       }
       if (phi < 0.0) phi = 0.0;
@@ -814,7 +817,8 @@ int orc_step(const orc_mesh *m, int64_t nv, const double *u, const double *w, co
             face_view(m, adj.face[s], i, nout, xfc, xo);
             double d2 = 0.0;
             for (int d = 0; d < D; ++d) d2 += g[d] * (xfc[d] - xi[d]);
-            double ph = limiter_phi(p->limiter, d2, fmax - fi[k], fmin - fi[k], eps2);
+            double mag = fabs(fmax) > fabs(fmin) ? fabs(fmax) : fabs(fmin);
+            double ph = limiter_phi(p->limiter, d2, fmax - fi[k], fmin - fi[k], eps2 * mag * mag);
             if (ph < phi) phi = ph;
           }
           if (phi < 0.0) phi = 0.0;

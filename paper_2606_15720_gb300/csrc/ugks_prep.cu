@@ -82,7 +82,9 @@ __device__ __forceinline__ Vec5 ghost_state(const BCDev& bc, const Vec5& Wi, int
   return cons_of<D>(p, K);
 }
 
-// Venkatakrishnan / Barth-Jespersen limiter value for one face.
+// Venkatakrishnan / Barth-Jespersen limiter value for one face; eps2 is the
+// Venkatakrishnan constant (K_v h)^3 already scaled by the squared magnitude
+// of the limited quantity on the stencil.
 __device__ __forceinline__ double limiter_fn(int kind, double d2, double dmax, double dmin, double eps2) {
   if (kind == 0 || d2 == 0.0) return 1.0;
   const double dp = d2 > 0.0 ? dmax : dmin;
@@ -363,7 +365,8 @@ __global__ void k_cell(int64_t Nc, Gas g, const double* W, const double* q, cons
       double d2 = 0.0;
 #pragma unroll
       for (int d = 0; d < D; ++d) d2 += grad[t][d] * s.r[d];
-      phi[t] = fmin(phi[t], limiter_fn(g.limiter, d2, wmax[t] - Wi.v[t], wmin[t] - Wi.v[t], eps2));
+      const double mag = fmax(fabs(wmax[t]), fabs(wmin[t]));
+      phi[t] = fmin(phi[t], limiter_fn(g.limiter, d2, wmax[t] - Wi.v[t], wmin[t] - Wi.v[t], eps2 * mag * mag));
     }
   }
 #pragma unroll

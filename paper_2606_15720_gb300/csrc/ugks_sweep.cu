@@ -150,8 +150,13 @@ __global__ void __launch_bounds__(512) k_sweep(SweepArgs<T> a) {
           fmn[r] = fmin(fmn[r], fo[r]);
         }
       }
-      const T eps2 = a.eps2[c];
-      T phi[NR];
+      const T eps2c = a.eps2[c];
+      T phi[NR], eps2[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const T mag = fmax(fabs(fmx[r]), fabs(fmn[r]));
+        eps2[r] = eps2c * mag * mag;  // Venkatakrishnan constant in the units of f
+      }
 #pragma unroll
       for (int r = 0; r < NR; ++r) phi[r] = T(1);
       if (limiter != 0) {
@@ -168,8 +173,8 @@ __global__ void __launch_bounds__(512) k_sweep(SweepArgs<T> a) {
               if (limiter == 2) {
                 ph = fmin(T(1), dp / d2);
               } else {
-                T num = dp * dp + eps2 + T(2) * d2 * dp;
-                T den = dp * dp + T(2) * d2 * d2 + dp * d2 + eps2;
+                T num = dp * dp + eps2[r] + T(2) * d2 * dp;
+                T den = dp * dp + T(2) * d2 * d2 + dp * d2 + eps2[r];
                 ph = den != T(0) ? num / den : T(1);
               }
             }

@@ -86,10 +86,11 @@ def strip1d_case():
     return mesh, grid, gas, prim
 
 
-def sphere_case(cells=2500, nvx=11):
-    mesh = I.sphere_tet_mesh(cells, seed=3)
+def sphere_case(cells=2500, nvx=11, mach=2.0, vmax=6.0):
+    # the velocity grid must resolve the gas (spacing ~ thermal speed): 11^3 on [-6, 6]^3
+    mesh = I.sphere_tet_mesh(cells, seed=3, mach=mach)
     u_inf = mesh.bc[1].u[0]
-    grid = I.midpoint_grid(nvx, -12, 12, 3)
+    grid = I.midpoint_grid(nvx, -vmax, vmax, 3)
     gas = I.Gas(model="shakhov", Pr=2 / 3, omega=0.81, mu_ref=I.mu_ref_from_kn(0.05, 0.81), cfl=0.8)
     prim = I.smooth_random_primitives(mesh, seed=9, amp=0.1, U0=(u_inf, 0, 0), length=(12, 10, 10))
     return mesh, grid, gas, prim
@@ -135,7 +136,7 @@ def test_fp32_one_step_matches_oracle(U, name):
 LONG_CASES = {
     "cavity_bgk": cavity_case,
     "periodic3d_shakhov": periodic3d_case,
-    "sphere_tet_small": lambda: sphere_case(cells=1200, nvx=9),
+    "sphere_tet_small": lambda: sphere_case(cells=1200, nvx=12),
 }
 
 
