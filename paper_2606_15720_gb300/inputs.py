@@ -546,3 +546,56 @@ def prim_to_conservative(prim: np.ndarray, dim: int, K: int) -> np.ndarray:
     W[:, 1:1 + dim] = rho[:, None] * U
     W[:, -1] = 0.5 * rho * np.sum(U * U, axis=1) + (K + 3) * rho * T / 4.0
     return W
+
+
+def submesh(mesh: Mesh, seeds, rings: int):
+    """Cells within ``rings`` face hops of ``seeds``, as a closed mesh.
+
+    Faces to cells outside the patch become faces of an added outflow boundary
+    condition (flipped so that the owner is inside).  Returns (cells, mesh)
+    where ``cells`` are the original indices in patch order."""
+    nb = [[] for _ in range(mesh.n_cells)]
+    for o, n in zip(mesh.face_owner, mesh.face_neighbor):
+        if n >= 0:
+            nb[o].append(n)
+            nb[n].append(o)
+    cells = set(int(c) for c in seeds)
+    frontier = set(cells)
+    for _ in range(rings):
+        new = {j for c in frontier for j in nb[c]} - cells
+        cells |= new
+        frontier = new
+    cells = np.array(sorted(cells), dtype=np.int64)
+    local = -np.ones(mesh.n_cells, dtype=np.int64)
+    local[cells] = np.arange(cells.size)
+    inside = local >= 0
+    own, nei = mesh.face_owner, mesh.face_neighbor
+    keep = inside[own] | ((nei >= 0) & inside[np.maximum(nei, 0)])
+    fo, fn = own[keep], nei[keep]
+    nrm = mesh.face_normal[keep].copy()
+    cen = mesh.face_centroid[keep].copy()
+    shift = mesh.face_shift[keep].copy()
+    out_bc = len(mesh.bc)
+    new_own = np.empty(fo.size, dtype=np.int64)
+    new_nei = np.empty(fo.size, dtype=np.int64)
+    for t in range(fo.size):
+        o, n = fo[t], fn[t]
+        if inside[o]:
+            new_own[t] = local[o]
+            if n < 0:
+                new_nei[t] = n
+            elif inside[n]:
+                new_nei[t] = local[n]
+            else:
+                new_nei[t] = -(out_bc + 1)
+                shift[t] = 0.0
+        else:                                      # neighbour inside, owner outside: flip
+            new_own[t] = local[n]
+            new_nei[t] = -(out_bc + 1)
+            nrm[t] = -nrm[t]
+            cen[t] = cen[t] - shift[t]
+            shift[t] = 0.0
+    return cells, Mesh(dim=mesh.dim, cell_volume=mesh.cell_volume[cells], cell_centroid=mesh.cell_centroid[cells],
+                       face_owner=new_own, face_neighbor=new_nei, face_area=mesh.face_area[keep], face_normal=nrm,
+                       face_centroid=cen, face_shift=shift, bc=list(mesh.bc) + [BC(BC_OUTFLOW)],
+                       name=mesh.name + "_patch")

@@ -14,50 +14,6 @@ from paper_2606_15720_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 
-def extract_patch(mesh: I.Mesh, seeds, rings: int):
-    nb = [[] for _ in range(mesh.n_cells)]
-    for o, n in zip(mesh.face_owner, mesh.face_neighbor):
-        if n >= 0:
-            nb[o].append(n)
-            nb[n].append(o)
-    cells = set(int(c) for c in seeds)
-    frontier = set(cells)
-    for _ in range(rings):
-        new = {j for c in frontier for j in nb[c]} - cells
-        cells |= new
-        frontier = new
-    cells = np.array(sorted(cells), dtype=np.int64)
-    local = -np.ones(mesh.n_cells, dtype=np.int64)
-    local[cells] = np.arange(cells.size)
-    inside = local >= 0
-    own, nei = mesh.face_owner, mesh.face_neighbor
-    keep = inside[own] | ((nei >= 0) & inside[np.maximum(nei, 0)])
-    fo, fn = own[keep], nei[keep]
-    nrm = mesh.face_normal[keep].copy()
-    cen = mesh.face_centroid[keep].copy()
-    out_bc = len(mesh.bc)
-    new_own = np.empty(fo.size, dtype=np.int64)
-    new_nei = np.empty(fo.size, dtype=np.int64)
-    for t in range(fo.size):
-        o, n = fo[t], fn[t]
-        if inside[o]:
-            new_own[t] = local[o]
-            if n < 0:
-                new_nei[t] = n
-            elif inside[n]:
-                new_nei[t] = local[n]
-            else:
-                new_nei[t] = -(out_bc + 1)
-        else:                                      # neighbour inside, owner outside: flip
-            new_own[t] = local[n]
-            new_nei[t] = -(out_bc + 1)
-            nrm[t] = -nrm[t]
-    return cells, I.Mesh(dim=mesh.dim, cell_volume=mesh.cell_volume[cells], cell_centroid=mesh.cell_centroid[cells],
-                         face_owner=new_own, face_neighbor=new_nei, face_area=mesh.face_area[keep], face_normal=nrm,
-                         face_centroid=cen, face_shift=np.zeros_like(cen),
-                         bc=list(mesh.bc) + [I.BC(I.BC_OUTFLOW)], name="patch")
-
-
 def test_sphere_full_size_sampled_cells_match_oracle():
     from paper_2606_15720_gb300 import ugks as U
     mesh = I.sphere_tet_mesh(100_000, seed=2)
@@ -78,7 +34,7 @@ def test_sphere_full_size_sampled_cells_match_oracle():
         s.step(1)
         W1 = s.moments()
         f1 = s.get_f(picks)                                   # [n, 1, nv]
-    cells, pm = extract_patch(mesh, picks, rings=3)
+    cells, pm = I.submesh(mesh, picks, rings=3)
     f0 = O.initial_f(pm, grid, W0[cells], 0)
     Wo, fo, _, _ = O.run(pm, grid, gas, W0[cells], f0, 1, dt=dt)
     loc = np.searchsorted(cells, picks)
