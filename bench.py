@@ -42,9 +42,9 @@ MESH_SEED = 2
 NV_AXIS = 32
 
 
-def build_workload():
-    mesh = I.sphere_tet_mesh(MESH_CELLS, seed=MESH_SEED)
-    grid = I.midpoint_grid(NV_AXIS, -12.0, 12.0, 3)
+def build_workload(cells=MESH_CELLS, nv_axis=NV_AXIS):
+    mesh = I.sphere_tet_mesh(cells, seed=MESH_SEED)
+    grid = I.midpoint_grid(nv_axis, -12.0, 12.0, 3)
     gas = I.Gas(model="shakhov", K=0, Pr=2.0 / 3.0, omega=0.81, mu_ref=I.mu_ref_from_kn(0.05, 0.81), cfl=0.8)
     prim = I.uniform_primitives(mesh, 1.0, mesh.bc[1].u, 1.0)   # freestream start
     W0 = I.prim_to_conservative(prim, 3, 0)
@@ -206,7 +206,7 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2606_15720_gb300 import ugks as U
 
-    mesh, grid, gas, W0 = build_workload()
+    mesh, grid, gas, W0 = build_workload(args.cells, args.nv_axis)
     stream = torch.cuda.Stream()
     n_reduced = 1
     dof = mesh.n_cells * grid.n_v * n_reduced
@@ -257,9 +257,11 @@ def run_gpu(args):
 
     # end to end through the one-shot C call with host buffers: mesh, grid and
     # W_init copied in, n steps, W and the residual copied out
+    if args.no_e2e:
+        e2e = None
     barrier()
     t0 = time.perf_counter()
-    W_e2e, res_e2e = U.solve(mesh, grid, gas, W0, args.steps, storage="f32")
+    W_e2e, res_e2e = U.solve(mesh, grid, gas, W0, args.steps if not args.no_e2e else 0, storage="f32")
     e2e_s = time.perf_counter() - t0
     barrier()
     in_bytes = sum(a.nbytes for a in (mesh.cell_volume, mesh.cell_centroid, mesh.face_owner, mesh.face_neighbor,
@@ -269,7 +271,7 @@ def run_gpu(args):
     te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": dof * world * args.steps / float(te.item()), "unit": UNIT,
+    e2e = None if args.no_e2e else {"value": dof * world * args.steps / float(te.item()), "unit": UNIT,
            "h2d_bytes_per_step": int(math.ceil(in_bytes / args.steps)),
            "d2h_bytes_per_step": int(math.ceil(out_bytes / args.steps)),
            "includes": "ugks_solve: create from host arrays (renumbering, geometry, f init), all steps, W and residual read back"}
@@ -279,14 +281,16 @@ def run_gpu(args):
             dist.destroy_process_group()
         return 0
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and (args.cells, args.nv_axis) == (MESH_CELLS, NV_AXIS):
         cpu = cpu_baseline(mesh, grid, gas, W0)
+    workload = WORKLOAD if (args.cells, args.nv_axis) == (MESH_CELLS, NV_AXIS) else \
+        f"sphere_tet{args.cells // 1000}k_v{args.nv_axis}cube_shakhov_fp32 (reduced size for profiling)"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_cells": mesh.n_cells, "n_faces": mesh.n_faces, "n_v": grid.n_v,
+            "config": {"workload": workload, "n_cells": mesh.n_cells, "n_faces": mesh.n_faces, "n_v": grid.n_v,
                        "n_reduced": n_reduced, "dof_per_step": dof, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (two 13.1 GB distribution buffers)",
+                       "l2": "inputs larger than L2 (two %.1f GB distribution buffers)" % (dof * 4 / 1e9),
                        "state_after": {"residual": [float(x) for x in res],
                                        "finite": bool(np.all(np.isfinite(W_end)))}},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
@@ -306,6 +310,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cells", type=int, default=MESH_CELLS, help="mesh size (profiling runs only)")
+    ap.add_argument("--nv-axis", type=int, default=NV_AXIS, help="velocities per axis (profiling runs only)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
