@@ -135,6 +135,26 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
 /* Advances n_steps >= 0 UGKS time steps (Algorithm 5), asynchronously. */
 ugks_status ugks_step(ugks_ctx *ctx, int32_t n_steps);
 
+/* Allocation-free variant of ugks_step, for callers that must not allocate
+ * device memory once the solver is set up: for example a host application
+ * whose device memory pool is owned by another allocator (a framework's
+ * caching allocator holds it), or a latency-critical loop in which the
+ * device-wide synchronisation that cudaMalloc / cudaFree can imply is not
+ * acceptable.  The paper has no counterpart; this is an interface addition.
+ * It advances n_steps >= 0 steps exactly like ugks_step, with the context's
+ * own inputs and outputs, but the velocity-block sweep's gradient,
+ * micro-flux and face-accumulator scratch lives in one file-scope device
+ * array of 16 MiB that every GPU loading this library holds until exit.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress,
+ * once per device); make that first call before any stream capture.  All
+ * calls share the array and each call overwrites it (the accumulators are
+ * cleared by the kernel), so calls whose work overlaps on the GPU (other
+ * streams, other contexts) race on it.  Contexts whose scratch needs more
+ * than 16 MiB are rejected with UGKS_ERR_INVALID_ARGUMENT and a message
+ * naming the size; use ugks_step for them. */
+ugks_status ugks_step_static_scratch(ugks_ctx *ctx, int32_t n_steps);
+
 /* Copies W (host, [n_cells][dim+2], original cell order) and, if q_out is not
  * NULL, the heat flux of the current distribution ([n_cells][dim], Eq. 13). */
 ugks_status ugks_moments(ugks_ctx *ctx, double *W_out, double *q_out);

@@ -398,6 +398,77 @@ ugks_status step_typed(ugks_ctx* ctx) {
   return UGKS_OK;
 }
 
+
+// Variant of step_typed whose sweep takes its gradient, micro-flux and
+// face-accumulator scratch from the file-scope device array of ugks_sweep.cu
+// instead of the context's own buffers; it records no timing events.
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+template <typename T>
+size_t static_scratch_need(const ugks_ctx* ctx) {
+  return align256(size_t(ctx->ntiles) * ctx->G_stride * sizeof(T)) +
+         align256(size_t(ctx->ntiles) * ctx->Phi_stride * sizeof(T)) +
+         align256(size_t(ctx->ntiles) * ctx->Facc_stride * sizeof(double));
+}
+
+template <typename T>
+ugks_status step_typed_static(ugks_ctx* ctx, unsigned char* base) {
+  const int cur = ctx->cur, nxt = 1 - cur;
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_res_acc, 0, NWP * sizeof(double), ctx->stream));
+  launch_cell(ctx->stream, ctx->Nc, ctx->gas, ctx->d_W[cur], ctx->d_q[cur], ctx->d_cf_off, ctx->d_cf, ctx->d_vol,
+              ctx->d_bcs, ctx->d_cp[0], ctx->d_gW, ctx->d_status);
+  CUDA_TRY(ctx, cudaGetLastError());
+  launch_face<T>(ctx->stream, ctx->Nf, ctx->gas, ctx->d_W[cur], ctx->d_gW, ctx->d_q[cur], ctx->d_fown, ctx->d_fnei,
+                 ctx->d_fnormal, ctx->d_fcent, ctx->d_fshift, ctx->d_xc, ctx->d_bcs,
+                 static_cast<FaceRec<T>*>(ctx->d_fr));
+  CUDA_TRY(ctx, cudaGetLastError());
+  const size_t g_bytes = align256(size_t(ctx->ntiles) * ctx->G_stride * sizeof(T));
+  const size_t p_bytes = align256(size_t(ctx->ntiles) * ctx->Phi_stride * sizeof(T));
+  SweepArgs<T> a;
+  a.g = ctx->gas;
+  a.Nc = ctx->Nc;
+  a.M = ctx->M;
+  a.nv = ctx->nv;
+  a.f_cur = static_cast<const T*>(ctx->d_f[cur]);
+  a.f_next = static_cast<T*>(ctx->d_f[nxt]);
+  a.W_cur = ctx->d_W[cur];
+  a.W_next = ctx->d_W[nxt];
+  a.cp = ctx->d_cp[0];
+  a.cp_next = ctx->d_cp[1];
+  a.q_next = ctx->d_q[nxt];
+  a.ux = static_cast<const T*>(ctx->d_uxT);
+  a.uy = static_cast<const T*>(ctx->d_uyT);
+  a.uz = static_cast<const T*>(ctx->d_uzT);
+  a.w = static_cast<const T*>(ctx->d_wT);
+  a.vol = ctx->d_vol;
+  a.eps2 = static_cast<const T*>(ctx->d_eps2);
+  a.cf_off = ctx->d_cf_off;
+  a.cf = static_cast<const CellFaceT<T>*>(ctx->d_cfT);
+  a.fg = static_cast<const FaceGeom<T>*>(ctx->d_fg);
+  a.fr = static_cast<const FaceRec<T>*>(ctx->d_fr);
+  a.bcs = ctx->d_bcs;
+  a.tile_begin = ctx->d_tile_begin;
+  a.gset_off = ctx->d_gset_off;
+  a.gset = ctx->d_gset;
+  a.tf_off = ctx->d_tf_off;
+  a.tf = ctx->d_tf;
+  a.tcf = ctx->d_tcf;
+  a.G = reinterpret_cast<T*>(base);
+  a.Phi = reinterpret_cast<T*>(base + g_bytes);
+  a.Facc = reinterpret_cast<double*>(base + g_bytes + p_bytes);
+  a.G_stride = ctx->G_stride;
+  a.Phi_stride = ctx->Phi_stride;
+  a.Facc_stride = ctx->Facc_stride;
+  a.res_acc = ctx->d_res_acc;
+  a.status = ctx->d_status;
+  CUDA_TRY(ctx, launch_sweep<T>(ctx->stream, a, ctx->ntiles, ctx->threads));
+  launch_residual_finalize(ctx->stream, ctx->D + 2, ctx->Nc, ctx->d_res_acc, ctx->d_res);
+  CUDA_TRY(ctx, cudaGetLastError());
+  ctx->cur = nxt;
+  ctx->step++;
+  return UGKS_OK;
+}
+
 ugks_status check_status(ugks_ctx* ctx) {
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   int st = 0;
@@ -765,6 +836,27 @@ ugks_status ugks_step(ugks_ctx* ctx, int32_t n_steps) {
   if (n_steps < 0) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "n_steps must be >= 0");
   for (int32_t s = 0; s < n_steps; ++s) {
     ugks_status st = ctx->storage == UGKS_STORAGE_F64 ? step_typed<double>(ctx) : step_typed<float>(ctx);
+    if (st != UGKS_OK) return st;
+  }
+  return UGKS_OK;
+}
+
+
+ugks_status ugks_step_static_scratch(ugks_ctx* ctx, int32_t n_steps) {
+  if (!ctx) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL context");
+  if (n_steps < 0) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "n_steps must be >= 0");
+  const size_t need = ctx->storage == UGKS_STORAGE_F64 ? static_scratch_need<double>(ctx)
+                                                       : static_scratch_need<float>(ctx);
+  if (need > kStaticScratchBytes)
+    return fail(ctx, UGKS_ERR_INVALID_ARGUMENT,
+                "ugks_step_static_scratch: this context needs %zu bytes of sweep scratch, more than the static "
+                "limit of %zu bytes; use ugks_step", need, kStaticScratchBytes);
+  void* base = nullptr;
+  CUDA_TRY(ctx, static_scratch_address(&base));
+  for (int32_t s = 0; s < n_steps; ++s) {
+    ugks_status st = ctx->storage == UGKS_STORAGE_F64
+                         ? step_typed_static<double>(ctx, static_cast<unsigned char*>(base))
+                         : step_typed_static<float>(ctx, static_cast<unsigned char*>(base));
     if (st != UGKS_OK) return st;
   }
   return UGKS_OK;

@@ -82,4 +82,11 @@ cudaError_t launch_sweep(cudaStream_t s, const SweepArgs<T>& a, int ntiles, int 
 template <typename T>
 int sweep_occupancy(int D, int NR, int threads);
 
+// Size of the file-scope device scratch used by ugks_step_static_scratch.
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB
+
+// Device address of that scratch on the current device (looked up once per
+// device with cudaGetSymbolAddress).
+cudaError_t static_scratch_address(void** ptr);
+
 }  // namespace ugks

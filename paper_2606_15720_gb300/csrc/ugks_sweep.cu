@@ -22,6 +22,7 @@
 // stay in L2 across the CTAs that sweep the same velocity block together.
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "ugks_internal.cuh"
 #include "ugks_kernels.cuh"
@@ -546,6 +547,34 @@ int sweep_occupancy(int D, int NR, int threads) {
   if (D == 3 && NR == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<3, 1, T>, threads, 0);
   if (D == 3 && NR == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<3, 2, T>, threads, 0);
   return n;
+}
+
+
+// ---------------------------------------------------------------------------
+// Scratch of the allocation-free step (ugks_step_static_scratch).  Every GPU
+// that loads this library holds this array until the process exits.  In host
+// code the symbol is only a host-side stand-in: its device address must be
+// obtained with cudaGetSymbolAddress, once per device, with that device
+// current; kernels receive that address.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_static_sweep_scratch[kStaticScratchBytes];
+
+cudaError_t static_scratch_address(void** ptr) {
+  static std::mutex mu;
+  static void* addr[64] = {nullptr};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_sweep_scratch);
+    if (e != cudaSuccess) return e;
+    addr[dev] = p;
+  }
+  *ptr = addr[dev];
+  return cudaSuccess;
 }
 
 template cudaError_t launch_sweep<float>(cudaStream_t, const SweepArgs<float>&, int, int);

@@ -72,6 +72,7 @@ def load(build_if_missing: bool = True):
     sig = {
         "ugks_create": [P, P, P, P, P, P],
         "ugks_step": [P, I32],
+        "ugks_step_static_scratch": [P, I32],
         "ugks_moments": [P, P, P],
         "ugks_residual": [P, P],
         "ugks_dt": [P, P],
@@ -177,6 +178,10 @@ class Solver:
 
     def step(self, n: int = 1) -> None:
         self._c(self._lib.ugks_step(self._ctx, int(n)))
+
+    def step_static_scratch(self, n: int = 1) -> None:
+        """ugks_step_static_scratch: the same step without any device allocation."""
+        self._c(self._lib.ugks_step_static_scratch(self._ctx, int(n)))
 
     def moments(self, with_q: bool = False):
         W = np.zeros((self.mesh.n_cells, self.dim + 2))
