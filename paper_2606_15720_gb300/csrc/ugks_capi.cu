@@ -63,13 +63,13 @@ struct ugks_ctx {
   // distributions
   void* d_f[2] = {nullptr, nullptr};
   // tiles and scratch
-  int ntiles = 0, threads = 512;
+  int ntiles = 0, grid = 0, threads = 1024;
+  size_t smem_bytes = 0;
   int64_t *d_tile_begin = nullptr, *d_gset_off = nullptr, *d_gset = nullptr, *d_tf_off = nullptr;
   TileFace* d_tf = nullptr;
   int32_t* d_tcf = nullptr;
-  void *d_G = nullptr, *d_Phi = nullptr;
   double* d_Facc = nullptr;
-  int64_t G_stride = 0, Phi_stride = 0, Facc_stride = 0;
+  int64_t smem_g_elems = 0, smem_phi_elems = 0, Facc_stride = 0;
   int cur = 0;
   int64_t step = 0;
   bool stats_on = false;
@@ -314,11 +314,6 @@ ugks_status build_typed(ugks_ctx* ctx, const std::vector<CellFace>& cf, const st
     CUDA_TRY(ctx, dalloc(ctx, &f, fsz));
     ctx->d_f[s] = f;
   }
-  T *G, *Phi;
-  CUDA_TRY(ctx, dalloc(ctx, &G, size_t(ctx->ntiles) * ctx->G_stride * sizeof(T)));
-  CUDA_TRY(ctx, dalloc(ctx, &Phi, size_t(ctx->ntiles) * ctx->Phi_stride * sizeof(T)));
-  ctx->d_G = G;
-  ctx->d_Phi = Phi;
   return UGKS_OK;
 }
 
@@ -378,16 +373,15 @@ ugks_status step_typed(ugks_ctx* ctx) {
   a.tf_off = ctx->d_tf_off;
   a.tf = ctx->d_tf;
   a.tcf = ctx->d_tcf;
-  a.G = static_cast<T*>(ctx->d_G);
-  a.Phi = static_cast<T*>(ctx->d_Phi);
+  a.ntiles = ctx->ntiles;
+  a.smem_g_elems = ctx->smem_g_elems;
+  a.smem_phi_elems = ctx->smem_phi_elems;
   a.Facc = ctx->d_Facc;
-  a.G_stride = ctx->G_stride;
-  a.Phi_stride = ctx->Phi_stride;
   a.Facc_stride = ctx->Facc_stride;
   a.res_acc = ctx->d_res_acc;
   a.status = ctx->d_status;
   record_start(ctx, 2, &ev);
-  CUDA_TRY(ctx, launch_sweep<T>(ctx->stream, a, ctx->ntiles, ctx->threads));
+  CUDA_TRY(ctx, launch_sweep<T>(ctx->stream, a, ctx->grid, ctx->threads, ctx->smem_bytes));
   record_stop(ctx, 2, ev);
   record_start(ctx, 3, &ev);
   launch_residual_finalize(ctx->stream, ctx->D + 2, ctx->Nc, ctx->d_res_acc, ctx->d_res);
@@ -399,16 +393,14 @@ ugks_status step_typed(ugks_ctx* ctx) {
 }
 
 
-// Variant of step_typed whose sweep takes its gradient, micro-flux and
-// face-accumulator scratch from the file-scope device array of ugks_sweep.cu
-// instead of the context's own buffers; it records no timing events.
+// Variant of step_typed whose sweep takes its face-accumulator scratch from
+// the file-scope device array of ugks_sweep.cu instead of the context's own
+// buffer; it records no timing events.
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 template <typename T>
 size_t static_scratch_need(const ugks_ctx* ctx) {
-  return align256(size_t(ctx->ntiles) * ctx->G_stride * sizeof(T)) +
-         align256(size_t(ctx->ntiles) * ctx->Phi_stride * sizeof(T)) +
-         align256(size_t(ctx->ntiles) * ctx->Facc_stride * sizeof(double));
+  return align256(size_t(ctx->ntiles) * ctx->Facc_stride * sizeof(double));
 }
 
 template <typename T>
@@ -422,8 +414,6 @@ ugks_status step_typed_static(ugks_ctx* ctx, unsigned char* base) {
                  ctx->d_fnormal, ctx->d_fcent, ctx->d_fshift, ctx->d_xc, ctx->d_bcs,
                  static_cast<FaceRec<T>*>(ctx->d_fr));
   CUDA_TRY(ctx, cudaGetLastError());
-  const size_t g_bytes = align256(size_t(ctx->ntiles) * ctx->G_stride * sizeof(T));
-  const size_t p_bytes = align256(size_t(ctx->ntiles) * ctx->Phi_stride * sizeof(T));
   SweepArgs<T> a;
   a.g = ctx->gas;
   a.Nc = ctx->Nc;
@@ -453,15 +443,14 @@ ugks_status step_typed_static(ugks_ctx* ctx, unsigned char* base) {
   a.tf_off = ctx->d_tf_off;
   a.tf = ctx->d_tf;
   a.tcf = ctx->d_tcf;
-  a.G = reinterpret_cast<T*>(base);
-  a.Phi = reinterpret_cast<T*>(base + g_bytes);
-  a.Facc = reinterpret_cast<double*>(base + g_bytes + p_bytes);
-  a.G_stride = ctx->G_stride;
-  a.Phi_stride = ctx->Phi_stride;
+  a.ntiles = ctx->ntiles;
+  a.smem_g_elems = ctx->smem_g_elems;
+  a.smem_phi_elems = ctx->smem_phi_elems;
+  a.Facc = reinterpret_cast<double*>(base);
   a.Facc_stride = ctx->Facc_stride;
   a.res_acc = ctx->d_res_acc;
   a.status = ctx->d_status;
-  CUDA_TRY(ctx, launch_sweep<T>(ctx->stream, a, ctx->ntiles, ctx->threads));
+  CUDA_TRY(ctx, launch_sweep<T>(ctx->stream, a, ctx->grid, ctx->threads, ctx->smem_bytes));
   launch_residual_finalize(ctx->stream, ctx->D + 2, ctx->Nc, ctx->d_res_acc, ctx->d_res);
   CUDA_TRY(ctx, cudaGetLastError());
   ctx->cur = nxt;
@@ -627,64 +616,99 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
   }
 
   // ---- tiles of the sweep ----
-  ctx->threads = 512;
+  // One CTA of 1024 threads per SM sweeps tiles b, b + grid, ...; a tile's
+  // gradients and micro fluxes for one velocity block must fit in shared
+  // memory, which fixes the smallest tile count.
+  ctx->threads = 1024;
   int dev = 0, nsm = 1;
   CUDA_TRY(ctx, cudaGetDevice(&dev));
   CUDA_TRY(ctx, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  int occ = ctx->storage == UGKS_STORAGE_F64 ? sweep_occupancy<double>(D, ctx->NR, ctx->threads)
-                                             : sweep_occupancy<float>(D, ctx->NR, ctx->threads);
-  CUDA_TRY(ctx, cudaGetLastError());
-  if (occ < 1) occ = 1;
-  int64_t ntiles = int64_t(nsm) * occ;
-  if (p->tile_cells > 0) ntiles = (Nc + p->tile_cells - 1) / p->tile_cells;
-  ntiles = std::max<int64_t>(1, std::min<int64_t>(ntiles, std::max<int64_t>(1, Nc / 16)));
-  ctx->ntiles = int(ntiles);
-  std::vector<int64_t> tile_begin(ntiles + 1);
-  for (int64_t t = 0; t <= ntiles; ++t) tile_begin[t] = (Nc * t) / ntiles;
-  std::vector<int64_t> gset_off(ntiles + 1, 0), gset, tf_off(ntiles + 1, 0);
+  int smem_optin = 0;
+  CUDA_TRY(ctx, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t elem = ctx->storage == UGKS_STORAGE_F64 ? sizeof(double) : sizeof(float);
+  const size_t smem_budget = size_t(std::max(0, smem_optin - 8 * 1024));
+  std::vector<int64_t> tile_begin, gset_off, gset, tf_off;
   std::vector<TileFace> tfl;
   std::vector<int32_t> tcf(cf.size(), 0);
   std::vector<int64_t> cell_mark(Nc, -1), cell_local(Nc, -1), face_mark(Nf, -1), face_local(Nf, -1);
-  int64_t max_ng = 1, max_nf = 1;
-  for (int64_t t = 0; t < ntiles; ++t) {
-    int64_t ng = 0;
-    for (int64_t c = tile_begin[t]; c < tile_begin[t + 1]; ++c) {
-      cell_mark[c] = t;
-      cell_local[c] = ng++;
-      gset.push_back(c);
+  int64_t max_ng = 1, max_nf = 1, ntiles = 0;
+  auto build_tiles = [&](int64_t nt_) {
+    tile_begin.assign(nt_ + 1, 0);
+    for (int64_t t = 0; t <= nt_; ++t) tile_begin[t] = (Nc * t) / nt_;
+    gset_off.assign(nt_ + 1, 0);
+    tf_off.assign(nt_ + 1, 0);
+    gset.clear();
+    tfl.clear();
+    std::fill(cell_mark.begin(), cell_mark.end(), -1);
+    std::fill(face_mark.begin(), face_mark.end(), -1);
+    max_ng = 1;
+    max_nf = 1;
+    for (int64_t t = 0; t < nt_; ++t) {
+      int64_t ng = 0;
+      for (int64_t c = tile_begin[t]; c < tile_begin[t + 1]; ++c) {
+        cell_mark[c] = t;
+        cell_local[c] = ng++;
+        gset.push_back(c);
+      }
+      for (int64_t c = tile_begin[t]; c < tile_begin[t + 1]; ++c)
+        for (int64_t e = cf_off[c]; e < cf_off[c + 1]; ++e) {
+          int64_t o = cf[e].other;
+          if (o >= 0 && cell_mark[o] != t) {
+            cell_mark[o] = t;
+            cell_local[o] = ng++;
+            gset.push_back(o);
+          }
+        }
+      int64_t nfl = 0;
+      for (int64_t c = tile_begin[t]; c < tile_begin[t + 1]; ++c)
+        for (int64_t e = cf_off[c]; e < cf_off[c + 1]; ++e) {
+          int64_t f = cf[e].face;
+          if (face_mark[f] != t) {
+            face_mark[f] = t;
+            face_local[f] = nfl++;
+            TileFace tfe;
+            tfe.face = f;
+            tfe.lo = int32_t(cell_local[fown[f]]);
+            tfe.ln = fnei[f] >= 0 ? int32_t(cell_local[fnei[f]]) : -1;
+            tfl.push_back(tfe);
+          }
+          tcf[e] = int32_t(face_local[f] << 1) | (cf[e].sign < 0 ? 1 : 0);
+        }
+      gset_off[t + 1] = gset_off[t] + ng;
+      tf_off[t + 1] = tf_off[t] + nfl;
+      max_ng = std::max(max_ng, ng);
+      max_nf = std::max(max_nf, nfl);
     }
-    for (int64_t c = tile_begin[t]; c < tile_begin[t + 1]; ++c)
-      for (int64_t e = cf_off[c]; e < cf_off[c + 1]; ++e) {
-        int64_t o = cf[e].other;
-        if (o >= 0 && cell_mark[o] != t) {
-          cell_mark[o] = t;
-          cell_local[o] = ng++;
-          gset.push_back(o);
-        }
-      }
-    int64_t nfl = 0;
-    for (int64_t c = tile_begin[t]; c < tile_begin[t + 1]; ++c)
-      for (int64_t e = cf_off[c]; e < cf_off[c + 1]; ++e) {
-        int64_t f = cf[e].face;
-        if (face_mark[f] != t) {
-          face_mark[f] = t;
-          face_local[f] = nfl++;
-          TileFace tfe;
-          tfe.face = f;
-          tfe.lo = int32_t(cell_local[fown[f]]);
-          tfe.ln = fnei[f] >= 0 ? int32_t(cell_local[fnei[f]]) : -1;
-          tfl.push_back(tfe);
-        }
-        tcf[e] = int32_t(face_local[f] << 1) | (cf[e].sign < 0 ? 1 : 0);
-      }
-    gset_off[t + 1] = gset_off[t] + ng;
-    tf_off[t + 1] = tf_off[t] + nfl;
-    max_ng = std::max(max_ng, ng);
-    max_nf = std::max(max_nf, nfl);
+  };
+  auto smem_need = [&]() {
+    return size_t(max_ng) * ctx->NR * D * BV * elem + size_t(max_nf) * ctx->NR * BV * elem;
+  };
+  if (p->tile_cells > 0) {
+    ntiles = std::max<int64_t>(1, (Nc + p->tile_cells - 1) / p->tile_cells);
+    build_tiles(ntiles);
+    if (smem_need() > smem_budget)
+      return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "tile_cells=%d needs %zu bytes of shared memory per tile (limit %zu)",
+                  p->tile_cells, smem_need(), smem_budget);
+  } else {
+    for (int64_t k = 1;; ++k) {
+      ntiles = std::min<int64_t>(int64_t(nsm) * k, Nc);
+      build_tiles(ntiles);
+      if (smem_need() <= smem_budget) break;
+      if (ntiles == Nc) return fail(ctx, UGKS_ERR_UNSUPPORTED, "cell stencil too large for shared memory");
+    }
   }
-  ctx->G_stride = max_ng * ctx->NR * D * BV;
-  ctx->Phi_stride = max_nf * ctx->NR * BV;
+  ctx->ntiles = int(ntiles);
+  ctx->smem_g_elems = max_ng * ctx->NR * D * BV;
+  ctx->smem_phi_elems = max_nf * ctx->NR * BV;
+  ctx->smem_bytes = smem_need();
   ctx->Facc_stride = max_nf * FACC_W;
+  int occ = ctx->storage == UGKS_STORAGE_F64
+                ? sweep_occupancy<double>(D, ctx->NR, ctx->threads, ctx->smem_bytes)
+                : sweep_occupancy<float>(D, ctx->NR, ctx->threads, ctx->smem_bytes);
+  CUDA_TRY(ctx, cudaGetLastError());
+  if (occ < 1) return fail(ctx, UGKS_ERR_UNSUPPORTED, "the sweep kernel cannot be resident with %zu bytes of shared memory",
+                           ctx->smem_bytes);
+  ctx->grid = int(std::min<int64_t>(ntiles, int64_t(nsm) * occ));
 
   // ---- gas ----
   Gas& g = ctx->gas;

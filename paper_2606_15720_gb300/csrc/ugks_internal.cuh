@@ -34,9 +34,10 @@ struct CellFace {
   int32_t bc_type; // 0 interior, else UGKS_BC_*
 };
 
-// Same entry in the storage/compute precision of the sweep kernel.
+// Same entry in the storage/compute precision of the sweep kernel (16-byte
+// aligned so that a copy to registers is a few vector loads).
 template <typename T>
-struct CellFaceT {
+struct __align__(16) CellFaceT {
   T w[3];
   T r[3];
   T area;
@@ -47,7 +48,7 @@ struct CellFaceT {
 
 // Constant per-face geometry in the sweep precision.
 template <typename T>
-struct FaceGeom {
+struct __align__(16) FaceGeom {
   T n[3];          // unit normal owner -> neighbour
   T rl[3];         // face centroid - owner centroid
   T rr[3];         // face centroid - neighbour centroid (neighbour's frame), or 0
@@ -62,7 +63,7 @@ struct FaceGeom {
 // slopes.  Wall faces: the unit-density wall Maxwellian (rho_pref, U, lam,
 // kappa) and zero elsewhere.
 template <typename T>
-struct FaceRec {
+struct __align__(16) FaceRec {
   T G[5];          // integrals of c1..c5 over [0, dt]
   T rho_pref;      // rho0 (lambda0/pi)^(D/2)
   T lam;           // lambda0

@@ -68,19 +68,20 @@ struct SweepArgs {
   const int64_t* tf_off;         // [ntiles+1]
   const TileFace* tf;            // tile faces
   const int32_t* tcf;            // per cell incidence as local tile-face index << 1 | (sign < 0)
-  T* G;                          // per-tile scratch: gradients [gmax][NR][D][BV]
-  T* Phi;                        // per-tile scratch: micro fluxes [fmax][NR][BV]
+  int ntiles;                    // tiles; CTA b sweeps tiles b, b + gridDim.x, ...
+  int64_t smem_g_elems;          // shared memory: gradients [gmax][NR][D][BV]
+  int64_t smem_phi_elems;        // shared memory: micro fluxes [fmax][NR][BV]
   double* Facc;                  // per-tile scratch: face accumulators [fmax][FACC_W]
-  int64_t G_stride, Phi_stride, Facc_stride;
+  int64_t Facc_stride;
   double* res_acc;               // [NWP] sum of squared W increments
   int* status;
 };
 
 template <typename T>
-cudaError_t launch_sweep(cudaStream_t s, const SweepArgs<T>& a, int ntiles, int threads);
+cudaError_t launch_sweep(cudaStream_t s, const SweepArgs<T>& a, int grid, int threads, size_t smem_bytes);
 
 template <typename T>
-int sweep_occupancy(int D, int NR, int threads);
+int sweep_occupancy(int D, int NR, int threads, size_t smem_bytes);
 
 // Size of the file-scope device scratch used by ugks_step_static_scratch.
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB

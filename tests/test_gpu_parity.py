@@ -182,7 +182,7 @@ def test_tiling_does_not_change_the_result(U):
     W0 = I.prim_to_conservative(prim, 3, 0)
     for storage in ("f64", "f32"):
         outs = []
-        for tc in (16, 97, 100000):
+        for tc in (16, 97, 0):
             with U.Solver(mesh, grid, gas, W0, storage=storage, tile_cells=tc) as s:
                 s.step(4)
                 outs.append(s.moments())
