@@ -194,6 +194,18 @@ def run_reference(args):
     return 0
 
 
+def count_launches(stats):
+    """Kernel launches of the library in the timed region, from its per-region
+    event counts (velocity_block_sweep of the blocked sweep spans several
+    kernels; conserve is two kernels)."""
+    if stats.get("block_fluxes", (0, 0))[1]:
+        per = {"cell_stage": 1, "face_stage": 1, "block_reconstruction": 1, "block_fluxes": 1, "block_stage1": 1,
+               "conserve": 2, "stage2": 1, "residual": 1}
+    else:
+        per = {"cell_stage": 1, "face_stage": 1, "velocity_block_sweep": 1, "residual": 1}
+    return int(sum(per.get(k, 0) * n for k, (_, n) in stats.items()))
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -216,7 +228,8 @@ def run_gpu(args):
             dist.barrier()
 
     with torch.cuda.stream(stream):
-        solver = U.Solver(mesh, grid, gas, W0, storage="f32", stream=int(stream.cuda_stream))
+        solver = U.Solver(mesh, grid, gas, W0, storage="f32", stream=int(stream.cuda_stream), sweep=args.sweep,
+                          block_velocities=args.block_velocities)
         assert solver.n_reduced == n_reduced
         solver.step(args.warmup)
         solver.residual()
@@ -261,7 +274,8 @@ def run_gpu(args):
         e2e = None
     barrier()
     t0 = time.perf_counter()
-    W_e2e, res_e2e = U.solve(mesh, grid, gas, W0, args.steps if not args.no_e2e else 0, storage="f32")
+    W_e2e, res_e2e = U.solve(mesh, grid, gas, W0, args.steps if not args.no_e2e else 0, storage="f32",
+                             sweep=args.sweep, block_velocities=args.block_velocities)
     e2e_s = time.perf_counter() - t0
     barrier()
     in_bytes = sum(a.nbytes for a in (mesh.cell_volume, mesh.cell_centroid, mesh.face_owner, mesh.face_neighbor,
@@ -290,11 +304,12 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
             "config": {"workload": workload, "n_cells": mesh.n_cells, "n_faces": mesh.n_faces, "n_v": grid.n_v,
                        "n_reduced": n_reduced, "dof_per_step": dof, "parallelism": f"replicas x{world}",
+                       "sweep": args.sweep, "block_velocities": args.block_velocities,
                        "l2": "inputs larger than L2 (two %.1f GB distribution buffers)" % (dof * 4 / 1e9),
                        "state_after": {"residual": [float(x) for x in res],
                                        "finite": bool(np.all(np.isfinite(W_end)))}},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(sum(n for _, n in stats.values())),
+            "gpu_launches": count_launches(stats),
             "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in stats.items()},
             "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -313,6 +328,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cells", type=int, default=MESH_CELLS, help="mesh size (profiling runs only)")
     ap.add_argument("--nv-axis", type=int, default=NV_AXIS, help="velocities per axis (profiling runs only)")
+    ap.add_argument("--sweep", default="auto", choices=["auto", "blocked", "tiled"])
+    ap.add_argument("--block-velocities", type=int, default=0, choices=[0, 32, 64, 128])
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

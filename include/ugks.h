@@ -54,6 +54,7 @@ enum { UGKS_BC_WALL = 1, UGKS_BC_FARFIELD = 2, UGKS_BC_OUTFLOW = 3 };
 enum { UGKS_MODEL_BGK = 0, UGKS_MODEL_SHAKHOV = 1 };
 enum { UGKS_LIMITER_NONE = 0, UGKS_LIMITER_VENKATAKRISHNAN = 1, UGKS_LIMITER_BARTH_JESPERSEN = 2 };
 enum { UGKS_STORAGE_F64 = 0, UGKS_STORAGE_F32 = 1, UGKS_STORAGE_F16 = 2, UGKS_STORAGE_BF16 = 3 };
+enum { UGKS_SWEEP_AUTO = 0, UGKS_SWEEP_TILED = 1, UGKS_SWEEP_BLOCKED = 2 };
 
 /* Boundary condition of the faces whose neighbour is -(index+1).
  * WALL: diffuse isothermal wall (Sec. 2.1, Eq. 36-38) with wall velocity u
@@ -110,7 +111,14 @@ typedef struct {
  *   limiter: slope limiter of the least-squares reconstruction, venkat_K its constant
  *   shock_tau_fix: add dt |p_l - p_r| / (p_l + p_r) to the interface relaxation time
  *   storage: precision of the stored distribution (F64, F32 supported)
- *   tile_cells: cells per device tile, 0 = automatic */
+ *   tile_cells: cells per tile of the tiled sweep, 0 = automatic
+ *   sweep: device organisation of the velocity-block sweep (Sec. 2.2.2,
+ *     Table B.1), UGKS_SWEEP_*: BLOCKED runs gradients, fluxes and the first
+ *     stage of each velocity block as three grid-wide kernels; TILED runs one
+ *     persistent kernel over spatial tiles held in shared memory; AUTO picks
+ *     BLOCKED.  Both give the same result up to rounding order.
+ *   block_velocities: velocities per block of the blocked sweep (32, 64 or
+ *     128; 0 = automatic) */
 typedef struct {
   int32_t model;
   int32_t K;
@@ -121,6 +129,8 @@ typedef struct {
   int32_t shock_tau_fix;
   int32_t storage;
   int32_t tile_cells;
+  int32_t sweep;
+  int32_t block_velocities;
 } ugks_params;
 
 /* Creates a solver context.  Copies mesh, grid and W_init (host,
@@ -142,9 +152,10 @@ ugks_status ugks_step(ugks_ctx *ctx, int32_t n_steps);
  * device-wide synchronisation that cudaMalloc / cudaFree can imply is not
  * acceptable.  The paper has no counterpart; this is an interface addition.
  * It advances n_steps >= 0 steps exactly like ugks_step, with the context's
- * own inputs and outputs, but the velocity-block sweep's gradient,
- * micro-flux and face-accumulator scratch lives in one file-scope device
- * array of 16 MiB that every GPU loading this library holds until exit.  It
+ * own inputs and outputs, but the velocity-block sweep's scratch (blocked
+ * sweep: the gradients and micro fluxes of one block and the face
+ * accumulators; tiled sweep: the face accumulators) lives in one file-scope
+ * device array of 16 MiB that every GPU loading this library holds until exit.  It
  * calls no cudaMalloc, cudaFree or other allocating routine.  The first call
  * on a device looks up that array's device address (cudaGetSymbolAddress,
  * once per device); make that first call before any stream capture.  All

@@ -1,0 +1,6 @@
+// double instantiation of the block-parallel velocity sweep (ugks_blocked.cuh).
+#include "ugks_blocked.cuh"
+
+namespace ugks {
+UGKS_INSTANTIATE_BLOCKED(double)
+}  // namespace ugks

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -28,8 +29,15 @@ struct KernelTiming {
   cudaEvent_t start, stop;
 };
 
-const char* const kKernelNames[] = {"cell_stage", "face_stage", "velocity_block_sweep", "residual"};
-constexpr int kNumKernels = 4;
+// Timed regions of ugks_stats.  velocity_block_sweep is the whole sweep (the
+// persistent kernel of the tiled sweep; every block kernel plus the
+// conservative update and the second stage of the blocked sweep); the
+// block_* entries and the two after them split the blocked sweep by kernel.
+const char* const kKernelNames[] = {"cell_stage",   "face_stage",   "velocity_block_sweep",
+                                    "residual",     "block_reconstruction", "block_fluxes",
+                                    "block_stage1", "conserve",     "stage2"};
+constexpr int kNumKernels = 9;
+enum { kTCell = 0, kTFace, kTSweep, kTRes, kTGrad, kTFlux, kTStage1, kTConserve, kTStage2 };
 
 }  // namespace
 
@@ -59,10 +67,18 @@ struct ugks_ctx {
   BCDev* d_bcs = nullptr;
   // velocities
   double *d_u = nullptr, *d_wgt = nullptr, *d_ux = nullptr, *d_uy = nullptr, *d_uz = nullptr, *d_wp = nullptr;
-  void *d_uxT = nullptr, *d_uyT = nullptr, *d_uzT = nullptr, *d_wT = nullptr;
+  void *d_uxT = nullptr, *d_uyT = nullptr, *d_uzT = nullptr, *d_wT = nullptr, *d_velT = nullptr;
   // distributions
   void* d_f[2] = {nullptr, nullptr};
-  // tiles and scratch
+  // sweep organisation: 1 tiled, 2 blocked; velocities per lane of the blocked sweep
+  int variant = 2, vb = 1;
+  // blocked sweep: 32-bit incidence records, per-block scratch
+  int32_t* d_cf_off32 = nullptr;
+  void* d_inc = nullptr;
+  void* d_X = nullptr;
+  double *d_Facc_b = nullptr, *d_qpart = nullptr;
+  int nchunk = 1;
+  // tiles and scratch of the tiled sweep
   int ntiles = 0, grid = 0, threads = 1024;
   size_t smem_bytes = 0;
   int64_t *d_tile_begin = nullptr, *d_gset_off = nullptr, *d_gset = nullptr, *d_tf_off = nullptr;
@@ -74,8 +90,9 @@ struct ugks_ctx {
   int64_t step = 0;
   bool stats_on = false;
   std::vector<KernelTiming> timings;
-  double stat_ms[kNumKernels] = {0, 0, 0, 0};
-  int64_t stat_count[kNumKernels] = {0, 0, 0, 0};
+  std::vector<cudaEvent_t> event_pool;
+  double stat_ms[kNumKernels] = {};
+  int64_t stat_count[kNumKernels] = {};
   std::string err;
 };
 
@@ -127,6 +144,8 @@ void release(ugks_ctx* ctx) {
     cudaEventDestroy(t.stop);
   }
   ctx->timings.clear();
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  ctx->event_pool.clear();
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -229,6 +248,11 @@ ugks_status validate(const ugks_mesh* m, const ugks_vgrid* v, const ugks_params*
   if (p->storage != UGKS_STORAGE_F64 && p->storage != UGKS_STORAGE_F32)
     return fail(nullptr, UGKS_ERR_UNSUPPORTED, "storage precision %d not implemented", p->storage);
   if (p->tile_cells < 0) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "tile_cells must be >= 0");
+  if (p->sweep < UGKS_SWEEP_AUTO || p->sweep > UGKS_SWEEP_BLOCKED)
+    return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "unknown sweep %d", p->sweep);
+  if (p->block_velocities != 0 && p->block_velocities != 32 && p->block_velocities != 64 &&
+      p->block_velocities != 128)
+    return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "block_velocities must be 0, 32, 64 or 128");
   return UGKS_OK;
 }
 
@@ -237,21 +261,44 @@ size_t tsize() {
   return sizeof(T);
 }
 
+cudaEvent_t pooled_event(ugks_ctx* ctx) {
+  cudaEvent_t e = nullptr;
+  if (!ctx->event_pool.empty()) {
+    e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    e = nullptr;
+  }
+  return e;
+}
+
 void record_start(ugks_ctx* ctx, int id, cudaEvent_t* ev) {
   *ev = nullptr;
   if (!ctx->stats_on) return;
-  cudaEventCreate(ev);
-  cudaEventRecord(*ev, ctx->stream);
+  *ev = pooled_event(ctx);
+  if (*ev) cudaEventRecord(*ev, ctx->stream);
   (void)id;
 }
 
 void record_stop(ugks_ctx* ctx, int id, cudaEvent_t start) {
   if (!ctx->stats_on || !start) return;
-  cudaEvent_t stop;
-  cudaEventCreate(&stop);
+  cudaEvent_t stop = pooled_event(ctx);
+  if (!stop) {
+    ctx->event_pool.push_back(start);
+    return;
+  }
   cudaEventRecord(stop, ctx->stream);
   ctx->timings.push_back({id, start, stop});
 }
+
+// Scratch of the blocked sweep: the per-face buffer of one block, the face
+// accumulators, the heat-flux partial sums of the second stage.
+template <typename T>
+size_t blocked_X_bytes(const ugks_ctx* ctx) {
+  return size_t(ctx->Nf) * ctx->NR * ctx->vb * BV * sizeof(T);
+}
+size_t blocked_Facc_bytes(const ugks_ctx* ctx) { return size_t(ctx->Nf) * FACC_W * sizeof(double); }
+size_t blocked_qpart_bytes(const ugks_ctx* ctx) { return size_t(ctx->nchunk) * ctx->Nc * 3 * sizeof(double); }
 
 template <typename T>
 ugks_status build_typed(ugks_ctx* ctx, const std::vector<CellFace>& cf, const std::vector<double>& eps2,
@@ -305,9 +352,41 @@ ugks_status build_typed(ugks_ctx* ctx, const std::vector<CellFace>& cf, const st
   ctx->d_uyT = b;
   ctx->d_uzT = c;
   ctx->d_wT = w;
+  {
+    std::vector<Vel4<T>> vel(Mp);
+    for (size_t k = 0; k < Mp; ++k) vel[k] = Vel4<T>{tux[k], tuy[k], tuz[k], tw[k]};
+    Vel4<T>* dv;
+    CUDA_TRY(ctx, upload(ctx, &dv, vel.data(), Mp * sizeof(Vel4<T>)));
+    ctx->d_velT = dv;
+  }
   FaceRec<T>* fr;
   CUDA_TRY(ctx, dalloc(ctx, &fr, size_t(ctx->Nf) * sizeof(FaceRec<T>)));
   ctx->d_fr = fr;
+  if (ctx->variant == 2) {
+    std::vector<IncT<T>> inc(cf.size());
+    for (size_t e = 0; e < cf.size(); ++e) {
+      const CellFace& c = cf[e];
+      IncT<T>& r = inc[e];
+      for (int d = 0; d < 3; ++d) {
+        r.w[d] = T(c.w[d]);
+        r.r[d] = T(c.r[d]);
+        r.n[d] = c.sign > 0 ? T(fg64[c.face].n[d]) : -T(fg64[c.face].n[d]);
+      }
+      r.sarea = c.sign > 0 ? T(c.area) : -T(c.area);
+      r.face = int32_t(c.face);
+      r.other = int32_t(c.other);
+      r.bc = c.other < 0 ? int32_t(-c.other - 1) : -1;
+      r.flags = c.bc_type == UGKS_BC_WALL ? 1 : 0;
+    }
+    IncT<T>* di;
+    CUDA_TRY(ctx, upload(ctx, &di, inc.data(), inc.size() * sizeof(IncT<T>)));
+    ctx->d_inc = di;
+    T* X;
+    CUDA_TRY(ctx, dalloc(ctx, &X, blocked_X_bytes<T>(ctx)));
+    ctx->d_X = X;
+    CUDA_TRY(ctx, dalloc(ctx, &ctx->d_Facc_b, blocked_Facc_bytes(ctx)));
+    CUDA_TRY(ctx, dalloc(ctx, &ctx->d_qpart, blocked_qpart_bytes(ctx)));
+  }
   const size_t fsz = size_t(ctx->NR) * ctx->M * ctx->Nc * BV * sizeof(T);
   for (int s = 0; s < 2; ++s) {
     T* f;
@@ -328,6 +407,75 @@ ugks_status init_state_typed(ugks_ctx* ctx) {
   return UGKS_OK;
 }
 
+#define LAUNCH_TRY(ctx, call)                                                                     \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(ctx, UGKS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// The velocity-block sweep of Algorithm 5 as block kernels: for every block
+// of vb x 32 velocities gradients -> fluxes -> first stage, then the
+// conservative update and the second stage.  The last M mod vb blocks run
+// with one velocity per lane.
+template <typename T>
+ugks_status sweep_blocked(ugks_ctx* ctx, int cur, void* X, double* Facc, double* qpart) {
+  const int nxt = 1 - cur;
+  BlockedArgs<T> a;
+  a.g = ctx->gas;
+  a.Nc = int32_t(ctx->Nc);
+  a.Nf = int32_t(ctx->Nf);
+  a.M = ctx->M;
+  a.nv = ctx->nv;
+  a.f_cur = static_cast<const T*>(ctx->d_f[cur]);
+  a.f_next = static_cast<T*>(ctx->d_f[nxt]);
+  a.W_cur = ctx->d_W[cur];
+  a.W_next = ctx->d_W[nxt];
+  a.cp = ctx->d_cp[0];
+  a.cp_next = ctx->d_cp[1];
+  a.q_next = ctx->d_q[nxt];
+  a.vel = static_cast<const Vel4<T>*>(ctx->d_velT);
+  a.vol = ctx->d_vol;
+  a.eps2 = static_cast<const T*>(ctx->d_eps2);
+  a.cf_off = ctx->d_cf_off32;
+  a.inc = static_cast<const IncT<T>*>(ctx->d_inc);
+  a.fg = static_cast<const FaceGeom<T>*>(ctx->d_fg);
+  a.fr = static_cast<const FaceRec<T>*>(ctx->d_fr);
+  a.bcs = ctx->d_bcs;
+  a.X = static_cast<T*>(X);
+  a.Facc = Facc;
+  a.qpart = qpart;
+  a.nchunk = ctx->nchunk;
+  a.res_acc = ctx->d_res_acc;
+  a.status = ctx->d_status;
+  cudaStream_t s = ctx->stream;
+  cudaEvent_t ev_all, ev;
+  record_start(ctx, kTSweep, &ev_all);
+  const int64_t M = ctx->M;
+  int64_t m0 = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int vb = pass == 0 ? ctx->vb : 1;
+    for (; m0 + vb <= M; m0 += vb) {
+      record_start(ctx, kTGrad, &ev);
+      LAUNCH_TRY(ctx, launch_brecon<T>(s, a, m0, vb));
+      record_stop(ctx, kTGrad, ev);
+      record_start(ctx, kTFlux, &ev);
+      LAUNCH_TRY(ctx, launch_bflux<T>(s, a, m0, vb, m0 == 0 ? 1 : 0));
+      record_stop(ctx, kTFlux, ev);
+      record_start(ctx, kTStage1, &ev);
+      LAUNCH_TRY(ctx, launch_bstage1<T>(s, a, m0, vb));
+      record_stop(ctx, kTStage1, ev);
+    }
+  }
+  record_start(ctx, kTConserve, &ev);
+  LAUNCH_TRY(ctx, launch_bconserve<T>(s, a));
+  record_stop(ctx, kTConserve, ev);
+  record_start(ctx, kTStage2, &ev);
+  LAUNCH_TRY(ctx, launch_bstage2<T>(s, a));
+  record_stop(ctx, kTStage2, ev);
+  record_stop(ctx, kTSweep, ev_all);
+  return UGKS_OK;
+}
+
 template <typename T>
 ugks_status step_typed(ugks_ctx* ctx) {
   const int cur = ctx->cur, nxt = 1 - cur;
@@ -344,6 +492,17 @@ ugks_status step_typed(ugks_ctx* ctx) {
                  static_cast<FaceRec<T>*>(ctx->d_fr));
   CUDA_TRY(ctx, cudaGetLastError());
   record_stop(ctx, 1, ev);
+  if (ctx->variant == 2) {
+    ugks_status st = sweep_blocked<T>(ctx, cur, ctx->d_X, ctx->d_Facc_b, ctx->d_qpart);
+    if (st != UGKS_OK) return st;
+    record_start(ctx, kTRes, &ev);
+    launch_residual_finalize(ctx->stream, ctx->D + 2, ctx->Nc, ctx->d_res_acc, ctx->d_res);
+    CUDA_TRY(ctx, cudaGetLastError());
+    record_stop(ctx, kTRes, ev);
+    ctx->cur = nxt;
+    ctx->step++;
+    return UGKS_OK;
+  }
   SweepArgs<T> a;
   a.g = ctx->gas;
   a.Nc = ctx->Nc;
@@ -393,13 +552,16 @@ ugks_status step_typed(ugks_ctx* ctx) {
 }
 
 
-// Variant of step_typed whose sweep takes its face-accumulator scratch from
-// the file-scope device array of ugks_sweep.cu instead of the context's own
-// buffer; it records no timing events.
+// Variant of step_typed whose sweep takes its scratch (blocked sweep:
+// gradients, micro fluxes and face accumulators; tiled sweep: face
+// accumulators) from the file-scope device array of ugks_sweep.cu instead of
+// the context's own buffers; it records no timing events.
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 template <typename T>
 size_t static_scratch_need(const ugks_ctx* ctx) {
+  if (ctx->variant == 2)
+    return align256(blocked_X_bytes<T>(ctx)) + align256(blocked_Facc_bytes(ctx)) + align256(blocked_qpart_bytes(ctx));
   return align256(size_t(ctx->ntiles) * ctx->Facc_stride * sizeof(double));
 }
 
@@ -414,6 +576,21 @@ ugks_status step_typed_static(ugks_ctx* ctx, unsigned char* base) {
                  ctx->d_fnormal, ctx->d_fcent, ctx->d_fshift, ctx->d_xc, ctx->d_bcs,
                  static_cast<FaceRec<T>*>(ctx->d_fr));
   CUDA_TRY(ctx, cudaGetLastError());
+  if (ctx->variant == 2) {
+    unsigned char* X = base;
+    unsigned char* Facc = X + align256(blocked_X_bytes<T>(ctx));
+    unsigned char* qpart = Facc + align256(blocked_Facc_bytes(ctx));
+    const bool was_on = ctx->stats_on;
+    ctx->stats_on = false;
+    ugks_status st = sweep_blocked<T>(ctx, cur, X, reinterpret_cast<double*>(Facc), reinterpret_cast<double*>(qpart));
+    ctx->stats_on = was_on;
+    if (st != UGKS_OK) return st;
+    launch_residual_finalize(ctx->stream, ctx->D + 2, ctx->Nc, ctx->d_res_acc, ctx->d_res);
+    CUDA_TRY(ctx, cudaGetLastError());
+    ctx->cur = nxt;
+    ctx->step++;
+    return UGKS_OK;
+  }
   SweepArgs<T> a;
   a.g = ctx->gas;
   a.Nc = ctx->Nc;
@@ -615,7 +792,20 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
     wp[k] = v->weight[k];
   }
 
-  // ---- tiles of the sweep ----
+  // ---- organisation of the sweep ----
+  // The blocked sweep indexes cells, faces and incidences with 32 bits.
+  const bool fits32 = Nc < INT32_MAX && Nf < INT32_MAX && int64_t(cf.size()) < INT32_MAX;
+  ctx->variant = p->sweep == UGKS_SWEEP_TILED ? 1 : 2;
+  if (ctx->variant == 2 && !fits32) {
+    if (p->sweep == UGKS_SWEEP_BLOCKED)
+      return fail(ctx, UGKS_ERR_UNSUPPORTED, "the blocked sweep needs fewer than 2^31 cells, faces and incidences");
+    ctx->variant = 1;
+  }
+  ctx->vb = p->block_velocities > 0 ? p->block_velocities / BV : 2;
+  if (ctx->vb > ctx->M) ctx->vb = 1;
+  ctx->nchunk = int(std::min<int64_t>(ctx->M, 8));
+
+  // ---- tiles of the tiled sweep ----
   // One CTA of 1024 threads per SM sweeps tiles b, b + grid, ...; a tile's
   // gradients and micro fluxes for one velocity block must fit in shared
   // memory, which fixes the smallest tile count.
@@ -683,7 +873,9 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
   auto smem_need = [&]() {
     return size_t(max_ng) * ctx->NR * D * BV * elem + size_t(max_nf) * ctx->NR * BV * elem;
   };
-  if (p->tile_cells > 0) {
+  if (ctx->variant != 1) {
+    // no tiles
+  } else if (p->tile_cells > 0) {
     ntiles = std::max<int64_t>(1, (Nc + p->tile_cells - 1) / p->tile_cells);
     build_tiles(ntiles);
     if (smem_need() > smem_budget)
@@ -697,18 +889,21 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
       if (ntiles == Nc) return fail(ctx, UGKS_ERR_UNSUPPORTED, "cell stencil too large for shared memory");
     }
   }
-  ctx->ntiles = int(ntiles);
-  ctx->smem_g_elems = max_ng * ctx->NR * D * BV;
-  ctx->smem_phi_elems = max_nf * ctx->NR * BV;
-  ctx->smem_bytes = smem_need();
-  ctx->Facc_stride = max_nf * FACC_W;
-  int occ = ctx->storage == UGKS_STORAGE_F64
-                ? sweep_occupancy<double>(D, ctx->NR, ctx->threads, ctx->smem_bytes)
-                : sweep_occupancy<float>(D, ctx->NR, ctx->threads, ctx->smem_bytes);
-  CUDA_TRY(ctx, cudaGetLastError());
-  if (occ < 1) return fail(ctx, UGKS_ERR_UNSUPPORTED, "the sweep kernel cannot be resident with %zu bytes of shared memory",
-                           ctx->smem_bytes);
-  ctx->grid = int(std::min<int64_t>(ntiles, int64_t(nsm) * occ));
+  if (ctx->variant == 1) {
+    ctx->ntiles = int(ntiles);
+    ctx->smem_g_elems = max_ng * ctx->NR * D * BV;
+    ctx->smem_phi_elems = max_nf * ctx->NR * BV;
+    ctx->smem_bytes = smem_need();
+    ctx->Facc_stride = max_nf * FACC_W;
+    int occ = ctx->storage == UGKS_STORAGE_F64
+                  ? sweep_occupancy<double>(D, ctx->NR, ctx->threads, ctx->smem_bytes)
+                  : sweep_occupancy<float>(D, ctx->NR, ctx->threads, ctx->smem_bytes);
+    CUDA_TRY(ctx, cudaGetLastError());
+    if (occ < 1)
+      return fail(ctx, UGKS_ERR_UNSUPPORTED, "the sweep kernel cannot be resident with %zu bytes of shared memory",
+                  ctx->smem_bytes);
+    ctx->grid = int(std::min<int64_t>(ntiles, int64_t(nsm) * occ));
+  }
 
   // ---- gas ----
   Gas& g = ctx->gas;
@@ -788,13 +983,18 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
   CUDA_TRY(ctx, upload(ctx, &ctx->d_uy, uy.data(), Mp * sizeof(double)));
   CUDA_TRY(ctx, upload(ctx, &ctx->d_uz, uz.data(), Mp * sizeof(double)));
   CUDA_TRY(ctx, upload(ctx, &ctx->d_wp, wp.data(), Mp * sizeof(double)));
-  CUDA_TRY(ctx, upload(ctx, &ctx->d_tile_begin, tile_begin.data(), tile_begin.size() * sizeof(int64_t)));
-  CUDA_TRY(ctx, upload(ctx, &ctx->d_gset_off, gset_off.data(), gset_off.size() * sizeof(int64_t)));
-  CUDA_TRY(ctx, upload(ctx, &ctx->d_gset, gset.data(), gset.size() * sizeof(int64_t)));
-  CUDA_TRY(ctx, upload(ctx, &ctx->d_tf_off, tf_off.data(), tf_off.size() * sizeof(int64_t)));
-  CUDA_TRY(ctx, upload(ctx, &ctx->d_tf, tfl.data(), tfl.size() * sizeof(TileFace)));
-  CUDA_TRY(ctx, upload(ctx, &ctx->d_tcf, tcf.data(), tcf.size() * sizeof(int32_t)));
-  CUDA_TRY(ctx, dalloc(ctx, &ctx->d_Facc, size_t(ntiles) * ctx->Facc_stride * sizeof(double)));
+  if (ctx->variant == 1) {
+    CUDA_TRY(ctx, upload(ctx, &ctx->d_tile_begin, tile_begin.data(), tile_begin.size() * sizeof(int64_t)));
+    CUDA_TRY(ctx, upload(ctx, &ctx->d_gset_off, gset_off.data(), gset_off.size() * sizeof(int64_t)));
+    CUDA_TRY(ctx, upload(ctx, &ctx->d_gset, gset.data(), gset.size() * sizeof(int64_t)));
+    CUDA_TRY(ctx, upload(ctx, &ctx->d_tf_off, tf_off.data(), tf_off.size() * sizeof(int64_t)));
+    CUDA_TRY(ctx, upload(ctx, &ctx->d_tf, tfl.data(), tfl.size() * sizeof(TileFace)));
+    CUDA_TRY(ctx, upload(ctx, &ctx->d_tcf, tcf.data(), tcf.size() * sizeof(int32_t)));
+    CUDA_TRY(ctx, dalloc(ctx, &ctx->d_Facc, size_t(ntiles) * ctx->Facc_stride * sizeof(double)));
+  } else {
+    std::vector<int32_t> off32(cf_off.begin(), cf_off.end());
+    CUDA_TRY(ctx, upload(ctx, &ctx->d_cf_off32, off32.data(), off32.size() * sizeof(int32_t)));
+  }
 
   // ---- time step ----
   if (p->dt_override > 0.0) {
@@ -1028,8 +1228,8 @@ ugks_status ugks_stats_enable(ugks_ctx* ctx, int32_t on) {
   if (!ctx) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL context");
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   for (auto& t : ctx->timings) {
-    cudaEventDestroy(t.start);
-    cudaEventDestroy(t.stop);
+    ctx->event_pool.push_back(t.start);
+    ctx->event_pool.push_back(t.stop);
   }
   ctx->timings.clear();
   for (int i = 0; i < kNumKernels; ++i) {
@@ -1048,8 +1248,8 @@ ugks_status ugks_stats(ugks_ctx* ctx, int32_t cap, const char** names, double* m
     CUDA_TRY(ctx, cudaEventElapsedTime(&e, t.start, t.stop));
     ctx->stat_ms[t.id] += e;
     ctx->stat_count[t.id]++;
-    cudaEventDestroy(t.start);
-    cudaEventDestroy(t.stop);
+    ctx->event_pool.push_back(t.start);
+    ctx->event_pool.push_back(t.stop);
   }
   ctx->timings.clear();
   for (int i = 0; i < kNumKernels && i < cap; ++i) {

@@ -77,6 +77,26 @@ struct __align__(16) FaceRec {
   T pad[2];
 };
 
+// One velocity of the padded grid and its quadrature weight, loaded by one
+// vector access in the blocked sweep.
+template <typename T>
+struct __align__(16) Vel4 {
+  T x, y, z, w;
+};
+
+// Per-cell incidence entry of the blocked sweep, in the sweep precision.
+template <typename T>
+struct __align__(16) IncT {
+  T w[3];          // least-squares weight M^-1 d (zero for walls)
+  T r[3];          // face centroid minus cell centroid (the cell's frame)
+  T n[3];          // unit normal pointing out of the cell
+  T sarea;         // +area on the owner side, -area on the neighbour side
+  int32_t face;    // global face index
+  int32_t other;   // neighbour cell, or -(bc+1)
+  int32_t bc;      // -1 interior, else bc index
+  int32_t flags;   // bit 0: wall
+};
+
 struct BCDev {
   int32_t type;
   int32_t pad;

@@ -1,5 +1,5 @@
-// Host-side launchers of the UGKS kernels (implemented in ugks_prep.cu and
-// ugks_sweep.cu), called by the C ABI in ugks_capi.cu.
+// Host-side launchers of the UGKS kernels (implemented in ugks_prep.cu,
+// ugks_sweep.cu and ugks_blocked_*.cu), called by the C ABI in ugks_capi.cu.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -82,6 +82,48 @@ cudaError_t launch_sweep(cudaStream_t s, const SweepArgs<T>& a, int grid, int th
 
 template <typename T>
 int sweep_occupancy(int D, int NR, int threads, size_t smem_bytes);
+
+// Arguments of the block-parallel sweep (ugks_blocked.cuh).  Cell and face
+// indices are 32-bit inside these kernels (checked at create time).
+template <typename T>
+struct BlockedArgs {
+  Gas g;
+  int32_t Nc, Nf;
+  int64_t M, nv;
+  const T* f_cur;                // f^n        [NR][M][Nc][BV]
+  T* f_next;                     // f~ then f^{n+1}
+  const double* W_cur;           // [Nc][NWP]
+  double* W_next;
+  const CellPrim* cp;            // primitive record of W^n (with q^n)
+  CellPrim* cp_next;             // primitive record of W^{n+1}
+  double* q_next;                // [Nc][3] heat flux of f^{n+1}
+  const Vel4<T>* vel;            // [M*BV] velocities and weights (padded: zero)
+  const double* vol;
+  const T* eps2;                 // limiter constant (K_v |Omega|^(1/D))^3 per cell
+  const int32_t* cf_off;         // per cell incidence CSR
+  const IncT<T>* inc;
+  const FaceGeom<T>* fg;
+  const FaceRec<T>* fr;
+  const BCDev* bcs;
+  T* X;                          // per face, one block [Nf][NR][VB][BV]: the upwind
+                                 // reconstruction, then the micro flux
+  double* Facc;                  // face accumulators [Nf][FACC_W]
+  double* qpart;                 // heat-flux partial sums [nchunk][Nc][3]
+  int nchunk;                    // velocity chunks of the second stage
+  double* res_acc;               // [NWP] sum of squared W increments
+  int* status;
+};
+
+template <typename T>
+cudaError_t launch_brecon(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb);
+template <typename T>
+cudaError_t launch_bflux(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb, int first);
+template <typename T>
+cudaError_t launch_bstage1(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb);
+template <typename T>
+cudaError_t launch_bconserve(cudaStream_t s, const BlockedArgs<T>& a);
+template <typename T>
+cudaError_t launch_bstage2(cudaStream_t s, const BlockedArgs<T>& a);
 
 // Size of the file-scope device scratch used by ugks_step_static_scratch.
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB

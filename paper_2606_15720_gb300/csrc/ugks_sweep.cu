@@ -27,89 +27,11 @@
 #include <cstdint>
 #include <mutex>
 
+#include "ugks_device.cuh"
 #include "ugks_internal.cuh"
 #include "ugks_kernels.cuh"
 
 namespace ugks {
-
-namespace {
-
-template <typename T>
-__device__ __forceinline__ T t_exp(T x);
-template <>
-__device__ __forceinline__ float t_exp<float>(float x) {
-  return __expf(x);
-}
-template <>
-__device__ __forceinline__ double t_exp<double>(double x) {
-  return exp(x);
-}
-
-// (lambda/pi)^(D/2)
-template <int D, typename T>
-__device__ __forceinline__ T maxwell_pref(T lam) {
-  T s = lam * T(0.31830988618379067154);
-  if (D == 1) return sqrt(s);
-  if (D == 2) return s;
-  return s * sqrt(s);
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ size_t frow(int r, int64_t m, int64_t c, int64_t M, int64_t Nc) {
-  return ((size_t(r) * size_t(M) + size_t(m)) * size_t(Nc) + size_t(c)) * BV;
-}
-
-// Selects component t (0..4) of five warp-uniform values without local memory.
-template <typename T>
-__device__ __forceinline__ T pick5(int t, T a0, T a1, T a2, T a3, T a4) {
-  return t == 0 ? a0 : t == 1 ? a1 : t == 2 ? a2 : t == 3 ? a3 : a4;
-}
-
-}  // namespace
-
-// Sums eight per-lane values over the warp with a transposed butterfly (9
-// shuffles instead of 5 per value): afterwards lane L holds the total of value
-// number ((L >> 4) & 1) * 4 + ((L >> 3) & 1) * 2 + ((L >> 2) & 1).
-template <typename T>
-__device__ __forceinline__ T warp_sum8(T v0, T v1, T v2, T v3, T v4, T v5, T v6, T v7, int lane) {
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-  T a0 = (b4 ? v4 : v0) + __shfl_xor_sync(0xffffffffu, b4 ? v0 : v4, 16);
-  T a1 = (b4 ? v5 : v1) + __shfl_xor_sync(0xffffffffu, b4 ? v1 : v5, 16);
-  T a2 = (b4 ? v6 : v2) + __shfl_xor_sync(0xffffffffu, b4 ? v2 : v6, 16);
-  T a3 = (b4 ? v7 : v3) + __shfl_xor_sync(0xffffffffu, b4 ? v3 : v7, 16);
-  T c0 = (b3 ? a2 : a0) + __shfl_xor_sync(0xffffffffu, b3 ? a0 : a2, 8);
-  T c1 = (b3 ? a3 : a1) + __shfl_xor_sync(0xffffffffu, b3 ? a1 : a3, 8);
-  T d0 = (b2 ? c1 : c0) + __shfl_xor_sync(0xffffffffu, b2 ? c0 : c1, 4);
-  d0 += __shfl_xor_sync(0xffffffffu, d0, 2);
-  d0 += __shfl_xor_sync(0xffffffffu, d0, 1);
-  return d0;
-}
-
-template <typename T>
-__device__ __forceinline__ T energy_in(int, T wi, T u2, T phi_h, T phi_b) {
-  return T(0.5) * wi * (u2 * phi_h + phi_b);
-}
-
-__device__ __forceinline__ int sum8_index(int lane) {
-  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-}
-
-template <typename T>
-__device__ __forceinline__ T fast_div(T a, T b);
-template <>
-__device__ __forceinline__ float fast_div<float>(float a, float b) {
-  return __fdividef(a, b);
-}
-template <>
-__device__ __forceinline__ double fast_div<double>(double a, double b) {
-  return a / b;
-}
 
 template <int D, int NR, typename T>
 __global__ void __launch_bounds__(1024, 1) k_sweep(SweepArgs<T> a) {

@@ -18,6 +18,7 @@ from . import build as _build
 from .inputs import LIMITERS, MODELS, Gas, Mesh, VelocityGrid
 
 STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+SWEEP = {"auto": 0, "tiled": 1, "blocked": 2}
 STATUS = {0: "UGKS_OK", 1: "UGKS_ERR_INVALID_ARGUMENT", 2: "UGKS_ERR_MESH", 3: "UGKS_ERR_VGRID",
           4: "UGKS_ERR_OUT_OF_MEMORY", 5: "UGKS_ERR_CUDA", 6: "UGKS_ERR_NONFINITE", 7: "UGKS_ERR_TIMEOUT",
           8: "UGKS_ERR_UNSUPPORTED"}
@@ -53,7 +54,8 @@ class ugks_params(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("K", ctypes.c_int32), ("Pr", ctypes.c_double),
                 ("omega", ctypes.c_double), ("mu_ref", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("dt_override", ctypes.c_double), ("limiter", ctypes.c_int32), ("venkat_K", ctypes.c_double),
-                ("shock_tau_fix", ctypes.c_int32), ("storage", ctypes.c_int32), ("tile_cells", ctypes.c_int32)]
+                ("shock_tau_fix", ctypes.c_int32), ("storage", ctypes.c_int32), ("tile_cells", ctypes.c_int32),
+                ("sweep", ctypes.c_int32), ("block_velocities", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -124,10 +126,12 @@ class _MeshArgs:
         self.grid = ugks_vgrid(grid.n_v, _ptr(self.u), _ptr(self.w))
 
 
-def make_params(gas: Gas, storage: str = "f32", tile_cells: int = 0) -> ugks_params:
+def make_params(gas: Gas, storage: str = "f32", tile_cells: int = 0, sweep: str = "auto",
+                block_velocities: int = 0) -> ugks_params:
     return ugks_params(MODELS[gas.model], int(gas.K), float(gas.Pr), float(gas.omega), float(gas.mu_ref),
                        float(gas.cfl), float(gas.dt), LIMITERS[gas.limiter], float(gas.venkat_K),
-                       int(bool(gas.shock_tau_fix)), STORAGE[storage], int(tile_cells))
+                       int(bool(gas.shock_tau_fix)), STORAGE[storage], int(tile_cells), SWEEP[sweep],
+                       int(block_velocities))
 
 
 def _check(lib, status: int, ctx=None):
@@ -151,12 +155,13 @@ class Solver:
     """One ugks_ctx: ugks_create / ugks_step / ugks_moments / ugks_residual."""
 
     def __init__(self, mesh: Mesh, grid: VelocityGrid, gas: Gas, W_init: Optional[np.ndarray] = None,
-                 storage: str = "f32", tile_cells: int = 0, stream: Optional[int] = None):
+                 storage: str = "f32", tile_cells: int = 0, stream: Optional[int] = None, sweep: str = "auto",
+                 block_velocities: int = 0):
         self._lib = load()
         self.mesh, self.grid, self.gas = mesh, grid, gas
         self.dim = mesh.dim
         args = _MeshArgs(mesh, grid)
-        prm = make_params(gas, storage, tile_cells)
+        prm = make_params(gas, storage, tile_cells, sweep, block_velocities)
         W = None if W_init is None else np.ascontiguousarray(W_init, dtype=np.float64)
         if W is not None and W.shape != (mesh.n_cells, mesh.dim + 2):
             raise ValueError("W_init must be [n_cells, dim+2]")
@@ -223,7 +228,7 @@ class Solver:
         self._c(self._lib.ugks_stats_enable(self._ctx, int(bool(on))))
 
     def stats(self) -> dict:
-        cap = 8
+        cap = 16
         names = (ctypes.c_char_p * cap)()
         ms = np.zeros(cap)
         cnt = np.zeros(cap, dtype=np.int64)
@@ -250,11 +255,11 @@ class Solver:
 
 
 def solve(mesh: Mesh, grid: VelocityGrid, gas: Gas, W_init: np.ndarray, n_steps: int, storage: str = "f32",
-          tile_cells: int = 0):
+          tile_cells: int = 0, sweep: str = "auto", block_velocities: int = 0):
     """ugks_solve: one call with host buffers (create, n steps, W and residual, destroy)."""
     lib = load()
     args = _MeshArgs(mesh, grid)
-    prm = make_params(gas, storage, tile_cells)
+    prm = make_params(gas, storage, tile_cells, sweep, block_velocities)
     W = np.ascontiguousarray(W_init, dtype=np.float64)
     Wout = np.zeros_like(W)
     res = np.zeros(mesh.dim + 2)

@@ -26,15 +26,17 @@ def _w_err(a, b):
     return float(max(e))
 
 
+@pytest.mark.parametrize("sweep", [dict(sweep="blocked", block_velocities=64), dict(sweep="tiled", tile_cells=48)],
+                         ids=["blocked", "tiled"])
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-11), ("f32", 1e-5)])
-def test_static_scratch_step_matches_ordinary_step_on_two_calls(storage, tol):
+def test_static_scratch_step_matches_ordinary_step_on_two_calls(storage, tol, sweep):
     from paper_2606_15720_gb300 import ugks as U
     mesh = I.cavity_mesh(16)
     grid = I.midpoint_grid(20, -4.5, 4.5, 2)
     gas = I.Gas(model="shakhov", Pr=2 / 3, omega=0.81, mu_ref=I.mu_ref_from_kn(0.075, 0.81), cfl=0.8)
     W0 = I.prim_to_conservative(I.smooth_random_primitives(mesh, seed=21, amp=0.1), 2, 0)
-    with U.Solver(mesh, grid, gas, W0, storage=storage, tile_cells=48) as ref, \
-            U.Solver(mesh, grid, gas, W0, storage=storage, tile_cells=48) as na:
+    with U.Solver(mesh, grid, gas, W0, storage=storage, **sweep) as ref, \
+            U.Solver(mesh, grid, gas, W0, storage=storage, **sweep) as na:
         for call in range(2):
             ref.step(3)
             na.step_static_scratch(3)
@@ -48,10 +50,12 @@ def test_static_scratch_step_matches_ordinary_step_on_two_calls(storage, tol):
 
 def test_static_scratch_step_rejects_contexts_beyond_its_size():
     from paper_2606_15720_gb300 import ugks as U
+    # blocked sweep, 64 velocities per block: its per-face buffer alone needs
+    # 131584 faces x 2 x 64 x 8 B = 135 MB
     mesh = I.cavity_mesh(256)
     grid = I.midpoint_grid(24, -4.5, 4.5, 2)
     gas = I.Gas(model="bgk", omega=0.81, mu_ref=I.mu_ref_from_kn(0.075, 0.81), cfl=0.8)
-    with U.Solver(mesh, grid, gas, None, storage="f64") as s:
+    with U.Solver(mesh, grid, gas, None, storage="f64", sweep="blocked", block_velocities=64) as s:
         with pytest.raises(U.UGKSError) as e:
             s.step_static_scratch(1)
         assert e.value.status == 1 and "static limit" in str(e.value)
