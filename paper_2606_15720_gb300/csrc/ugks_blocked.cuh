@@ -30,7 +30,9 @@
 // one warp, the block kernels are stream-ordered, partial sums are added in
 // a fixed order), so every result is bitwise reproducible.
 #pragma once
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 
 #include "ugks_device.cuh"
@@ -87,6 +89,55 @@ __device__ __forceinline__ void ghost_state(const BlockedArgs<T>& a, int bc_inde
     U[1] = T(bc.u[1]);
     U[2] = T(bc.u[2]);
   }
+}
+
+// Cubic in c (coefficients in mono_index order) by nested Horner: 3, 9 or 19 FMA.
+template <int D, typename T>
+__device__ __forceinline__ T horner_cubic(const T (&p)[NPoly<D>::value], T c0, T c1, T c2) {
+  if constexpr (D == 1) {
+    return fma(c0, fma(c0, fma(c0, p[3], p[2]), p[1]), p[0]);
+  } else if constexpr (D == 2) {
+    const T x0 = fma(c1, p[7], fma(c0, p[6], p[3]));
+    const T x1 = fma(c1, p[8], p[4]);
+    const T y0 = fma(c1, x1, fma(c0, x0, p[1]));
+    const T y1 = fma(c1, fma(c1, p[9], p[5]), p[2]);
+    return fma(c1, y1, fma(c0, y0, p[0]));
+  } else {
+    const T x0 = fma(c2, p[12], fma(c1, p[11], fma(c0, p[10], p[4])));
+    const T x1 = fma(c2, p[14], fma(c1, p[13], p[5]));
+    const T x2 = fma(c2, p[15], p[6]);
+    const T y0 = fma(c2, x2, fma(c1, x1, fma(c0, x0, p[1])));
+    const T z0 = fma(c2, p[17], fma(c1, p[16], p[7]));
+    const T z1 = fma(c2, p[18], p[8]);
+    const T y1 = fma(c2, z1, fma(c1, z0, p[2]));
+    const T y2 = fma(c2, fma(c2, p[19], p[9]), p[3]);
+    return fma(c2, y2, fma(c1, y1, fma(c0, y0, p[0])));
+  }
+}
+
+// Equilibrium record of one cell from its FP64 primitive record.
+template <int D, typename T>
+__device__ __forceinline__ CellEq<T> make_cell_eq(const Gas& g, const CellPrim& p, double vol) {
+  CellEq<T> e;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    e.U[d] = T(p.U[d]);
+    e.q[d] = T(p.q[d]);
+  }
+  e.lam = T(p.lam);
+  e.pref = T(p.rho * pow(p.lam / M_PI, 0.5 * D));
+  e.s0 = g.shakhov ? T(4.0 * (1.0 - g.Pr) * p.lam * p.lam / (5.0 * p.rho)) : T(0);
+  e.kap = T(g.Kxi / (2.0 * p.lam));
+  e.beta = T(g.dt / (2.0 * p.tau));
+  e.inv_vol = T(1.0 / vol);
+  return e;
+}
+
+template <int D, typename T>
+__global__ void k_bcelleq(const BlockedArgs<T> a) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.Nc) return;
+  a.ceq0[c] = make_cell_eq<D, T>(a.g, a.cp[c], a.vol[c]);
 }
 
 // ---------------------------------------------------------------------------
@@ -211,14 +262,20 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon(const BlockedArgs<T>
         }
     }
   }
+  T ug[NR][VB];  // u . (limited gradient), the same on every face
 #pragma unroll
   for (int r = 0; r < NR; ++r)
 #pragma unroll
     for (int j = 0; j < VB; ++j) {
       const T p = fmin(fmax(phi[r][j], T(0)), T(1));
+      ug[r][j] = T(0);
 #pragma unroll
-      for (int d = 0; d < D; ++d) g[r][j][d] *= p;
+      for (int d = 0; d < D; ++d) {
+        g[r][j][d] *= p;
+        ug[r][j] += v.u[j][d] * g[r][j][d];
+      }
     }
+  const FacePoly<D, NR, T>* FP = static_cast<const FacePoly<D, NR, T>*>(a.fpoly);
   // free-transport part on every face for which this cell is upwind
   const T dt = T(a.g.dt);
   const T hdt2 = T(0.5 * a.g.dt * a.g.dt);
@@ -238,8 +295,8 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon(const BlockedArgs<T>
         c0[i] = dt;
         c1[i] = -hdt2;
       } else {
-        c0[i] = a.fr[face[i]].G[0];
-        c1[i] = a.fr[face[i]].G[1];
+        c0[i] = FP[face[i]].G0;
+        c1[i] = FP[face[i]].G1;
       }
     }
 #pragma unroll
@@ -261,13 +318,10 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon(const BlockedArgs<T>
         if (un > T(0)) {
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
-            T ff = fc[r][j], ug = T(0);
+            T ff = fc[r][j];
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-              ff += g[r][j][d] * rr[d];
-              ug += v.u[j][d] * g[r][j][d];
-            }
-            Xf[(r * VB + j) * BV] = c0[i] * ff + c1[i] * ug;
+            for (int d = 0; d < D; ++d) ff += g[r][j][d] * rr[d];
+            Xf[(r * VB + j) * BV] = c0[i] * ff + c1[i] * ug[r][j];
           }
         }
       }
@@ -278,43 +332,84 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon(const BlockedArgs<T>
 // ---------------------------------------------------------------------------
 // K1: micro fluxes of one velocity block and their FP64 moments (Eq. 29,
 // 32-38, 52).  X holds the upwind free-transport part on entry and the flux
-// on exit.
+// on exit.  The kernel is persistent: each warp walks faces f, f + stride,
+// ... and stages the next face's records (FacePoly, FaceGeom), its X rows and
+// its accumulators into shared memory with cp.async while it computes the
+// current face, so the loads of one face overlap the arithmetic of the
+// previous one.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = unsigned(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Shared-memory stage of one face: [FacePoly][FaceGeom][X rows][accumulators].
 template <int D, int NR, int VB, typename T>
-__global__ void __launch_bounds__(kBlockedThreads) k_bflux(const BlockedArgs<T> a, const int64_t m0,
-                                                           const int first) {
+struct FluxStage {
+  static constexpr int SP = int(sizeof(FacePoly<D, NR, T>));
+  static constexpr int SG = int(sizeof(FaceGeom<T>));
+  static constexpr int SX = NR * VB * BV * int(sizeof(T));
+  static constexpr int SF = FACC_W * int(sizeof(double));
+  static constexpr int BYTES = SP + SG + SX + SF;
+  static_assert(SP % 16 == 0 && SG % 16 == 0 && SX % 16 == 0 && SF % 16 == 0, "16-byte stage pieces");
+};
+
+template <int D, int NR, int VB, typename T>
+__device__ __forceinline__ void flux_prefetch(const BlockedArgs<T>& a, int f, unsigned char* st, int lane) {
+  using S = FluxStage<D, NR, VB, T>;
+  const unsigned char* srcP = static_cast<const unsigned char*>(a.fpoly) + size_t(f) * S::SP;
+  const unsigned char* srcG = reinterpret_cast<const unsigned char*>(a.fg) + size_t(f) * S::SG;
+  const unsigned char* srcX = reinterpret_cast<const unsigned char*>(a.X) + size_t(f) * S::SX;
+  const unsigned char* srcF = reinterpret_cast<const unsigned char*>(a.Facc) + size_t(f) * S::SF;
+  for (int q = lane; q < S::BYTES / 16; q += 32) {
+    const int b = q * 16;
+    const unsigned char* src = b < S::SP                   ? srcP + b
+                               : b < S::SP + S::SG         ? srcG + (b - S::SP)
+                               : b < S::SP + S::SG + S::SX ? srcX + (b - S::SP - S::SG)
+                                                           : srcF + (b - S::SP - S::SG - S::SX);
+    cp_async16(st + b, src);
+  }
+}
+
+template <int D, int NR, int VB, typename T>
+__device__ __forceinline__ void flux_face(const BlockedArgs<T>& a, const int f, const unsigned char* st,
+                                          const BlockVel<D, NR, VB, T>& v, const int first, const int lane) {
+  using S = FluxStage<D, NR, VB, T>;
   constexpr int NW = D + 2;
-  const int lane = threadIdx.x & 31;
-  const int f = blockIdx.x * (kBlockedThreads / 32) + (threadIdx.x >> 5);
-  if (f >= a.Nf) return;
+  const FacePoly<D, NR, T>& R = *reinterpret_cast<const FacePoly<D, NR, T>*>(st);
+  const FaceGeom<T>& fg = *reinterpret_cast<const FaceGeom<T>*>(st + S::SP);
+  const T* Xs = reinterpret_cast<const T*>(st + S::SP + S::SG) + lane;
+  const double* Fs = reinterpret_cast<const double*>(st + S::SP + S::SG + S::SX);
   const int idx8 = sum8_index(lane);
   const bool writer = (lane & 3) == 0 && idx8 < NW;
   double* Fa = a.Facc + size_t(f) * FACC_W;
-  const double fold = (writer && !first) ? Fa[idx8] : 0.0;  // issued early, used at the end
   const T dt = T(a.g.dt);
-  BlockVel<D, NR, VB, T> v;
-  v.load(a, m0, lane);
-  const FaceGeom<T> fg = a.fg[f];
-  const FaceRec<T> R = a.fr[f];
   T* Xf = a.X + size_t(f) * (NR * VB * BV) + lane;
   T m_in[NWP], m_out[NWP];  // moments of the block, conservative variable order (energy at D + 1)
 #pragma unroll
   for (int t = 0; t < NWP; ++t) m_in[t] = m_out[t] = T(0);
+  T n[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) n[d] = fg.n[d];
 
   if (fg.bc_type == 1) {
     // diffuse wall (Eq. 36-38): free transport on the incoming side; the
     // re-emitted half is the unit-density wall Maxwellian, scaled by rho_w
     // once all blocks are summed.
-    const double fold_out = (writer && !first) ? Fa[5 + idx8] : 0.0;
 #pragma unroll
     for (int j = 0; j < VB; ++j) {
       T un = T(0);
 #pragma unroll
-      for (int d = 0; d < D; ++d) un += v.u[j][d] * fg.n[d];
+      for (int d = 0; d < D; ++d) un += v.u[j][d] * n[d];
       T phi_h = T(0), phi_b = T(0), out_h = T(0);
       if (un > T(0)) {
-        phi_h = un * Xf[(0 * VB + j) * BV];
-        if (NR == 2) phi_b = un * Xf[((NR - 1) * VB + j) * BV];
+        phi_h = un * Xs[(0 * VB + j) * BV];
+        if (NR == 2) phi_b = un * Xs[((NR - 1) * VB + j) * BV];
       } else if (un < T(0)) {
         T c2 = T(0);
 #pragma unroll
@@ -337,8 +432,8 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bflux(const BlockedArgs<T> 
     const T sin = warp_sum8<T>(m_in[0], m_in[1], m_in[2], m_in[3], m_in[4], T(0), T(0), T(0), lane);
     const T sout = warp_sum8<T>(m_out[0], m_out[1], m_out[2], m_out[3], m_out[4], T(0), T(0), T(0), lane);
     if (writer) {
-      Fa[idx8] = fold + double(sin);
-      Fa[5 + idx8] = fold_out + double(sout);
+      Fa[idx8] = (first ? 0.0 : Fs[idx8]) + double(sin);
+      Fa[5 + idx8] = (first ? 0.0 : Fs[5 + idx8]) + double(sout);
     }
     return;
   }
@@ -357,52 +452,31 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bflux(const BlockedArgs<T> 
   for (int j = 0; j < VB; ++j) {
     T un = T(0);
 #pragma unroll
-    for (int d = 0; d < D; ++d) un += v.u[j][d] * fg.n[d];
+    for (int d = 0; d < D; ++d) un += v.u[j][d] * n[d];
     T phi_h = T(0), phi_b = T(0);
     if (un != T(0)) {
       T tr[NR];
       if (un > T(0) || !ghost) {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) tr[r] = Xf[(r * VB + j) * BV];
+        for (int r = 0; r < NR; ++r) tr[r] = Xs[(r * VB + j) * BV];
       } else {
         T c2 = T(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) c2 += (v.u[j][d] - gU[d]) * (v.u[j][d] - gU[d]);
         const T H = gr * t_exp(-gl * c2);
-        tr[0] = R.G[0] * H;
-        if (NR == 2) tr[NR - 1] = R.G[0] * (gk * H);
+        tr[0] = R.G0 * H;
+        if (NR == 2) tr[NR - 1] = R.G0 * (gk * H);
       }
-      // equilibrium part: G2 (g0 + g0+) + G3 u.grad g0 + G4 d_t g0 (Eq. 32-33)
-      T c2 = T(0), cq = T(0);
+      // equilibrium part G2 (g0 + g0+) + G3 u.grad g0 + G4 d_t g0 = g0(u) P(c) (Eq. 32-33)
+      T c[3] = {T(0), T(0), T(0)}, c2 = T(0);
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        const T cd = v.u[j][d] - R.U[d];
-        c2 += cd * cd;
-        cq += cd * R.q[d];
+        c[d] = v.u[j][d] - R.U[d];
+        c2 += c[d] * c[d];
       }
       const T H0 = R.rho_pref * t_exp(-R.lam * c2);
-      const T sq = R.sq * cq;
-      const T twolc2 = T(2) * R.lam * c2;
-      const T h0 = H0 * (T(1) + sq * (twolc2 - T(2 + D)));
-      T ugH = T(0), ugB = T(0);
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        T poly = R.a[d][0] + T(0.5) * R.a[d][D + 1] * v.u2[j];
-#pragma unroll
-        for (int e = 0; e < D; ++e) poly += R.a[d][1 + e] * v.u[j][e];
-        ugH += v.u[j][d] * (poly + T(0.5) * R.a[d][D + 1] * R.kappa);
-        if (NR == 2) ugB += v.u[j][d] * (poly * R.kappa + T(0.5) * R.a[d][D + 1] * R.xi4);
-      }
-      T pA = R.A[0] + T(0.5) * R.A[D + 1] * v.u2[j];
-#pragma unroll
-      for (int e = 0; e < D; ++e) pA += R.A[1 + e] * v.u[j][e];
-      const T dtH = pA + T(0.5) * R.A[D + 1] * R.kappa;
-      phi_h = un * (tr[0] + R.G[2] * h0 + H0 * (R.G[3] * ugH + R.G[4] * dtH));
-      if (NR == 2) {
-        const T b0 = H0 * R.kappa * (T(1) + sq * (twolc2 - T(D)));
-        const T dtB = pA * R.kappa + T(0.5) * R.A[D + 1] * R.xi4;
-        phi_b = un * (tr[NR - 1] + R.G[2] * b0 + H0 * (R.G[3] * ugB + R.G[4] * dtB));
-      }
+      phi_h = un * fma(H0, horner_cubic<D, T>(R.P[0], c[0], c[1], c[2]), tr[0]);
+      if (NR == 2) phi_b = un * fma(H0, horner_cubic<D, T>(R.P[NR - 1], c[0], c[1], c[2]), tr[NR - 1]);
     }
     Xf[(0 * VB + j) * BV] = phi_h;
     if (NR == 2) Xf[((NR - 1) * VB + j) * BV] = phi_b;
@@ -414,7 +488,32 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bflux(const BlockedArgs<T> 
   }
   // value index t of the reduction is conservative variable t (energy at D + 1)
   const T sm = warp_sum8<T>(m_in[0], m_in[1], m_in[2], m_in[3], m_in[4], T(0), T(0), T(0), lane);
-  if (writer) Fa[idx8] = fold + double(sm);
+  if (writer) Fa[idx8] = (first ? 0.0 : Fs[idx8]) + double(sm);
+}
+
+template <int D, int NR, int VB, typename T>
+__global__ void __launch_bounds__(kBlockedThreads) k_bflux(const BlockedArgs<T> a, const int64_t m0,
+                                                           const int first) {
+  using S = FluxStage<D, NR, VB, T>;
+  extern __shared__ __align__(16) unsigned char flux_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* const st = flux_smem + warp * (2 * S::BYTES);
+  BlockVel<D, NR, VB, T> v;
+  v.load(a, m0, lane);
+  const int stride = gridDim.x * (kBlockedThreads / 32);
+  int f = blockIdx.x * (kBlockedThreads / 32) + warp;
+  if (f < a.Nf) flux_prefetch<D, NR, VB, T>(a, f, st, lane);
+  cp_async_commit();
+  for (int it = 0; f < a.Nf; f += stride, ++it) {
+    const int fn = f + stride;
+    if (fn < a.Nf) flux_prefetch<D, NR, VB, T>(a, fn, st + ((it + 1) & 1) * S::BYTES, lane);
+    cp_async_commit();
+    cp_async_wait<1>();  // this face's stage has landed
+    __syncwarp();
+    flux_face<D, NR, VB, T>(a, f, st + (it & 1) * S::BYTES, v, first, lane);
+    __syncwarp();        // all lanes done with the stage before it is refilled
+  }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -429,18 +528,8 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage1(const BlockedArgs<T
   const size_t base = size_t(m0) * sj + size_t(c) * BV + lane;
   BlockVel<D, NR, VB, T> v;
   v.load(a, m0, lane);
-  const T dt = T(a.g.dt);
-  const CellPrim& p = a.cp[c];
-  const T rho = T(p.rho), lam = T(p.lam), beta0 = dt / (T(2) * T(p.tau));
-  const T pref = rho * maxwell_pref<D>(lam);
-  const T s0 = a.g.shakhov ? T(4.0 * (1.0 - a.g.Pr)) * lam * lam / (T(5) * rho) : T(0);
-  const T kap = T(a.g.Kxi) / (T(2) * lam);
-  T Uc[3], qc[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    Uc[d] = T(p.U[d]);
-    qc[d] = T(p.q[d]);
-  }
+  const CellEq<T> E = a.ceq0[c];
+  const T lam = E.lam, beta0 = E.beta, pref = E.pref, s0 = E.s0, kap = E.kap;
   T flux[NR][VB];
 #pragma unroll
   for (int r = 0; r < NR; ++r)
@@ -472,15 +561,15 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage1(const BlockedArgs<T
 #pragma unroll
         for (int j = 0; j < VB; ++j) flux[r][j] += sa[i] * P[i][r][j];
   }
-  const T inv_vol = T(1.0 / a.vol[c]);
+  const T inv_vol = E.inv_vol;
 #pragma unroll
   for (int j = 0; j < VB; ++j) {
     T c2 = T(0), cq = T(0);
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      const T cd = v.u[j][d] - Uc[d];
+      const T cd = v.u[j][d] - E.U[d];
       c2 += cd * cd;
-      cq += cd * qc[d];
+      cq += cd * E.q[d];
     }
     const T H = pref * t_exp(-lam * c2);
     const T s = s0 * cq;
@@ -495,6 +584,363 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage1(const BlockedArgs<T
       a.f_next[idx] = v.real[j] ? ft : T(0);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined per-cell kernels (K2 and K3 on meshes with at most kEllMax faces
+// per cell).  Each warp walks cells c, c + stride, ...; per cell it needs
+// the cell's incidence records (an ELL table: W slots per cell, padding
+// flagged) and then rows addressed through them (neighbour or flux rows).
+// Both are staged into shared memory with cp.async: the records two cells
+// ahead, the rows one cell ahead, so the dependent loads of the next cells
+// overlap the arithmetic of the current one.
+// ---------------------------------------------------------------------------
+constexpr int kEllMax = 8;
+
+// cp.async of one 4- or 8-byte value.
+template <int N>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
+  static_assert(N == 4 || N == 8, "cp.async.ca copies 4, 8 or 16 bytes");
+  const unsigned s = unsigned(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(N) : "memory");
+}
+
+// Contiguous bytes (a multiple of 16) by all lanes of the warp.
+__device__ __forceinline__ void stage_bytes(unsigned char* dst, const void* src, int bytes, int lane) {
+  const unsigned char* s = static_cast<const unsigned char*>(src);
+  for (int q = lane; q < bytes / 16; q += 32) cp_async16(dst + q * 16, s + q * 16);
+}
+
+// The NR x VB rows (one per reduced distribution and sub-block) of cell c.
+template <int NR, int VB, typename T>
+__device__ __forceinline__ void stage_cell_rows(unsigned char* dst, const BlockedArgs<T>& a, int64_t m0, int c,
+                                                int lane) {
+  constexpr int CH = BV * int(sizeof(T)) / 16;  // 16-byte chunks per row
+  const size_t sj = size_t(a.Nc) * BV, sr = size_t(a.M) * sj;
+  for (int q = lane; q < NR * VB * CH; q += 32) {
+    const int row = q / CH, part = q % CH, r = row / VB, j = row % VB;
+    const T* src = a.f_cur + r * sr + (size_t(m0) + j) * sj + size_t(c) * BV;
+    cp_async16(dst + q * 16, reinterpret_cast<const unsigned char*>(src) + part * 16);
+  }
+}
+
+template <int NR, int VB, typename T>
+struct CellStage {
+  static constexpr int ROW = NR * VB * BV * int(sizeof(T));  // rows of one cell or one face
+  static constexpr int INC = int(sizeof(IncT<T>));
+};
+
+// Shared-memory bytes per warp of the pipelined kernels (3 record slots, 2 row slots).
+template <int NR, int VB, typename T>
+__host__ __device__ constexpr int recon_warp_bytes(int W) {
+  return 3 * (W * CellStage<NR, VB, T>::INC + 16) + 2 * ((W + 1) * CellStage<NR, VB, T>::ROW + W * 16);
+}
+template <int NR, int VB, typename T>
+__host__ __device__ constexpr int stage1_warp_bytes(int W) {
+  return 3 * (W * CellStage<NR, VB, T>::INC + int(sizeof(CellEq<T>))) + 2 * ((W + 1) * CellStage<NR, VB, T>::ROW);
+}
+
+// byte offset of the 16-byte chunk of a FacePoly that holds G0 and G1
+template <int D, int NR, typename T>
+__host__ __device__ constexpr int g01_chunk() {
+  using FP = FacePoly<D, NR, T>;
+  return (int(offsetof(FP, G0)) / 16) * 16;
+}
+
+template <int D, int NR, int VB, typename T>
+__global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<T> a, const int64_t m0) {
+  using CS = CellStage<NR, VB, T>;
+  using FP = FacePoly<D, NR, T>;
+  static_assert(offsetof(FP, G1) + sizeof(T) <= size_t(g01_chunk<D, NR, T>() + 16),
+                "G0 and G1 share one 16-byte chunk");
+  extern __shared__ __align__(16) unsigned char cell_smem[];
+  const int W = a.W;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int AB = W * CS::INC + 16, BB = (W + 1) * CS::ROW + W * 16;
+  unsigned char* const As = cell_smem + warp * recon_warp_bytes<NR, VB, T>(W);
+  unsigned char* const Bs = As + 3 * AB;
+  BlockVel<D, NR, VB, T> v;
+  v.load(a, m0, lane);
+  const int Kxi = a.g.Kxi, limiter = a.g.limiter;
+  const T dt = T(a.g.dt);
+  const T hdt2 = T(0.5 * a.g.dt * a.g.dt);
+  const int stride = gridDim.x * nwarps;
+  const int cbeg = blockIdx.x * nwarps + warp;
+
+  auto issueA = [&](int c, unsigned char* dst) {
+    stage_bytes(dst, a.ell + size_t(c) * W, W * CS::INC, lane);
+    if (lane == 0) cp_async_small<int(sizeof(T))>(dst + W * CS::INC, a.eps2 + c);
+  };
+  auto issueB = [&](int c, const unsigned char* A, unsigned char* dst) {
+    const IncT<T>* inc = reinterpret_cast<const IncT<T>*>(A);
+    for (int i = 0; i < W; ++i) {
+      const int fl = inc[i].flags;
+      if (fl & 3) continue;  // wall or padding: no neighbour row, no G0/G1
+      const int o = inc[i].other;
+      if (o >= 0) stage_cell_rows<NR, VB, T>(dst + i * CS::ROW, a, m0, o, lane);
+      if (lane == 0)
+        cp_async16(dst + (W + 1) * CS::ROW + i * 16,
+                   static_cast<const unsigned char*>(a.fpoly) + size_t(inc[i].face) * sizeof(FacePoly<D, NR, T>) +
+                       g01_chunk<D, NR, T>());
+    }
+    stage_cell_rows<NR, VB, T>(dst + W * CS::ROW, a, m0, c, lane);
+  };
+
+  if (cbeg < a.Nc) issueA(cbeg, As);
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncwarp();
+  if (cbeg < a.Nc) issueB(cbeg, As, Bs);
+  if (cbeg + stride < a.Nc) issueA(cbeg + stride, As + AB);
+  cp_async_commit();
+  int it = 0;
+  for (int c = cbeg; c < a.Nc; c += stride, ++it) {
+    cp_async_wait<0>();  // rows of c and records of c + stride have landed
+    __syncwarp();
+    const int cn = c + stride, cnn = c + 2 * stride;
+    if (cn < a.Nc) issueB(cn, As + ((it + 1) % 3) * AB, Bs + ((it + 1) & 1) * BB);
+    if (cnn < a.Nc) issueA(cnn, As + ((it + 2) % 3) * AB);
+    cp_async_commit();
+
+    const unsigned char* A = As + (it % 3) * AB;
+    const unsigned char* B = Bs + (it & 1) * BB;
+    const IncT<T>* inc = reinterpret_cast<const IncT<T>*>(A);
+    const T* rows = reinterpret_cast<const T*>(B) + lane;  // [W+1][NR][VB][BV]
+    const T* own = rows + W * (NR * VB * BV);
+    T fc[NR][VB], g[NR][VB][D], fmx[NR][VB], fmn[NR][VB];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int j = 0; j < VB; ++j) {
+        fc[r][j] = own[(r * VB + j) * BV];
+        fmx[r][j] = fmn[r][j] = fc[r][j];
+#pragma unroll
+        for (int d = 0; d < D; ++d) g[r][j][d] = T(0);
+      }
+    for (int i = 0; i < W; ++i) {
+      const int fl = inc[i].flags;
+      if (fl & 3) continue;  // walls: one-sided stencil; padding
+      T wd[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) wd[d] = inc[i].w[d];
+      T fo[NR][VB];
+      if (inc[i].other >= 0) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+#pragma unroll
+          for (int j = 0; j < VB; ++j) fo[r][j] = rows[(i * NR * VB + r * VB + j) * BV];
+      } else {
+        T rho, lam, U[3];
+        ghost_state<D, NR, T>(a, inc[i].bc, c, rho, lam, U);
+        const T pref = rho * maxwell_pref<D>(lam);
+#pragma unroll
+        for (int j = 0; j < VB; ++j) {
+          T c2 = T(0);
+#pragma unroll
+          for (int d = 0; d < D; ++d) c2 += (v.u[j][d] - U[d]) * (v.u[j][d] - U[d]);
+          const T H = v.real[j] ? pref * t_exp(-lam * c2) : T(0);
+          fo[0][j] = H;
+          if (NR == 2) fo[NR - 1][j] = T(Kxi) / (T(2) * lam) * H;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int j = 0; j < VB; ++j) {
+          const T df = fo[r][j] - fc[r][j];
+#pragma unroll
+          for (int d = 0; d < D; ++d) g[r][j][d] += wd[d] * df;
+          fmx[r][j] = fmax(fmx[r][j], fo[r][j]);
+          fmn[r][j] = fmin(fmn[r][j], fo[r][j]);
+        }
+    }
+    T phi[NR][VB];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int j = 0; j < VB; ++j) phi[r][j] = T(1);
+    if (limiter != 0) {
+      const T eps2c = *reinterpret_cast<const T*>(A + W * CS::INC);
+      T eps2[NR][VB], dmx[NR][VB], dmn[NR][VB];
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int j = 0; j < VB; ++j) {
+          const T mag = fmax(fabs(fmx[r][j]), fabs(fmn[r][j]));
+          eps2[r][j] = eps2c * mag * mag;  // Venkatakrishnan constant in the units of f
+          dmx[r][j] = fmx[r][j] - fc[r][j];
+          dmn[r][j] = fmn[r][j] - fc[r][j];
+        }
+      for (int i = 0; i < W; ++i) {
+        if (inc[i].flags & 2) continue;  // padding
+        T rr[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) rr[d] = inc[i].r[d];
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+#pragma unroll
+          for (int j = 0; j < VB; ++j) {
+            T d2 = T(0);
+#pragma unroll
+            for (int d = 0; d < D; ++d) d2 += g[r][j][d] * rr[d];
+            const T dp = d2 > T(0) ? dmx[r][j] : dmn[r][j];
+            T ph;
+            if (limiter == 2) {
+              ph = d2 != T(0) ? fast_div(dp, d2) : T(1);
+            } else {
+              // (dp^2 + eps + 2 d2 dp) / (dp^2 + 2 d2^2 + dp d2 + eps); equals 1 at d2 = 0
+              const T num = fma(dp, dp + T(2) * d2, eps2[r][j]);
+              const T den = fma(dp + d2, dp, fma(T(2) * d2, d2, eps2[r][j]));
+              ph = fast_div(num, den);
+            }
+            phi[r][j] = fmin(phi[r][j], ph);  // fmin ignores a NaN from 0/0 (then d2 = 0, phi stays)
+          }
+      }
+    }
+    T ug[NR][VB];  // u . (limited gradient), the same on every face
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int j = 0; j < VB; ++j) {
+        const T p = fmin(fmax(phi[r][j], T(0)), T(1));
+        ug[r][j] = T(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          g[r][j][d] *= p;
+          ug[r][j] += v.u[j][d] * g[r][j][d];
+        }
+      }
+    // free-transport part on every face for which this cell is upwind
+    const T* G01 = reinterpret_cast<const T*>(B + (W + 1) * CS::ROW);
+    constexpr int g0i = (int(offsetof(FP, G0)) - g01_chunk<D, NR, T>()) / int(sizeof(T));
+    for (int i = 0; i < W; ++i) {
+      const int fl = inc[i].flags;
+      if (fl & 2) continue;
+      T c0, c1;
+      if (fl & 1) {
+        c0 = dt;
+        c1 = -hdt2;
+      } else {
+        c0 = G01[i * (16 / int(sizeof(T))) + g0i];
+        c1 = G01[i * (16 / int(sizeof(T))) + g0i + 1];
+      }
+      T n[D], rr[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        n[d] = inc[i].n[d];
+        rr[d] = inc[i].r[d];
+      }
+      T* Xf = a.X + size_t(inc[i].face) * (NR * VB * BV) + lane;
+#pragma unroll
+      for (int j = 0; j < VB; ++j) {
+        T un = T(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) un += v.u[j][d] * n[d];
+        if (un > T(0)) {
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            T ff = fc[r][j];
+#pragma unroll
+            for (int d = 0; d < D; ++d) ff += g[r][j][d] * rr[d];
+            Xf[(r * VB + j) * BV] = c0 * ff + c1 * ug[r][j];
+          }
+        }
+      }
+    }
+    __syncwarp();  // all lanes done with the slots before they are refilled
+  }
+  cp_async_wait<0>();
+}
+
+template <int D, int NR, int VB, typename T>
+__global__ void __launch_bounds__(kBlockedThreads) k_bstage1_p(const BlockedArgs<T> a, const int64_t m0) {
+  using CS = CellStage<NR, VB, T>;
+  extern __shared__ __align__(16) unsigned char cell_smem[];
+  const int W = a.W;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int AB = W * CS::INC + int(sizeof(CellEq<T>)), BB = (W + 1) * CS::ROW;
+  unsigned char* const As = cell_smem + warp * stage1_warp_bytes<NR, VB, T>(W);
+  unsigned char* const Bs = As + 3 * AB;
+  BlockVel<D, NR, VB, T> v;
+  v.load(a, m0, lane);
+  const size_t sj = size_t(a.Nc) * BV, sr = size_t(a.M) * sj;
+  const int stride = gridDim.x * nwarps;
+  const int cbeg = blockIdx.x * nwarps + warp;
+
+  auto issueA = [&](int c, unsigned char* dst) {
+    stage_bytes(dst, a.ell + size_t(c) * W, W * CS::INC, lane);
+    stage_bytes(dst + W * CS::INC, a.ceq0 + c, int(sizeof(CellEq<T>)), lane);
+  };
+  auto issueB = [&](int c, const unsigned char* A, unsigned char* dst) {
+    const IncT<T>* inc = reinterpret_cast<const IncT<T>*>(A);
+    for (int i = 0; i < W; ++i) {
+      if (inc[i].flags & 2) continue;
+      stage_bytes(dst + i * CS::ROW, a.X + size_t(inc[i].face) * (NR * VB * BV), CS::ROW, lane);
+    }
+    stage_cell_rows<NR, VB, T>(dst + W * CS::ROW, a, m0, c, lane);
+  };
+
+  if (cbeg < a.Nc) issueA(cbeg, As);
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncwarp();
+  if (cbeg < a.Nc) issueB(cbeg, As, Bs);
+  if (cbeg + stride < a.Nc) issueA(cbeg + stride, As + AB);
+  cp_async_commit();
+  int it = 0;
+  for (int c = cbeg; c < a.Nc; c += stride, ++it) {
+    cp_async_wait<0>();
+    __syncwarp();
+    const int cn = c + stride, cnn = c + 2 * stride;
+    if (cn < a.Nc) issueB(cn, As + ((it + 1) % 3) * AB, Bs + ((it + 1) & 1) * BB);
+    if (cnn < a.Nc) issueA(cnn, As + ((it + 2) % 3) * AB);
+    cp_async_commit();
+
+    const unsigned char* A = As + (it % 3) * AB;
+    const unsigned char* B = Bs + (it & 1) * BB;
+    const IncT<T>* inc = reinterpret_cast<const IncT<T>*>(A);
+    const CellEq<T>& E = *reinterpret_cast<const CellEq<T>*>(A + W * CS::INC);
+    const T* rows = reinterpret_cast<const T*>(B) + lane;
+    T flux[NR][VB];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int j = 0; j < VB; ++j) flux[r][j] = T(0);
+    for (int i = 0; i < W; ++i) {
+      if (inc[i].flags & 2) continue;
+      const T sa = inc[i].sarea;
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int j = 0; j < VB; ++j) flux[r][j] += sa * rows[(i * NR * VB + r * VB + j) * BV];
+    }
+    const T* own = rows + W * (NR * VB * BV);
+    const T lam = E.lam, beta0 = E.beta, pref = E.pref, s0 = E.s0, kap = E.kap, inv_vol = E.inv_vol;
+    const size_t base = size_t(m0) * sj + size_t(c) * BV + lane;
+#pragma unroll
+    for (int j = 0; j < VB; ++j) {
+      T c2 = T(0), cq = T(0);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const T cd = v.u[j][d] - E.U[d];
+        c2 += cd * cd;
+        cq += cd * E.q[d];
+      }
+      const T H = pref * t_exp(-lam * c2);
+      const T s = s0 * cq;
+      T fp[NR];
+      fp[0] = H * (T(1) + s * (T(2) * lam * c2 - T(2 + D)));
+      if (NR == 2) fp[NR - 1] = kap * H * (T(1) + s * (T(2) * lam * c2 - T(D)));
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const T f = own[(r * VB + j) * BV];
+        const T ft = f - flux[r][j] * inv_vol + beta0 * (fp[r] - f);
+        a.f_next[base + r * sr + j * sj] = v.real[j] ? ft : T(0);
+      }
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -559,6 +1005,7 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bW(const BlockedArgs<T> a) 
     for (int d = 0; d < 3; ++d) pn.q[d] = a.cp[c].q[d];  // lagged heat flux in stage 2
     pn.pad = 0.0;
     a.cp_next[c] = pn;
+    a.ceq1[c] = make_cell_eq<D, T>(a.g, pn, a.vol[c]);
   }
 #pragma unroll
   for (int t = 0; t < NW; ++t) res[t] = warp_sum(res[t]);
@@ -581,8 +1028,8 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bW(const BlockedArgs<T> a) 
 // partial sums of q are flushed to FP64 every 32 blocks and reduced over the
 // warp once.
 // ---------------------------------------------------------------------------
-template <int D, int NR, typename T>
-__device__ __forceinline__ void stage2_block(const BlockedArgs<T>& a, int c, int e0, int e1, bool has_wall, int64_t m,
+template <int D, int NR, bool WALL, typename T>
+__device__ __forceinline__ void stage2_block(const BlockedArgs<T>& a, int c, int e0, int e1, int64_t m,
                                              int lane, const Vel4<T>& vq, T (&ft)[NR], const T (&Uc)[3], const T (&qc)[3], T pref, T lam,
                                              T s0, T kap, T beta1, T inv1, T iv, T* fc, size_t sr, size_t sj,
                                              T (&qp)[3]) {
@@ -593,12 +1040,12 @@ __device__ __forceinline__ void stage2_block(const BlockedArgs<T>& a, int c, int
   u[1] = D > 1 ? vq.y : T(0);
   u[2] = D > 2 ? vq.z : T(0);
   const bool real_v = k < a.nv;
-  if (has_wall) {
+  if (WALL) {
     for (int e = e0; e < e1; ++e) {
       if (!(a.inc[e].flags & 1)) continue;
       const int fidx = a.inc[e].face;
       const FaceGeom<T>& fg = a.fg[fidx];
-      const FaceRec<T>& R = a.fr[fidx];
+      const FacePoly<D, NR, T>& R = static_cast<const FacePoly<D, NR, T>*>(a.fpoly)[fidx];
       T un = T(0), c2 = T(0);
 #pragma unroll
       for (int d = 0; d < D; ++d) {
@@ -649,19 +1096,14 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage2(const BlockedArgs<T
   const int64_t me = mb + per < a.M ? mb + per : a.M;
   const size_t sj = size_t(a.Nc) * BV, sr = size_t(a.M) * sj;
   T* fc = a.f_next + size_t(c) * BV + lane;
-  const T dt = T(a.g.dt);
-  const CellPrim& p = a.cp_next[c];
-  const T rho = T(p.rho), lam = T(p.lam), beta1 = dt / (T(2) * T(p.tau));
+  const CellEq<T> E = a.ceq1[c];
+  const T lam = E.lam, beta1 = E.beta, pref = E.pref, s0 = E.s0, kap = E.kap, iv = E.inv_vol;
   const T inv1 = T(1) / (T(1) + beta1);
-  const T pref = rho * maxwell_pref<D>(lam);
-  const T s0 = a.g.shakhov ? T(4.0 * (1.0 - a.g.Pr)) * lam * lam / (T(5) * rho) : T(0);
-  const T kap = T(a.g.Kxi) / (T(2) * lam);
-  const T iv = T(1.0 / a.vol[c]);
   T Uc[3], qc[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    Uc[d] = T(p.U[d]);
-    qc[d] = T(p.q[d]);
+    Uc[d] = E.U[d];
+    qc[d] = E.q[d];
   }
   const int e0 = a.cf_off[c], e1 = a.cf_off[c + 1];
   bool has_wall = false;
@@ -670,21 +1112,45 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage2(const BlockedArgs<T
   T qp[3] = {T(0), T(0), T(0)};
   int since_flush = 0;
   int64_t m = mb;
-  for (; m + UNR <= me; m += UNR) {
-    T ft[UNR][NR];
-    Vel4<T> vq[UNR];
+  if (!has_wall) {
+    // interior cells (almost all): UNR blocks in flight
+    for (; m + UNR <= me; m += UNR) {
+      T ft[UNR][NR];
+      Vel4<T> vq[UNR];
 #pragma unroll
-    for (int i = 0; i < UNR; ++i) {
+      for (int i = 0; i < UNR; ++i) {
 #pragma unroll
-      for (int r = 0; r < NR; ++r) ft[i][r] = fc[r * sr + (m + i) * sj];
-      vq[i] = a.vel[(m + i) * BV + lane];
+        for (int r = 0; r < NR; ++r) ft[i][r] = fc[r * sr + (m + i) * sj];
+        vq[i] = a.vel[(m + i) * BV + lane];
+      }
+#pragma unroll
+      for (int i = 0; i < UNR; ++i)
+        stage2_block<D, NR, false, T>(a, c, e0, e1, m + i, lane, vq[i], ft[i], Uc, qc, pref, lam, s0, kap, beta1,
+                                      inv1, iv, fc, sr, sj, qp);
+      since_flush += UNR;
+      if (since_flush >= 32) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          qd[d] += double(qp[d]);
+          qp[d] = T(0);
+        }
+        since_flush = 0;
+      }
     }
+  }
+  // cells with a wall face, and the remainder
+  for (; m < me; ++m) {
+    T ft[NR];
 #pragma unroll
-    for (int i = 0; i < UNR; ++i)
-      stage2_block<D, NR, T>(a, c, e0, e1, has_wall, m + i, lane, vq[i], ft[i], Uc, qc, pref, lam, s0, kap, beta1,
-                             inv1, iv, fc, sr, sj, qp);
-    since_flush += UNR;
-    if (since_flush >= 32) {
+    for (int r = 0; r < NR; ++r) ft[r] = fc[r * sr + m * sj];
+    const Vel4<T> vq = a.vel[m * BV + lane];
+    if (has_wall)
+      stage2_block<D, NR, true, T>(a, c, e0, e1, m, lane, vq, ft, Uc, qc, pref, lam, s0, kap, beta1, inv1, iv, fc, sr,
+                                   sj, qp);
+    else
+      stage2_block<D, NR, false, T>(a, c, e0, e1, m, lane, vq, ft, Uc, qc, pref, lam, s0, kap, beta1, inv1, iv, fc,
+                                    sr, sj, qp);
+    if (++since_flush >= 32) {
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         qd[d] += double(qp[d]);
@@ -692,14 +1158,6 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage2(const BlockedArgs<T
       }
       since_flush = 0;
     }
-  }
-  for (; m < me; ++m) {
-    T ft[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) ft[r] = fc[r * sr + m * sj];
-    const Vel4<T> vq = a.vel[m * BV + lane];
-    stage2_block<D, NR, T>(a, c, e0, e1, has_wall, m, lane, vq, ft, Uc, qc, pref, lam, s0, kap, beta1, inv1, iv, fc,
-                           sr, sj, qp);
   }
 #pragma unroll
   for (int d = 0; d < D; ++d) qd[d] = warp_sum(qd[d] + double(qp[d]));
@@ -742,25 +1200,132 @@ inline unsigned blocked_warp_grid(int64_t n) {
     else return cudaErrorInvalidValue;                                                                   \
   } while (0)
 
+// Persistent launch of a pipelined per-cell kernel with `bytes` of shared
+// memory per warp: warps per CTA chosen so that a CTA needs at most 100 KB.
+template <typename K>
+cudaError_t launch_cell_pipelined(K kernel, int nsm, int bytes, int& warps_out, unsigned& grid_out) {
+  int warps = kBlockedThreads / 32;
+  while (warps > 1 && warps * bytes > 100 * 1024) warps /= 2;
+  const int smem = warps * bytes;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, warps * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  warps_out = warps;
+  grid_out = unsigned(int64_t(per_sm) * nsm);  // CTAs resident on the whole GPU
+  return cudaSuccess;
+}
+
+// Per-warp shared memory above which the pipelined kernels are not used.
+constexpr int kPipelineWarpBytes = 24 * 1024;
+
+template <int D, int NR, int VB, typename T>
+cudaError_t launch_brecon_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0) {
+  const int bytes = recon_warp_bytes<NR, VB, T>(a.W);
+  if (a.W < 1 || a.W > kEllMax || bytes > kPipelineWarpBytes) {
+    k_brecon<D, NR, VB, T><<<blocked_warp_grid(a.Nc), kBlockedThreads, 0, s>>>(a, m0);
+    return cudaGetLastError();
+  }
+  static int cached_bytes = -1, cached_warps = 0;
+  static unsigned cached_grid = 0;
+  if (cached_bytes != bytes) {
+    cudaError_t e = launch_cell_pipelined(k_brecon_p<D, NR, VB, T>, a.nsm, bytes, cached_warps, cached_grid);
+    if (e != cudaSuccess) return e;
+    cached_bytes = bytes;
+  }
+  const unsigned grid = std::min<unsigned>(cached_grid, unsigned((a.Nc + cached_warps - 1) / cached_warps));
+  k_brecon_p<D, NR, VB, T><<<grid, cached_warps * 32, cached_warps * bytes, s>>>(a, m0);
+  return cudaGetLastError();
+}
+
+template <int D, int NR, int VB, typename T>
+cudaError_t launch_bstage1_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0) {
+  const int bytes = stage1_warp_bytes<NR, VB, T>(a.W);
+  if (a.W < 1 || a.W > kEllMax || bytes > kPipelineWarpBytes) {
+    k_bstage1<D, NR, VB, T><<<blocked_warp_grid(a.Nc), kBlockedThreads, 0, s>>>(a, m0);
+    return cudaGetLastError();
+  }
+  static int cached_bytes = -1, cached_warps = 0;
+  static unsigned cached_grid = 0;
+  if (cached_bytes != bytes) {
+    cudaError_t e =
+        launch_cell_pipelined(k_bstage1_p<D, NR, VB, T>, a.nsm, bytes, cached_warps, cached_grid);
+    if (e != cudaSuccess) return e;
+    cached_bytes = bytes;
+  }
+  const unsigned grid = std::min<unsigned>(cached_grid, unsigned((a.Nc + cached_warps - 1) / cached_warps));
+  k_bstage1_p<D, NR, VB, T><<<grid, cached_warps * 32, cached_warps * bytes, s>>>(a, m0);
+  return cudaGetLastError();
+}
+
+#define UGKS_CELL_CASES(FN)                                                                               \
+  FN(1, 2, 1) FN(1, 2, 2) FN(1, 2, 4) FN(2, 2, 1) FN(2, 2, 2) FN(2, 2, 4) FN(3, 1, 1) FN(3, 1, 2) FN(3, 1, 4) \
+  FN(3, 2, 1) FN(3, 2, 2) FN(3, 2, 4)
+
 template <typename T>
 cudaError_t launch_brecon(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb) {
-  UGKS_BLOCKED_DISPATCH(k_brecon, blocked_warp_grid(a.Nc), a, m0);
+  const int D = a.g.D, NR = a.g.NR;
+#define UGKS_RECON_CASE(d, nr, b) \
+  if (D == d && NR == nr && vb == b) return launch_brecon_tpl<d, nr, b, T>(s, a, m0);
+  UGKS_CELL_CASES(UGKS_RECON_CASE)
+#undef UGKS_RECON_CASE
+  return cudaErrorInvalidValue;
+}
+
+// Persistent launch of the flux kernel: as many CTAs as fit on the GPU
+// (occupancy with the kernel's shared-memory stages), at most one warp per face.
+template <int D, int NR, int VB, typename T>
+cudaError_t launch_bflux_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int first) {
+  constexpr int smem = 2 * (kBlockedThreads / 32) * FluxStage<D, NR, VB, T>::BYTES;
+  static int per_sm = 0;  // per instantiation, computed on first use
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_bflux<D, NR, VB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bflux<D, NR, VB, T>, kBlockedThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  }
+  const unsigned grid = unsigned(std::min<int64_t>(int64_t(per_sm) * a.nsm, blocked_warp_grid(a.Nf)));
+  k_bflux<D, NR, VB, T><<<grid, kBlockedThreads, smem, s>>>(a, m0, first);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_bflux(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb, int first) {
-  UGKS_BLOCKED_DISPATCH(k_bflux, blocked_warp_grid(a.Nf), a, m0, first);
-  return cudaGetLastError();
+  const int D = a.g.D, NR = a.g.NR;
+#define UGKS_FLUX_CASE(d, nr, b) \
+  if (D == d && NR == nr && vb == b) return launch_bflux_tpl<d, nr, b, T>(s, a, m0, first);
+  UGKS_FLUX_CASE(1, 2, 1) UGKS_FLUX_CASE(1, 2, 2) UGKS_FLUX_CASE(1, 2, 4)
+  UGKS_FLUX_CASE(2, 2, 1) UGKS_FLUX_CASE(2, 2, 2) UGKS_FLUX_CASE(2, 2, 4)
+  UGKS_FLUX_CASE(3, 1, 1) UGKS_FLUX_CASE(3, 1, 2) UGKS_FLUX_CASE(3, 1, 4)
+  UGKS_FLUX_CASE(3, 2, 1) UGKS_FLUX_CASE(3, 2, 2) UGKS_FLUX_CASE(3, 2, 4)
+#undef UGKS_FLUX_CASE
+  return cudaErrorInvalidValue;
 }
 
 template <typename T>
 cudaError_t launch_bstage1(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb) {
-  UGKS_BLOCKED_DISPATCH(k_bstage1, blocked_warp_grid(a.Nc), a, m0);
-  return cudaGetLastError();
+  const int D = a.g.D, NR = a.g.NR;
+#define UGKS_STAGE1_CASE(d, nr, b) \
+  if (D == d && NR == nr && vb == b) return launch_bstage1_tpl<d, nr, b, T>(s, a, m0);
+  UGKS_CELL_CASES(UGKS_STAGE1_CASE)
+#undef UGKS_STAGE1_CASE
+  return cudaErrorInvalidValue;
 }
 
 #undef UGKS_BLOCKED_DISPATCH
+
+template <typename T>
+cudaError_t launch_bcelleq(cudaStream_t s, const BlockedArgs<T>& a) {
+  const unsigned nb = unsigned((a.Nc + 255) / 256);
+  if (a.g.D == 1) k_bcelleq<1, T><<<nb, 256, 0, s>>>(a);
+  else if (a.g.D == 2) k_bcelleq<2, T><<<nb, 256, 0, s>>>(a);
+  else if (a.g.D == 3) k_bcelleq<3, T><<<nb, 256, 0, s>>>(a);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_bconserve(cudaStream_t s, const BlockedArgs<T>& a) {
@@ -790,6 +1355,7 @@ cudaError_t launch_bstage2(cudaStream_t s, const BlockedArgs<T>& a) {
   template cudaError_t launch_brecon<T>(cudaStream_t, const BlockedArgs<T>&, int64_t, int);          \
   template cudaError_t launch_bflux<T>(cudaStream_t, const BlockedArgs<T>&, int64_t, int, int);     \
   template cudaError_t launch_bstage1<T>(cudaStream_t, const BlockedArgs<T>&, int64_t, int);        \
+  template cudaError_t launch_bcelleq<T>(cudaStream_t, const BlockedArgs<T>&);                       \
   template cudaError_t launch_bconserve<T>(cudaStream_t, const BlockedArgs<T>&);                     \
   template cudaError_t launch_bstage2<T>(cudaStream_t, const BlockedArgs<T>&);
 

@@ -75,9 +75,14 @@ struct ugks_ctx {
   // blocked sweep: 32-bit incidence records, per-block scratch
   int32_t* d_cf_off32 = nullptr;
   void* d_inc = nullptr;
+  void* d_ell = nullptr;
+  int W = 0;
   void* d_X = nullptr;
+  void* d_fpoly = nullptr;
+  void *d_ceq0 = nullptr, *d_ceq1 = nullptr;
   double *d_Facc_b = nullptr, *d_qpart = nullptr;
   int nchunk = 1;
+  int nsm = 1;
   // tiles and scratch of the tiled sweep
   int ntiles = 0, grid = 0, threads = 1024;
   size_t smem_bytes = 0;
@@ -301,7 +306,8 @@ size_t blocked_Facc_bytes(const ugks_ctx* ctx) { return size_t(ctx->Nf) * FACC_W
 size_t blocked_qpart_bytes(const ugks_ctx* ctx) { return size_t(ctx->nchunk) * ctx->Nc * 3 * sizeof(double); }
 
 template <typename T>
-ugks_status build_typed(ugks_ctx* ctx, const std::vector<CellFace>& cf, const std::vector<double>& eps2,
+ugks_status build_typed(ugks_ctx* ctx, const std::vector<int64_t>& cf_off, const std::vector<CellFace>& cf,
+                        const std::vector<double>& eps2,
                         const std::vector<FaceGeom<double>>& fg64, const double* ux, const double* uy,
                         const double* uz, const double* wp) {
   std::vector<CellFaceT<T>> cft(cf.size());
@@ -359,10 +365,23 @@ ugks_status build_typed(ugks_ctx* ctx, const std::vector<CellFace>& cf, const st
     CUDA_TRY(ctx, upload(ctx, &dv, vel.data(), Mp * sizeof(Vel4<T>)));
     ctx->d_velT = dv;
   }
-  FaceRec<T>* fr;
-  CUDA_TRY(ctx, dalloc(ctx, &fr, size_t(ctx->Nf) * sizeof(FaceRec<T>)));
-  ctx->d_fr = fr;
+  if (ctx->variant == 1) {
+    FaceRec<T>* fr;
+    CUDA_TRY(ctx, dalloc(ctx, &fr, size_t(ctx->Nf) * sizeof(FaceRec<T>)));
+    ctx->d_fr = fr;
+  }
   if (ctx->variant == 2) {
+    const int D = ctx->D, NR = ctx->NR;
+    const size_t poly_bytes = D == 1   ? sizeof(FacePoly<1, 2, T>)
+                              : D == 2 ? sizeof(FacePoly<2, 2, T>)
+                              : NR == 1 ? sizeof(FacePoly<3, 1, T>)
+                                        : sizeof(FacePoly<3, 2, T>);
+    CUDA_TRY(ctx, dalloc(ctx, &ctx->d_fpoly, size_t(ctx->Nf) * poly_bytes));
+    CellEq<T>* ce;
+    CUDA_TRY(ctx, dalloc(ctx, &ce, size_t(ctx->Nc) * sizeof(CellEq<T>)));
+    ctx->d_ceq0 = ce;
+    CUDA_TRY(ctx, dalloc(ctx, &ce, size_t(ctx->Nc) * sizeof(CellEq<T>)));
+    ctx->d_ceq1 = ce;
     std::vector<IncT<T>> inc(cf.size());
     for (size_t e = 0; e < cf.size(); ++e) {
       const CellFace& c = cf[e];
@@ -381,6 +400,21 @@ ugks_status build_typed(ugks_ctx* ctx, const std::vector<CellFace>& cf, const st
     IncT<T>* di;
     CUDA_TRY(ctx, upload(ctx, &di, inc.data(), inc.size() * sizeof(IncT<T>)));
     ctx->d_inc = di;
+    // the same records as a padded table [Nc][W], W = the most faces of a cell
+    int W = 1;
+    for (int64_t c = 0; c < ctx->Nc; ++c) W = std::max<int>(W, int(cf_off[c + 1] - cf_off[c]));
+    ctx->W = W;
+    IncT<T> pad{};
+    pad.face = 0;
+    pad.other = -1;
+    pad.bc = -1;
+    pad.flags = 2;
+    std::vector<IncT<T>> ell(size_t(ctx->Nc) * W, pad);
+    for (int64_t c = 0; c < ctx->Nc; ++c)
+      for (int64_t e = cf_off[c]; e < cf_off[c + 1]; ++e) ell[size_t(c) * W + (e - cf_off[c])] = inc[e];
+    IncT<T>* de;
+    CUDA_TRY(ctx, upload(ctx, &de, ell.data(), ell.size() * sizeof(IncT<T>)));
+    ctx->d_ell = de;
     T* X;
     CUDA_TRY(ctx, dalloc(ctx, &X, blocked_X_bytes<T>(ctx)));
     ctx->d_X = X;
@@ -438,18 +472,24 @@ ugks_status sweep_blocked(ugks_ctx* ctx, int cur, void* X, double* Facc, double*
   a.eps2 = static_cast<const T*>(ctx->d_eps2);
   a.cf_off = ctx->d_cf_off32;
   a.inc = static_cast<const IncT<T>*>(ctx->d_inc);
+  a.ell = static_cast<const IncT<T>*>(ctx->d_ell);
+  a.W = ctx->W;
   a.fg = static_cast<const FaceGeom<T>*>(ctx->d_fg);
-  a.fr = static_cast<const FaceRec<T>*>(ctx->d_fr);
+  a.fpoly = ctx->d_fpoly;
+  a.ceq0 = static_cast<CellEq<T>*>(ctx->d_ceq0);
+  a.ceq1 = static_cast<CellEq<T>*>(ctx->d_ceq1);
   a.bcs = ctx->d_bcs;
   a.X = static_cast<T*>(X);
   a.Facc = Facc;
   a.qpart = qpart;
   a.nchunk = ctx->nchunk;
+  a.nsm = ctx->nsm;
   a.res_acc = ctx->d_res_acc;
   a.status = ctx->d_status;
   cudaStream_t s = ctx->stream;
   cudaEvent_t ev_all, ev;
   record_start(ctx, kTSweep, &ev_all);
+  LAUNCH_TRY(ctx, launch_bcelleq<T>(s, a));
   const int64_t M = ctx->M;
   int64_t m0 = 0;
   for (int pass = 0; pass < 2; ++pass) {
@@ -489,7 +529,7 @@ ugks_status step_typed(ugks_ctx* ctx) {
   record_start(ctx, 1, &ev);
   launch_face<T>(ctx->stream, ctx->Nf, ctx->gas, ctx->d_W[cur], ctx->d_gW, ctx->d_q[cur], ctx->d_fown, ctx->d_fnei,
                  ctx->d_fnormal, ctx->d_fcent, ctx->d_fshift, ctx->d_xc, ctx->d_bcs,
-                 static_cast<FaceRec<T>*>(ctx->d_fr));
+                 static_cast<FaceRec<T>*>(ctx->d_fr), ctx->d_fpoly);
   CUDA_TRY(ctx, cudaGetLastError());
   record_stop(ctx, 1, ev);
   if (ctx->variant == 2) {
@@ -574,7 +614,7 @@ ugks_status step_typed_static(ugks_ctx* ctx, unsigned char* base) {
   CUDA_TRY(ctx, cudaGetLastError());
   launch_face<T>(ctx->stream, ctx->Nf, ctx->gas, ctx->d_W[cur], ctx->d_gW, ctx->d_q[cur], ctx->d_fown, ctx->d_fnei,
                  ctx->d_fnormal, ctx->d_fcent, ctx->d_fshift, ctx->d_xc, ctx->d_bcs,
-                 static_cast<FaceRec<T>*>(ctx->d_fr));
+                 static_cast<FaceRec<T>*>(ctx->d_fr), ctx->d_fpoly);
   CUDA_TRY(ctx, cudaGetLastError());
   if (ctx->variant == 2) {
     unsigned char* X = base;
@@ -813,6 +853,7 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
   int dev = 0, nsm = 1;
   CUDA_TRY(ctx, cudaGetDevice(&dev));
   CUDA_TRY(ctx, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  ctx->nsm = nsm;
   int smem_optin = 0;
   CUDA_TRY(ctx, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const size_t elem = ctx->storage == UGKS_STORAGE_F64 ? sizeof(double) : sizeof(float);
@@ -1018,8 +1059,8 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
   g.dt = ctx->dt;
 
   ugks_status st = ctx->storage == UGKS_STORAGE_F64
-                       ? build_typed<double>(ctx, cf, eps2, fg, ux.data(), uy.data(), uz.data(), wp.data())
-                       : build_typed<float>(ctx, cf, eps2, fg, ux.data(), uy.data(), uz.data(), wp.data());
+                       ? build_typed<double>(ctx, cf_off, cf, eps2, fg, ux.data(), uy.data(), uz.data(), wp.data())
+                       : build_typed<float>(ctx, cf_off, cf, eps2, fg, ux.data(), uy.data(), uz.data(), wp.data());
   if (st != UGKS_OK) return st;
   st = ctx->storage == UGKS_STORAGE_F64 ? init_state_typed<double>(ctx) : init_state_typed<float>(ctx);
   if (st != UGKS_OK) return st;

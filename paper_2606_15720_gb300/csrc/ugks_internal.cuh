@@ -97,6 +97,54 @@ struct __align__(16) IncT {
   int32_t flags;   // bit 0: wall
 };
 
+// Number of monomials of degree <= 3 in D variables.
+template <int D>
+struct NPoly {
+  static constexpr int value = D == 1 ? 4 : D == 2 ? 10 : 20;
+};
+
+// Position of the monomial c0^e0 c1^e1 c2^e2 in the coefficient arrays of
+// FacePoly (degree by degree; within a degree by descending e0, then e1),
+// the order in which the nested Horner evaluation of the blocked sweep
+// reads them.
+template <int D>
+__host__ __device__ constexpr int mono_index(int e0, int e1, int e2) {
+  return D == 1 ? e0
+       : D == 2 ? ((e0 + e1) == 0 ? 0 : (e0 + e1) == 1 ? 1 : (e0 + e1) == 2 ? 3 : 6) + e1
+                : ((e0 + e1 + e2) == 0 ? 0 : (e0 + e1 + e2) == 1 ? 1 : (e0 + e1 + e2) == 2 ? 4 : 10) +
+                      (e1 + e2) * (e1 + e2 + 1) / 2 + e2;
+}
+
+// Per-step interface record of the blocked sweep (Eq. 32-35).  The
+// equilibrium part of the interface distribution, G2 (g0 + g0+) + G3 u.grad
+// g0 + G4 d_t g0, equals g0(u) * P_r(c) with c = u - U0 and P_r a cubic
+// polynomial whose coefficients are built in FP64 per face.  Wall faces: the
+// unit-density wall Maxwellian (rho_pref, U, lam, kappa), zero elsewhere.
+template <int D, int NR, typename T>
+struct __align__(16) FacePoly {
+  T U[3];          // U0
+  T lam;           // lambda0
+  T rho_pref;      // rho0 (lambda0/pi)^(D/2)
+  T kappa;         // K_xi / (2 lambda0)
+  T G0, G1;        // integrals of c1, c2 over [0, dt] (Eq. 34)
+  T P[NR][NPoly<D>::value];
+};
+
+// Per-cell equilibrium record of the blocked sweep in the sweep precision,
+// built from the FP64 primitive record: the (Shakhov) Maxwellian of the cell
+// and the relaxation factor of a stage update (Eq. 41-42).
+template <typename T>
+struct __align__(16) CellEq {
+  T U[3];
+  T lam;
+  T pref;          // rho (lambda/pi)^(D/2)
+  T s0;            // Shakhov prefactor 4 (1-Pr) lambda^2 / (5 rho), 0 for BGK
+  T kap;           // K_xi / (2 lambda)
+  T beta;          // dt / (2 tau)
+  T q[3];          // heat flux entering the Shakhov term
+  T inv_vol;
+};
+
 struct BCDev {
   int32_t type;
   int32_t pad;

@@ -22,7 +22,7 @@ void launch_cell(cudaStream_t s, int64_t Nc, const Gas& g, const double* W, cons
 template <typename T>
 void launch_face(cudaStream_t s, int64_t Nf, const Gas& g, const double* W, const double* gW, const double* q,
                  const int64_t* fown, const int64_t* fnei, const double* fnormal, const double* fcent,
-                 const double* fshift, const double* xc, const BCDev* bcs, FaceRec<T>* rec);
+                 const double* fshift, const double* xc, const BCDev* bcs, FaceRec<T>* rec, void* poly);
 
 template <typename T>
 void launch_moments(cudaStream_t s, int64_t Nc, int64_t M, const Gas& g, const T* f, const double* W,
@@ -102,14 +102,19 @@ struct BlockedArgs {
   const T* eps2;                 // limiter constant (K_v |Omega|^(1/D))^3 per cell
   const int32_t* cf_off;         // per cell incidence CSR
   const IncT<T>* inc;
+  const IncT<T>* ell;            // the same records as a padded table [Nc][W] (flags bit 1: padding)
+  int W;                         // ELL width: the largest number of faces of a cell
   const FaceGeom<T>* fg;
-  const FaceRec<T>* fr;
+  const void* fpoly;             // FacePoly<D, NR, T> [Nf] of this step
+  CellEq<T>* ceq0;               // equilibrium record of W^n (first stage)
+  CellEq<T>* ceq1;               // equilibrium record of W^{n+1} (second stage)
   const BCDev* bcs;
   T* X;                          // per face, one block [Nf][NR][VB][BV]: the upwind
                                  // reconstruction, then the micro flux
   double* Facc;                  // face accumulators [Nf][FACC_W]
   double* qpart;                 // heat-flux partial sums [nchunk][Nc][3]
   int nchunk;                    // velocity chunks of the second stage
+  int nsm;                       // multiprocessors of the device (persistent grids)
   double* res_acc;               // [NWP] sum of squared W increments
   int* status;
 };
@@ -120,6 +125,8 @@ template <typename T>
 cudaError_t launch_bflux(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb, int first);
 template <typename T>
 cudaError_t launch_bstage1(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb);
+template <typename T>
+cudaError_t launch_bcelleq(cudaStream_t s, const BlockedArgs<T>& a);
 template <typename T>
 cudaError_t launch_bconserve(cudaStream_t s, const BlockedArgs<T>& a);
 template <typename T>

@@ -387,10 +387,108 @@ __device__ __forceinline__ Vec5 slope_column(const double* gW, int64_t c, int d)
   return r;
 }
 
+// Coefficients of the equilibrium bracket of one reduced distribution as a
+// cubic in c = u - U0 (FacePoly): with u = c + U0,
+//   G2 mu (1 + s (c.q)(2 lambda |c|^2 - delta))
+// + G3 [mu (sum_d u_d a_d0 + sum_de a_de u_d u_e) + (mu |u|^2 + nu)/2 sum_d a_d,D+1 u_d]
+// + G4 [mu (A_0 + sum_e A_e u_e + A_D+1 |u|^2 / 2) + A_D+1 nu / 2]
+// (h: mu = 1, nu = kappa, delta = D + 2; b: mu = kappa, nu = <xi^4>, delta = D),
+// i.e. G2 (g0 + g0+) + G3 u.grad g0 + G4 d_t g0 divided by g0 (Eq. 32-33,
+// 18-19).  Expanded in FP64.
+template <int D>
+__device__ __forceinline__ void cub_add(double (&p)[NPoly<D>::value], int e0, int e1, int e2, double v) {
+  p[mono_index<D>(e0, e1, e2)] += v;
+}
+
+template <int D>
+__device__ __forceinline__ void bracket_cubic(double (&p)[NPoly<D>::value], const G5& G, const Vec5 (&a)[D],
+                                              const Vec5& A, const Prim& p0, double s, const double (&qf)[3],
+                                              double mu, double nu, double delta) {
+  constexpr int NP = NPoly<D>::value;
+#pragma unroll
+  for (int t = 0; t < NP; ++t) p[t] = 0.0;
+  const double G2 = G.g[2], G3 = G.g[3], G4 = G.g[4], lam = p0.lam;
+  double U2 = 0.0, aU = 0.0, quadU = 0.0, alpha = 0.0, AU = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    U2 += p0.U[d] * p0.U[d];
+    aU += a[d].v[0] * p0.U[d];
+    alpha += a[d].v[D + 1] * p0.U[d];
+    AU += A.v[1 + d] * p0.U[d];
+#pragma unroll
+    for (int e = 0; e < D; ++e) quadU += a[d].v[1 + e] * p0.U[d] * p0.U[e];
+  }
+  // G2 term (with the Shakhov correction)
+  cub_add<D>(p, 0, 0, 0, G2 * mu);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    cub_add<D>(p, d == 0, d == 1, d == 2, -delta * G2 * mu * s * qf[d]);
+#pragma unroll
+    for (int e = 0; e < D; ++e)
+      cub_add<D>(p, (d == 0) + 2 * (e == 0), (d == 1) + 2 * (e == 1), (d == 2) + 2 * (e == 2),
+                 2.0 * lam * G2 * mu * s * qf[d]);
+  }
+  // G3 term: sum_d u_d a_d0 + sum_de a_de u_d u_e
+  cub_add<D>(p, 0, 0, 0, G3 * mu * (aU + quadU));
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    double lin = a[k].v[0];
+#pragma unroll
+    for (int e = 0; e < D; ++e) lin += a[k].v[1 + e] * p0.U[e] + a[e].v[1 + k] * p0.U[e];
+    cub_add<D>(p, k == 0, k == 1, k == 2, G3 * mu * lin);
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+#pragma unroll
+    for (int e = 0; e < D; ++e)
+      cub_add<D>(p, (d == 0) + (e == 0), (d == 1) + (e == 1), (d == 2) + (e == 2), G3 * mu * a[d].v[1 + e]);
+  // G3 term: (mu |u|^2 + nu) / 2 sum_d a_d,D+1 u_d
+  cub_add<D>(p, 0, 0, 0, 0.5 * G3 * (mu * U2 + nu) * alpha);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const double b = a[d].v[D + 1];
+    cub_add<D>(p, d == 0, d == 1, d == 2, 0.5 * G3 * (mu * U2 + nu) * b + G3 * mu * alpha * p0.U[d]);
+    cub_add<D>(p, 2 * (d == 0), 2 * (d == 1), 2 * (d == 2), 0.5 * G3 * mu * alpha);
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+      cub_add<D>(p, (d == 0) + 2 * (e == 0), (d == 1) + 2 * (e == 1), (d == 2) + 2 * (e == 2), 0.5 * G3 * mu * b);
+      cub_add<D>(p, (d == 0) + (e == 0), (d == 1) + (e == 1), (d == 2) + (e == 2), G3 * mu * p0.U[e] * b);
+    }
+  }
+  // G4 term
+  const double A0 = A.v[0], A4 = A.v[D + 1];
+  cub_add<D>(p, 0, 0, 0, G4 * (mu * (A0 + AU + 0.5 * A4 * U2) + 0.5 * A4 * nu));
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    cub_add<D>(p, e == 0, e == 1, e == 2, G4 * mu * (A.v[1 + e] + A4 * p0.U[e]));
+    cub_add<D>(p, 2 * (e == 0), 2 * (e == 1), 2 * (e == 2), 0.5 * G4 * mu * A4);
+  }
+}
+
+template <int D, int NR, typename T>
+__device__ __forceinline__ void store_face_poly(void* out, int64_t f, const Prim& p0, double rho_pref, double kappa,
+                                                double G0, double G1, const double (&ph)[NPoly<D>::value],
+                                                const double (&pb)[NPoly<D>::value]) {
+  FacePoly<D, NR, T> P;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) P.U[d] = T(p0.U[d]);
+  P.lam = T(p0.lam);
+  P.rho_pref = T(rho_pref);
+  P.kappa = T(kappa);
+  P.G0 = T(G0);
+  P.G1 = T(G1);
+#pragma unroll
+  for (int t = 0; t < NPoly<D>::value; ++t) {
+    P.P[0][t] = T(ph[t]);
+    if (NR == 2) P.P[NR - 1][t] = T(pb[t]);
+  }
+  static_cast<FacePoly<D, NR, T>*>(out)[f] = P;
+}
+
 template <int D, typename T>
 __global__ void k_face(int64_t Nf, Gas g, const double* W, const double* gW, const double* q,
                        const int64_t* fown, const int64_t* fnei, const double* fnormal, const double* fcent,
-                       const double* fshift, const double* xc, const BCDev* bcs, FaceRec<T>* rec) {
+                       const double* fshift, const double* xc, const BCDev* bcs, FaceRec<T>* rec, void* poly) {
   constexpr int nw = D + 2;
   const int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (f >= Nf) return;
@@ -421,7 +519,21 @@ __global__ void k_face(int64_t Nf, Gas g, const double* W, const double* gW, con
 #pragma unroll
     for (int d = 0; d < 3; ++d) R.U[d] = T(bc.u[d]);
     R.kappa = T(g.Kxi / (2.0 * lam));
-    rec[f] = R;
+    if (rec) rec[f] = R;
+    if (poly) {
+      constexpr int NP = NPoly<D>::value;
+      double zero[NP];
+#pragma unroll
+      for (int t = 0; t < NP; ++t) zero[t] = 0.0;
+      Prim pw;
+      pw.rho = 1.0;
+      pw.lam = lam;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) pw.U[d] = bc.u[d];
+      const double rp = pow(lam / M_PI, 0.5 * D), kp = g.Kxi / (2.0 * lam);
+      if (g.NR == 2) store_face_poly<D, 2, T>(poly, f, pw, rp, kp, 0.0, 0.0, zero, zero);
+      else store_face_poly<D, 1, T>(poly, f, pw, rp, kp, 0.0, 0.0, zero, zero);
+    }
     return;
   }
   double n[3], rl[3];
@@ -491,9 +603,11 @@ __global__ void k_face(int64_t Nf, Gas g, const double* W, const double* gW, con
   Vec5 rhsA;
 #pragma unroll
   for (int t = 0; t < NWP; ++t) rhsA.v[t] = 0.0;
+  Vec5 av[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     const Vec5 a = maxwell_solve<D>(p0, K, dW0[d]);
+    av[d] = a;
 #pragma unroll
     for (int t = 0; t < nw; ++t) R.a[d][t] = T(a.v[t]);
     const Vec5 dF = euler_flux_derivative<D>(p0, K, d, W0, dW0[d]);
@@ -522,7 +636,26 @@ __global__ void k_face(int64_t Nf, Gas g, const double* W, const double* gW, con
   }
   R.kappa = T(g.Kxi / (2.0 * p0.lam));
   R.xi4 = T(g.Kxi * (g.Kxi + 2.0) / (4.0 * p0.lam * p0.lam));
-  rec[f] = R;
+  if (rec) rec[f] = R;
+  if (poly) {
+    constexpr int NP = NPoly<D>::value;
+    const double s = g.shakhov ? 4.0 * (1.0 - g.Pr) * p0.lam * p0.lam / (5.0 * p0.rho) : 0.0;
+    double qf[3] = {0.0, 0.0, 0.0};
+    if (g.shakhov)
+#pragma unroll
+      for (int d = 0; d < D; ++d) qf[d] = 0.5 * (q[o * 3 + d] + qr[d]);
+    const double kappa = g.Kxi / (2.0 * p0.lam);
+    const double xi4 = g.Kxi * (g.Kxi + 2.0) / (4.0 * p0.lam * p0.lam);
+    double ph[NP], pb[NP];
+    bracket_cubic<D>(ph, G, av, A, p0, s, qf, 1.0, kappa, double(D + 2));
+    const double rp = p0.rho * pow(p0.lam / M_PI, 0.5 * D);
+    if (g.NR == 2) {
+      bracket_cubic<D>(pb, G, av, A, p0, s, qf, kappa, xi4, double(D));
+      store_face_poly<D, 2, T>(poly, f, p0, rp, kappa, G.g[0], G.g[1], ph, pb);
+    } else {
+      store_face_poly<D, 1, T>(poly, f, p0, rp, kappa, G.g[0], G.g[1], ph, ph);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -641,11 +774,11 @@ void launch_cell(cudaStream_t s, int64_t Nc, const Gas& g, const double* W, cons
 template <typename T>
 void launch_face(cudaStream_t s, int64_t Nf, const Gas& g, const double* W, const double* gW, const double* q,
                  const int64_t* fown, const int64_t* fnei, const double* fnormal, const double* fcent,
-                 const double* fshift, const double* xc, const BCDev* bcs, FaceRec<T>* rec) {
+                 const double* fshift, const double* xc, const BCDev* bcs, FaceRec<T>* rec, void* poly) {
   const unsigned nb = blocks_for(Nf, 128);
-  if (g.D == 1) k_face<1, T><<<nb, 128, 0, s>>>(Nf, g, W, gW, q, fown, fnei, fnormal, fcent, fshift, xc, bcs, rec);
-  if (g.D == 2) k_face<2, T><<<nb, 128, 0, s>>>(Nf, g, W, gW, q, fown, fnei, fnormal, fcent, fshift, xc, bcs, rec);
-  if (g.D == 3) k_face<3, T><<<nb, 128, 0, s>>>(Nf, g, W, gW, q, fown, fnei, fnormal, fcent, fshift, xc, bcs, rec);
+  if (g.D == 1) k_face<1, T><<<nb, 128, 0, s>>>(Nf, g, W, gW, q, fown, fnei, fnormal, fcent, fshift, xc, bcs, rec, poly);
+  if (g.D == 2) k_face<2, T><<<nb, 128, 0, s>>>(Nf, g, W, gW, q, fown, fnei, fnormal, fcent, fshift, xc, bcs, rec, poly);
+  if (g.D == 3) k_face<3, T><<<nb, 128, 0, s>>>(Nf, g, W, gW, q, fown, fnei, fnormal, fcent, fshift, xc, bcs, rec, poly);
 }
 
 template <typename T>
@@ -680,7 +813,7 @@ void launch_residual_finalize(cudaStream_t s, int nw, int64_t Nc, const double* 
                                  const double*, const double*, const double*, T*);                              \
   template void launch_face<T>(cudaStream_t, int64_t, const Gas&, const double*, const double*, const double*,   \
                                const int64_t*, const int64_t*, const double*, const double*, const double*,      \
-                               const double*, const BCDev*, FaceRec<T>*);                                        \
+                               const double*, const BCDev*, FaceRec<T>*, void*);                                 \
   template void launch_moments<T>(cudaStream_t, int64_t, int64_t, const Gas&, const T*, const double*,           \
                                   const double*, const double*, const double*, const double*, double*, double*); \
   template void launch_gather_f<T>(cudaStream_t, int64_t, int64_t, int, int64_t, const T*, const int64_t*,       \
