@@ -58,34 +58,58 @@ def dist_env():
     return rank, world, local
 
 
+N_SM = 152            # GB300 multiprocessors
+FP32_LANES = 128      # FP32 lanes per multiprocessor
+
+
 def load_peaks():
+    """HBM GB/s (measured copy) and the FP32 CUDA-core peak in TFLOP/s derived
+    from unit counts and the maximum SM clock: 152 SMs x 128 lanes x 2 (FMA)."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as fh:
             d = json.load(fh)
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        mhz = float(d.get("sm_max_mhz", 2070.0))
+        return float(d["hbm_gbs"]), "measured", N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    return 6800.0, "fallback", N_SM * FP32_LANES * 2 * 2070e6 / 1e12
+
+
+# Algorithmic work of the blocked sweep per velocity (FP32 operations, FMA = 2;
+# derivation in DESIGN.md).  inc = faces per cell (4 on tetrahedra).
+def flops_recon(inc):       # per cell-velocity: LSQ gradient, limiter, upwind face values
+    return 17 + 41 * inc
+
+
+FLOPS_FLUX = 69             # per face-velocity: upwind pick, g0 P(c), flux, moments
+
+
+def flops_stage1(inc):      # per cell-velocity
+    return 27 + 2 * inc
+
+
+FLOPS_STAGE2 = 34           # per cell-velocity
+BYTES_STAGE = 8             # per DOF and stage update: read + write of an FP32 f value
 
 
 def sweep_source_hash():
     h = hashlib.sha256()
-    for fn in ("ugks_sweep.cu", "ugks_internal.cuh", "ugks_kernels.cuh"):
+    for fn in ("ugks_blocked.cuh", "ugks_internal.cuh", "ugks_kernels.cuh", "ugks_device.cuh"):
         with open(os.path.join(ROOT, "paper_2606_15720_gb300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic():
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    """DRAM bytes per launch of each blocked-sweep kernel from the committed
+    ncu summary, if it was taken on the current kernel source (else {})."""
     p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if not os.path.exists(p):
-        return None
+        return {}
     with open(p) as fh:
         d = json.load(fh)
     if d.get("source_hash") != sweep_source_hash():
-        return None
-    return d.get("bytes_per_launch_full_workload")
+        return {}
+    return d.get("dram_bytes_per_launch", {})
 
 
 class ClockSampler:
@@ -134,7 +158,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(mesh, grid, gas, W0, target_cells=3000, steps=2):
+def cpu_baseline(mesh, grid, gas, W0, target_cells=3000, steps=6):
     """The FP64 oracle as it stands, on a bounded sample of the workload: the
     face-connected patch of ~target_cells cells around a body-adjacent cell,
     all 32^3 velocities, `steps` steps."""
@@ -194,13 +218,70 @@ def run_reference(args):
     return 0
 
 
+def rooflines(stats, mesh, grid, dof, steps):
+    """Per-kernel rooflines of the blocked sweep from the library's event
+    timings (CUDA events on the stream the kernels run on), the roofline of
+    the dominant kernel, and the whole-step HBM and ALU views."""
+    hbm_peak, peak_kind, fp32_peak = load_peaks()
+    n_inc = 2 * mesh.n_faces - int(np.sum(mesh.face_neighbor < 0))
+    inc = n_inc / mesh.n_cells
+    nv = grid.n_v
+    traffic = recorded_traffic()
+    per_dof = {"block_reconstruction": (flops_recon(inc), 0), "block_fluxes": (FLOPS_FLUX * mesh.n_faces / mesh.n_cells, 0),
+               "block_stage1": (flops_stage1(inc), BYTES_STAGE), "stage2": (FLOPS_STAGE2, BYTES_STAGE)}
+    kernels = {}
+    for name, (fl, by) in per_dof.items():
+        ms, n = stats.get(name, (0.0, 0))
+        if not n:
+            continue
+        launch_s = ms / n * 1e-3
+        dof_launch = dof * steps / n              # phase-space points one launch processes
+        tflops = fl * dof_launch / launch_s / 1e12
+        gbs = by * dof_launch / launch_s / 1e9
+        bound = "alu" if by == 0 or fl / by > fp32_peak * 1e12 / (hbm_peak * 1e9) else "hbm"
+        kernels[name] = {"launch_ms": ms / n, "ms_per_step": ms / steps, "bound": bound,
+                         "flops_per_dof": fl, "bytes_per_dof": by,
+                         "alu_tflops": tflops, "alu_frac": tflops / fp32_peak,
+                         "hbm_gbs": gbs if by else None, "hbm_frac": gbs / hbm_peak if by else None,
+                         "dram_bytes_per_launch": traffic.get(name)}
+    roofline = None
+    if kernels:
+        top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+        k = kernels[top]
+        if k["bound"] == "alu":
+            roofline = {"bound": "alu", "kernel": top, "achieved": k["alu_tflops"], "peak": fp32_peak,
+                        "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock", "unit": "TFLOP/s",
+                        "frac": k["alu_frac"], "traffic": k["dram_bytes_per_launch"],
+                        "algorithmic_flops_per_launch": k["flops_per_dof"] * dof * steps / stats[top][1],
+                        "launch_ms": k["launch_ms"]}
+        else:
+            roofline = {"bound": "hbm", "kernel": top, "achieved": k["hbm_gbs"], "peak": hbm_peak,
+                        "peak_kind": peak_kind, "unit": "GB/s", "frac": k["hbm_frac"],
+                        "traffic": k["dram_bytes_per_launch"],
+                        "algorithmic_bytes_per_launch": k["bytes_per_dof"] * dof * steps / stats[top][1],
+                        "launch_ms": k["launch_ms"]}
+    sweep_ms, sweep_n = stats.get("velocity_block_sweep", (0.0, 0))
+    step_views = None
+    if sweep_n:
+        t = sweep_ms / sweep_n * 1e-3
+        fl = sum(v["flops_per_dof"] for v in kernels.values())
+        step_views = {"sweep_ms": sweep_ms / sweep_n,
+                      "hbm": {"bytes_per_dof": 16, "achieved_gbs": 16 * dof / t / 1e9,
+                              "frac": 16 * dof / t / 1e9 / hbm_peak, "peak": hbm_peak, "peak_kind": peak_kind},
+                      "alu": {"flops_per_dof": fl, "achieved_tflops": fl * dof / t / 1e12,
+                              "frac": fl * dof / t / 1e12 / fp32_peak, "peak": fp32_peak}}
+    return roofline, kernels, step_views
+
+
 def count_launches(stats):
     """Kernel launches of the library in the timed region, from its per-region
-    event counts (velocity_block_sweep of the blocked sweep spans several
-    kernels; conserve is two kernels)."""
+    event counts (the regions of the blocked sweep that span several kernels
+    count each)."""
     if stats.get("block_fluxes", (0, 0))[1]:
-        per = {"cell_stage": 1, "face_stage": 1, "block_reconstruction": 1, "block_fluxes": 1, "block_stage1": 1,
-               "conserve": 2, "stage2": 1, "residual": 1}
+        # velocity_block_sweep: the per-cell equilibrium records; conserve: wall
+        # density + W update; stage2: second stage + heat-flux chunk sum
+        per = {"cell_stage": 1, "face_stage": 1, "velocity_block_sweep": 1, "block_reconstruction": 1,
+               "block_fluxes": 1, "block_stage1": 1, "conserve": 2, "stage2": 2, "residual": 1}
     else:
         per = {"cell_stage": 1, "face_stage": 1, "velocity_block_sweep": 1, "residual": 1}
     return int(sum(per.get(k, 0) * n for k, (_, n) in stats.items()))
@@ -257,16 +338,7 @@ def run_gpu(args):
     ms_per_step = ms_max / args.steps
     value = dof * world / (ms_per_step * 1e-3)
 
-    # roofline of the dominant kernel (the velocity-block sweep): algorithmic
-    # bytes = stage-1 read + write of f and stage-2 read + write of f, 4 bytes each
-    sweep_ms, sweep_n = stats.get("velocity_block_sweep", (0.0, 0))
-    hbm_peak, peak_kind = load_peaks()
-    bytes_alg = 16.0 * dof
-    achieved = bytes_alg / (sweep_ms / max(sweep_n, 1) * 1e-3) / 1e9 if sweep_n else None
-    roofline = {"bound": "hbm", "kernel": "velocity_block_sweep", "achieved": achieved, "peak": hbm_peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": (achieved / hbm_peak) if achieved else None,
-                "traffic": recorded_traffic(), "algorithmic_bytes_per_launch": bytes_alg,
-                "launch_ms": sweep_ms / max(sweep_n, 1)}
+    roofline, kernels, step_views = rooflines(stats, mesh, grid, dof, args.steps)
 
     # end to end through the one-shot C call with host buffers: mesh, grid and
     # W_init copied in, n steps, W and the residual copied out
@@ -308,7 +380,8 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (two %.1f GB distribution buffers)" % (dof * 4 / 1e9),
                        "state_after": {"residual": [float(x) for x in res],
                                        "finite": bool(np.all(np.isfinite(W_end)))}},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "kernels": kernels, "step_roofline": step_views,
+            "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": count_launches(stats),
             "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in stats.items()},
             "clocks": clk}

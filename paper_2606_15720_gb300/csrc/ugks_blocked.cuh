@@ -1023,10 +1023,11 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bW(const BlockedArgs<T> a) 
 // ---------------------------------------------------------------------------
 // Second stage (Eq. 42) of one cell over one chunk of velocity blocks, with
 // the outgoing wall flux rho_w g_w (known only after the sweep), and the
-// chunk's partial sums of the heat flux of f^{n+1} (Eq. 13).  Four blocks are
-// loaded before any is updated (memory-level parallelism); per-lane FP32
-// partial sums of q are flushed to FP64 every 32 blocks and reduced over the
-// warp once.
+// chunk's partial sums of the heat flux of f^{n+1} (Eq. 13).  The 8 warps of
+// a CTA (8 cells) step through the chunk together, 8 blocks per round: the
+// CTA stages the round's velocity records in shared memory (one per thread)
+// and each warp keeps its cell's 8 rows in flight.  Per-lane FP32 partial
+// sums of q are flushed to FP64 every 32 blocks and reduced over the warp once.
 // ---------------------------------------------------------------------------
 template <int D, int NR, bool WALL, typename T>
 __device__ __forceinline__ void stage2_block(const BlockedArgs<T>& a, int c, int e0, int e1, int64_t m,
@@ -1085,18 +1086,20 @@ __device__ __forceinline__ void stage2_block(const BlockedArgs<T>& a, int c, int
 }
 
 template <int D, int NR, typename T>
-__global__ void __launch_bounds__(kBlockedThreads) k_bstage2(const BlockedArgs<T> a) {
-  constexpr int UNR = 8;
-  const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * (kBlockedThreads / 32) + (threadIdx.x >> 5);
-  if (c >= a.Nc) return;
+__global__ void __launch_bounds__(kBlockedThreads, sizeof(T) == 4 ? (NR == 1 ? 4 : 2) : 1) k_bstage2(const BlockedArgs<T> a) {
+  constexpr int UNR = kBlockedThreads / BV;  // blocks per round: one velocity record per thread of the CTA
+  __shared__ Vel4<T> sv[2][UNR * BV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * (kBlockedThreads / 32) + warp;
+  const bool valid = c < a.Nc;  // every warp takes part in the CTA barriers
+  const int cc = valid ? c : a.Nc - 1;
   const int chunk = blockIdx.y;
   const int64_t per = (a.M + a.nchunk - 1) / a.nchunk;
   const int64_t mb = int64_t(chunk) * per;
   const int64_t me = mb + per < a.M ? mb + per : a.M;
   const size_t sj = size_t(a.Nc) * BV, sr = size_t(a.M) * sj;
-  T* fc = a.f_next + size_t(c) * BV + lane;
-  const CellEq<T> E = a.ceq1[c];
+  T* fc = a.f_next + size_t(cc) * BV + lane;
+  const CellEq<T> E = a.ceq1[cc];
   const T lam = E.lam, beta1 = E.beta, pref = E.pref, s0 = E.s0, kap = E.kap, iv = E.inv_vol;
   const T inv1 = T(1) / (T(1) + beta1);
   T Uc[3], qc[3];
@@ -1105,60 +1108,55 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage2(const BlockedArgs<T
     Uc[d] = E.U[d];
     qc[d] = E.q[d];
   }
-  const int e0 = a.cf_off[c], e1 = a.cf_off[c + 1];
+  const int e0 = a.cf_off[cc], e1 = a.cf_off[cc + 1];
   bool has_wall = false;
   for (int e = e0; e < e1; ++e) has_wall |= (a.inc[e].flags & 1) != 0;
   double qd[3] = {0.0, 0.0, 0.0};
   T qp[3] = {T(0), T(0), T(0)};
-  int since_flush = 0;
-  int64_t m = mb;
-  if (!has_wall) {
-    // interior cells (almost all): UNR blocks in flight
-    for (; m + UNR <= me; m += UNR) {
-      T ft[UNR][NR];
-      Vel4<T> vq[UNR];
+
+  // round k covers blocks [m, m + UNR); its rows and velocity records are
+  // requested during round k - 1
+  auto load_rows = [&](int64_t m, T (&ft)[UNR][NR]) {
 #pragma unroll
-      for (int i = 0; i < UNR; ++i) {
+    for (int i = 0; i < UNR; ++i)
+      if (m + i < me)
 #pragma unroll
         for (int r = 0; r < NR; ++r) ft[i][r] = fc[r * sr + (m + i) * sj];
-        vq[i] = a.vel[(m + i) * BV + lane];
-      }
+  };
+  T ft[UNR][NR], fn[UNR][NR];
+  if (mb * BV + threadIdx.x < me * BV) sv[0][threadIdx.x] = a.vel[mb * BV + threadIdx.x];
+  if (valid) load_rows(mb, ft);
+  int k = 0;
+  for (int64_t m = mb; m < me; m += UNR, ++k) {
+    __syncthreads();  // round k's records are visible; round k - 1's slot is free
+    const int64_t mn = m + UNR;
+    if (mn * BV + threadIdx.x < me * BV) sv[(k + 1) & 1][threadIdx.x] = a.vel[mn * BV + threadIdx.x];
+    if (!valid) continue;
+    if (mn < me) load_rows(mn, fn);
 #pragma unroll
-      for (int i = 0; i < UNR; ++i)
-        stage2_block<D, NR, false, T>(a, c, e0, e1, m + i, lane, vq[i], ft[i], Uc, qc, pref, lam, s0, kap, beta1,
-                                      inv1, iv, fc, sr, sj, qp);
-      since_flush += UNR;
-      if (since_flush >= 32) {
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          qd[d] += double(qp[d]);
-          qp[d] = T(0);
-        }
-        since_flush = 0;
-      }
+    for (int i = 0; i < UNR; ++i) {
+      if (m + i >= me) break;
+      const Vel4<T> vq = sv[k & 1][i * BV + lane];
+      if (has_wall)
+        stage2_block<D, NR, true, T>(a, cc, e0, e1, m + i, lane, vq, ft[i], Uc, qc, pref, lam, s0, kap, beta1, inv1,
+                                     iv, fc, sr, sj, qp);
+      else
+        stage2_block<D, NR, false, T>(a, cc, e0, e1, m + i, lane, vq, ft[i], Uc, qc, pref, lam, s0, kap, beta1, inv1,
+                                      iv, fc, sr, sj, qp);
     }
-  }
-  // cells with a wall face, and the remainder
-  for (; m < me; ++m) {
-    T ft[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) ft[r] = fc[r * sr + m * sj];
-    const Vel4<T> vq = a.vel[m * BV + lane];
-    if (has_wall)
-      stage2_block<D, NR, true, T>(a, c, e0, e1, m, lane, vq, ft, Uc, qc, pref, lam, s0, kap, beta1, inv1, iv, fc, sr,
-                                   sj, qp);
-    else
-      stage2_block<D, NR, false, T>(a, c, e0, e1, m, lane, vq, ft, Uc, qc, pref, lam, s0, kap, beta1, inv1, iv, fc,
-                                    sr, sj, qp);
-    if (++since_flush >= 32) {
+    for (int i = 0; i < UNR; ++i)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) ft[i][r] = fn[i][r];
+    if ((k & 3) == 3) {  // flush the FP32 partial sums every 32 blocks
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         qd[d] += double(qp[d]);
         qp[d] = T(0);
       }
-      since_flush = 0;
     }
   }
+  if (!valid) return;
 #pragma unroll
   for (int d = 0; d < D; ++d) qd[d] = warp_sum(qd[d] + double(qp[d]));
   double* qo = a.qpart + (size_t(chunk) * a.Nc + c) * 3;

@@ -841,8 +841,8 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
       return fail(ctx, UGKS_ERR_UNSUPPORTED, "the blocked sweep needs fewer than 2^31 cells, faces and incidences");
     ctx->variant = 1;
   }
-  ctx->vb = p->block_velocities > 0 ? p->block_velocities / BV : 2;
-  if (ctx->vb > ctx->M) ctx->vb = 1;
+  ctx->vb = p->block_velocities > 0 ? p->block_velocities / BV : 4;
+  while (ctx->vb > ctx->M) ctx->vb /= 2;
   ctx->nchunk = int(std::min<int64_t>(ctx->M, 8));
 
   // ---- tiles of the tiled sweep ----
