@@ -330,6 +330,14 @@ def run_gpu(args):
         stats = solver.stats()
         res = solver.residual()
         W_end = solver.moments()
+        # surface quantities of the last step (pressure, shear, heat flux and
+        # C_p, C_t, C_h against the far-field state)
+        far = mesh.bc[1]
+        t0 = time.perf_counter()
+        faces, svals, scoef = solver.surface([far.rho, far.u[0], far.u[1], far.u[2], far.T])
+        surface = {"n_wall_faces": int(len(faces)), "ms": 1e3 * (time.perf_counter() - t0),
+                   "max_Cp": float(np.max(scoef[:, 0])), "max_Ch": float(np.max(scoef[:, 2])),
+                   "max_Ct": float(np.max(scoef[:, 1]))}
         solver.close()
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if dist is not None:
@@ -383,6 +391,7 @@ def run_gpu(args):
             "roofline": roofline, "kernels": kernels, "step_roofline": step_views,
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": count_launches(stats),
+            "surface": surface,
             "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in stats.items()},
             "clocks": clk}
     print(json.dumps(line), flush=True)

@@ -174,6 +174,24 @@ ugks_status ugks_moments(ugks_ctx *ctx, double *W_out, double *q_out);
  * R_m = sqrt(sum_i (W_im^{n+1} - W_im^n)^2 / n_cells).  Zero before any step. */
 ugks_status ugks_residual(ugks_ctx *ctx, double *res_out);
 
+/* Surface quantities of the last step on every diffuse-wall face, from the
+ * moments of the wall flux (Sec. 2.1; the paper evaluates the macroscopic
+ * surface quantities from the moments of the wall flux without printing
+ * formulas, read here as): with n the face normal pointing out of the gas,
+ * F the time-integrated face flux of Eq. 28 and P = F_momentum / dt,
+ *   p_w = P . n,  tau_w = P - p_w n,  q_w = (F_energy - U_w . F_momentum) / dt.
+ * faces[n] receives the wall faces (original indices, ascending) and
+ * vals[n][dim+2] the values (p_w, tau_w[0..dim-1], q_w).  If freestream =
+ * (rho, U[0..dim-1], T) is not NULL, coef[n][3] receives
+ *   C_p = (p_w - rho T/2) / (rho |U|^2 / 2),  C_t = |tau_w| / (rho |U|^2 / 2),
+ *   C_h = q_w / (rho |U|^3 / 2).
+ * *n_wall always receives the number of wall faces; the arrays must hold at
+ * least that many (cap), else UGKS_ERR_INVALID_ARGUMENT.  Zero before the
+ * first step.  Synchronises the context stream.  Blocked sweep only
+ * (UGKS_ERR_UNSUPPORTED for the tiled sweep). */
+ugks_status ugks_surface(ugks_ctx *ctx, const double *freestream, int64_t cap, int64_t *n_wall, int64_t *faces,
+                         double *vals, double *coef);
+
 /* Time step in use. */
 ugks_status ugks_dt(const ugks_ctx *ctx, double *dt_out);
 

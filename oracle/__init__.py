@@ -69,7 +69,9 @@ def load():
         lib = ctypes.CDLL(_LIB_PATH)
         P = ctypes.c_void_p
         lib.orc_run.restype = ctypes.c_int
-        lib.orc_run.argtypes = [P, ctypes.c_int64, P, P, P, P, P, ctypes.c_int32, P, P]
+        lib.orc_run.argtypes = [P, ctypes.c_int64, P, P, P, P, P, ctypes.c_int32, P, P, P]
+        lib.orc_surface.argtypes = [P, P, ctypes.c_double, P, P, P, P]
+        lib.orc_surface.restype = ctypes.c_int64
         lib.orc_time_step.restype = ctypes.c_double
         lib.orc_time_step.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_double]
         lib.orc_time_coefficients.argtypes = [ctypes.c_double, ctypes.c_double, P]
@@ -147,10 +149,11 @@ def time_step(mesh, vgrid, cfl: float) -> float:
 
 
 def run(mesh, vgrid, gas, W: np.ndarray, f: np.ndarray, nsteps: int, block_v: int = 0, p_v: int = 0,
-        dt: Optional[float] = None) -> Tuple[np.ndarray, np.ndarray, float, np.ndarray]:
+        dt: Optional[float] = None, face_flux: bool = False):
     """Advance (W, f) by nsteps UGKS steps.  Returns (W, f, dt, diag) where diag
     has one row per step: residual per conservative variable, then the largest
-    |wall mass flux|."""
+    |wall mass flux|; with face_flux=True also the last step's macro fluxes
+    F[face, 5] (time-integrated, Eq. 28)."""
     lib = load()
     pk = _Packed(mesh)
     prm = _params(gas, block_v, p_v, dt)
@@ -160,12 +163,33 @@ def run(mesh, vgrid, gas, W: np.ndarray, f: np.ndarray, nsteps: int, block_v: in
     f = _f64(f).copy()
     assert f.shape == (n_reduced(mesh.dim, gas.K), mesh.n_cells, vgrid.n_v)
     diag = np.zeros((max(nsteps, 1), mesh.dim + 3))
+    F = np.zeros((mesh.n_faces, 5))
     dt_out = ctypes.c_double(0.0)
     rc = lib.orc_run(ctypes.addressof(pk.s), vgrid.n_v, _p(u), _p(w), ctypes.addressof(prm), _p(W), _p(f),
-                     int(nsteps), ctypes.addressof(dt_out), _p(diag))
+                     int(nsteps), ctypes.addressof(dt_out), _p(diag), _p(F))
     if rc != 0:
         raise RuntimeError("oracle step failed (non-physical state or unsupported mesh)")
+    if face_flux:
+        return W, f, dt_out.value, diag[:nsteps], F
     return W, f, dt_out.value, diag[:nsteps]
+
+
+def surface(mesh, F: np.ndarray, dt: float, freestream=None):
+    """Surface quantities of the diffuse-wall faces from their time-integrated
+    fluxes F (reading R20): (faces, vals[:, p_w, tau_w[dim], q_w], coef[:, C_p,
+    C_t, C_h] or None)."""
+    lib = load()
+    pk = _Packed(mesh)
+    F = _f64(F)
+    nwall = int(np.sum([(mesh.bc[-j - 1].type == 1) for j in mesh.face_neighbor if j < 0]))
+    faces = np.zeros(max(nwall, 1), dtype=np.int64)
+    vals = np.zeros((max(nwall, 1), mesh.dim + 2))
+    coef = np.zeros((max(nwall, 1), 3))
+    fs = None if freestream is None else _f64(freestream)
+    n = lib.orc_surface(ctypes.addressof(pk.s), _p(F), float(dt), _p(fs) if fs is not None else None, _p(faces),
+                        _p(vals), _p(coef))
+    assert n == nwall
+    return faces[:n], vals[:n], (coef[:n] if fs is not None else None)
 
 
 def time_coefficients(dt: float, tau: float) -> np.ndarray:

@@ -31,6 +31,11 @@
  *   R12 stage 2 uses the lagged heat flux q^n.
  *   R13 residual R_m = sqrt(mean_i (dW_im)^2).
  *   R17/18 stage 1 uses q^n; the initial f is the discrete Maxwellian.
+ *   R20 surface quantities of a wall face from the moments F of its
+ *      time-integrated flux (n out of the gas, P = F_momentum / dt):
+ *      p_w = P.n, tau_w = P - p_w n, q_w = (F_energy - U_w.F_momentum) / dt;
+ *      coefficients against a free stream (rho, U, T): C_p = (p_w - rho T/2)
+ *      / (rho|U|^2/2), C_t = |tau_w| / (rho|U|^2/2), C_h = q_w / (rho|U|^3/2).
  * Parity: every function below is pinned by tests/test_oracle_pins.py.
  */
 #include <math.h>
@@ -610,7 +615,7 @@ static void ghost_W(int D, int K, const orc_bc *bc, const double *Wi, double *Wg
 }
 
 int orc_step(const orc_mesh *m, int64_t nv, const double *u, const double *w, const orc_params *p,
-             double dt, double *W, double *f, double *diag) {
+             double dt, double *W, double *f, double *diag, double *F_out) {
   const int D = m->dim, K = p->K, nw = D + 2;
   const int Kxi = K + 3 - D, nr = Kxi > 0 ? 2 : 1;
   const int shakhov = p->model == 1;
@@ -1005,6 +1010,7 @@ int orc_step(const orc_mesh *m, int64_t nv, const double *u, const double *w, co
   }
   if (bad) goto fail;
   memcpy(W, Wnew, sizeof(double) * Nc * nw);
+  if (F_out) memcpy(F_out, F, sizeof(double) * Nf * NW);
   if (diag) {
     for (int t = 0; t < nw; ++t) diag[t] = sqrt(res[t] / Nc);
     diag[nw] = wall_mass_max;
@@ -1019,15 +1025,58 @@ fail:
 }
 
 /* Runs n steps; dt from reading R4 unless p->dt_override > 0.  diag receives
- * nsteps rows of (residual[nw], max |wall mass flux|). */
+ * nsteps rows of (residual[nw], max |wall mass flux|); F_out (if not NULL)
+ * the macro fluxes F[face][5] of the last step. */
 int orc_run(const orc_mesh *m, int64_t nv, const double *u, const double *w, const orc_params *p,
-            double *W, double *f, int32_t nsteps, double *dt_out, double *diag) {
+            double *W, double *f, int32_t nsteps, double *dt_out, double *diag, double *F_out) {
   double dt = p->dt_override > 0.0 ? p->dt_override : orc_time_step(m, nv, u, w, p->cfl);
   if (dt_out) *dt_out = dt;
   for (int32_t s = 0; s < nsteps; ++s) {
-    if (orc_step(m, nv, u, w, p, dt, W, f, diag ? diag + (size_t)s * (m->dim + 3) : NULL)) return 1;
+    if (orc_step(m, nv, u, w, p, dt, W, f, diag ? diag + (size_t)s * (m->dim + 3) : NULL,
+                 s == nsteps - 1 ? F_out : NULL)) return 1;
   }
   return 0;
+}
+
+/* Surface quantities of every diffuse-wall face (reading R20), wall faces in
+ * ascending face order: faces[i], vals[i] = (p_w, tau_w[0..D-1], q_w) and, if
+ * freestream = (rho, U[0..D-1], T) is given, coef[i] = (C_p, C_t, C_h).
+ * Returns the number of wall faces. */
+int64_t orc_surface(const orc_mesh *m, const double *F, double dt, const double *freestream, int64_t *faces,
+                    double *vals, double *coef) {
+  const int D = m->dim;
+  int64_t nw_ = 0;
+  for (int64_t fidx = 0; fidx < m->n_faces; ++fidx) {
+    int64_t j = m->nei[fidx];
+    if (j >= 0 || m->bc[-j - 1].type != 1) continue;
+    const orc_bc *bc = &m->bc[-j - 1];
+    const double *n = m->nrm + fidx * D, *Ff = F + fidx * NW;
+    double P[MAXD], pn = 0.0, work = 0.0;
+    for (int d = 0; d < D; ++d) {
+      P[d] = Ff[1 + d] / dt;
+      pn += P[d] * n[d];
+      work += bc->u[d] * Ff[1 + d];
+    }
+    double *v = vals + nw_ * (D + 2);
+    v[0] = pn;
+    double t2 = 0.0;
+    for (int d = 0; d < D; ++d) {
+      v[1 + d] = P[d] - pn * n[d];
+      t2 += v[1 + d] * v[1 + d];
+    }
+    v[D + 1] = (Ff[D + 1] - work) / dt;
+    if (freestream && coef) {
+      double rho = freestream[0], U2 = 0.0, T = freestream[D + 1];
+      for (int d = 0; d < D; ++d) U2 += freestream[1 + d] * freestream[1 + d];
+      double qdyn = 0.5 * rho * U2;
+      coef[nw_ * 3 + 0] = (pn - 0.5 * rho * T) / qdyn;
+      coef[nw_ * 3 + 1] = sqrt(t2) / qdyn;
+      coef[nw_ * 3 + 2] = v[D + 1] / (qdyn * sqrt(U2));
+    }
+    faces[nw_] = fidx;
+    ++nw_;
+  }
+  return nw_;
 }
 
 int orc_num_threads(void) {

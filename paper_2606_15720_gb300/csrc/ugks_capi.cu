@@ -81,6 +81,12 @@ struct ugks_ctx {
   void* d_fpoly = nullptr;
   void *d_ceq0 = nullptr, *d_ceq1 = nullptr;
   double *d_Facc_b = nullptr, *d_qpart = nullptr;
+  // surface quantities: diffuse-wall faces (ascending), output buffers, the
+  // face accumulators of the last step
+  std::vector<int64_t> walls;
+  int64_t* d_walls = nullptr;
+  double *d_surf = nullptr, *d_freestream = nullptr;
+  const double* last_facc = nullptr;
   int nchunk = 1;
   int nsm = 1;
   // tiles and scratch of the tiled sweep
@@ -419,6 +425,8 @@ ugks_status build_typed(ugks_ctx* ctx, const std::vector<int64_t>& cf_off, const
     CUDA_TRY(ctx, dalloc(ctx, &X, blocked_X_bytes<T>(ctx)));
     ctx->d_X = X;
     CUDA_TRY(ctx, dalloc(ctx, &ctx->d_Facc_b, blocked_Facc_bytes(ctx)));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_Facc_b, 0, blocked_Facc_bytes(ctx), ctx->stream));
+    ctx->last_facc = ctx->d_Facc_b;
     CUDA_TRY(ctx, dalloc(ctx, &ctx->d_qpart, blocked_qpart_bytes(ctx)));
   }
   const size_t fsz = size_t(ctx->NR) * ctx->M * ctx->Nc * BV * sizeof(T);
@@ -535,6 +543,7 @@ ugks_status step_typed(ugks_ctx* ctx) {
   if (ctx->variant == 2) {
     ugks_status st = sweep_blocked<T>(ctx, cur, ctx->d_X, ctx->d_Facc_b, ctx->d_qpart);
     if (st != UGKS_OK) return st;
+    ctx->last_facc = ctx->d_Facc_b;
     record_start(ctx, kTRes, &ev);
     launch_residual_finalize(ctx->stream, ctx->D + 2, ctx->Nc, ctx->d_res_acc, ctx->d_res);
     CUDA_TRY(ctx, cudaGetLastError());
@@ -625,6 +634,7 @@ ugks_status step_typed_static(ugks_ctx* ctx, unsigned char* base) {
     ugks_status st = sweep_blocked<T>(ctx, cur, X, reinterpret_cast<double*>(Facc), reinterpret_cast<double*>(qpart));
     ctx->stats_on = was_on;
     if (st != UGKS_OK) return st;
+    ctx->last_facc = reinterpret_cast<double*>(Facc);
     launch_residual_finalize(ctx->stream, ctx->D + 2, ctx->Nc, ctx->d_res_acc, ctx->d_res);
     CUDA_TRY(ctx, cudaGetLastError());
     ctx->cur = nxt;
@@ -761,6 +771,10 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
     g.bc_type = nb >= 0 ? 0 : m->bc[-nb - 1].type;
     g.pad = 0;
   }
+  // ---- diffuse-wall faces (surface quantities) ----
+  for (int64_t f = 0; f < Nf; ++f)
+    if (fg[f].bc_type == UGKS_BC_WALL) ctx->walls.push_back(f);
+
   // ---- incidence CSR with least-squares weights ----
   std::vector<int64_t> cf_off(Nc + 1, 0);
   for (int64_t f = 0; f < Nf; ++f) {
@@ -1018,6 +1032,12 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
   CUDA_TRY(ctx, upload(ctx, &ctx->d_fcent, fcent.data(), Nf * 3 * sizeof(double)));
   CUDA_TRY(ctx, upload(ctx, &ctx->d_fshift, fshift.data(), Nf * 3 * sizeof(double)));
   CUDA_TRY(ctx, upload(ctx, &ctx->d_bcs, bcs.data(), bcs.size() * sizeof(BCDev)));
+  {
+    const size_t nwall = ctx->walls.size();
+    CUDA_TRY(ctx, upload(ctx, &ctx->d_walls, ctx->walls.data(), nwall * sizeof(int64_t)));
+    CUDA_TRY(ctx, dalloc(ctx, &ctx->d_surf, nwall * (D + 2 + 3) * sizeof(double)));
+    CUDA_TRY(ctx, dalloc(ctx, &ctx->d_freestream, 5 * sizeof(double)));
+  }
   CUDA_TRY(ctx, upload(ctx, &ctx->d_u, uflat.data(), uflat.size() * sizeof(double)));
   CUDA_TRY(ctx, upload(ctx, &ctx->d_wgt, v->weight, v->n_v * sizeof(double)));
   CUDA_TRY(ctx, upload(ctx, &ctx->d_ux, ux.data(), Mp * sizeof(double)));
@@ -1149,6 +1169,43 @@ ugks_status ugks_residual(ugks_ctx* ctx, double* res_out) {
   ugks_status st = check_status(ctx);
   if (st != UGKS_OK) return st;
   CUDA_TRY(ctx, cudaMemcpy(res_out, ctx->d_res, (ctx->D + 2) * sizeof(double), cudaMemcpyDeviceToHost));
+  return UGKS_OK;
+}
+
+ugks_status ugks_surface(ugks_ctx* ctx, const double* freestream, int64_t cap, int64_t* n_wall, int64_t* faces,
+                         double* vals, double* coef) {
+  if (!ctx || !n_wall) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "NULL argument");
+  const int64_t nwall = int64_t(ctx->walls.size());
+  *n_wall = nwall;
+  if (ctx->variant != 2)
+    return fail(ctx, UGKS_ERR_UNSUPPORTED, "ugks_surface needs the blocked sweep (sweep = UGKS_SWEEP_BLOCKED or AUTO)");
+  if (nwall == 0) return UGKS_OK;
+  if (cap < nwall || !faces || !vals || (freestream && !coef))
+    return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "ugks_surface: %lld wall faces need arrays of that capacity",
+                (long long)nwall);
+  const int D = ctx->D;
+  if (freestream) {
+    double U2 = 0.0;
+    for (int d = 0; d < D; ++d) U2 += freestream[1 + d] * freestream[1 + d];
+    if (!(freestream[0] > 0.0) || !(U2 > 0.0))
+      return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "ugks_surface: the free stream needs rho > 0 and |U| > 0");
+  }
+  ugks_status st = check_status(ctx);
+  if (st != UGKS_OK) return st;
+  double fs[5] = {0, 0, 0, 0, 0};
+  if (freestream)
+    for (int t = 0; t < D + 2; ++t) fs[t] = freestream[t];
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_freestream, fs, sizeof(fs), cudaMemcpyHostToDevice, ctx->stream));
+  double* d_vals = ctx->d_surf;
+  double* d_coef = ctx->d_surf + nwall * (D + 2);
+  launch_surface(ctx->stream, nwall, D, ctx->dt, ctx->d_walls, ctx->last_facc, FACC_W, ctx->d_fnormal, ctx->d_fnei,
+                 ctx->d_bcs, freestream ? ctx->d_freestream : nullptr, d_vals, d_coef);
+  CUDA_TRY(ctx, cudaGetLastError());
+  CUDA_TRY(ctx, cudaMemcpyAsync(vals, d_vals, nwall * (D + 2) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (freestream)
+    CUDA_TRY(ctx, cudaMemcpyAsync(coef, d_coef, nwall * 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  std::copy(ctx->walls.begin(), ctx->walls.end(), faces);
   return UGKS_OK;
 }
 

@@ -39,6 +39,10 @@ void launch_scatter_f(cudaStream_t s, int64_t Nc, int64_t M, int NR, int64_t nv,
 
 void launch_residual_finalize(cudaStream_t s, int nw, int64_t Nc, const double* acc, double* res);
 
+void launch_surface(cudaStream_t s, int64_t nwall, int D, double dt, const int64_t* walls, const double* Facc,
+                    int facc_stride, const double* fnormal, const int64_t* fnei, const BCDev* bcs,
+                    const double* freestream, double* vals, double* coef);
+
 // Arguments of the persistent velocity-block sweep (ugks_sweep.cu).
 template <typename T>
 struct SweepArgs {

@@ -659,6 +659,55 @@ __global__ void k_face(int64_t Nf, Gas g, const double* W, const double* gW, con
 }
 
 // ---------------------------------------------------------------------------
+// Surface quantities of the diffuse-wall faces from the moments of their
+// time-integrated flux F (FP64; Sec. 2.1: the macroscopic surface quantities
+// follow from the moments of the wall flux).  With n the face normal out of
+// the gas and P = F_momentum / dt: p_w = P.n, tau_w = P - p_w n,
+// q_w = (F_energy - U_w.F_momentum) / dt; optionally the coefficients against
+// a free stream (rho, U, T): C_p = (p_w - rho T/2) / (rho|U|^2/2),
+// C_t = |tau_w| / (rho|U|^2/2), C_h = q_w / (rho|U|^3/2).  One thread per wall face.
+// ---------------------------------------------------------------------------
+__global__ void k_surface(int64_t nwall, int D, double dt, const int64_t* walls, const double* Facc, int facc_stride,
+                          const double* fnormal, const int64_t* fnei, const BCDev* bcs, const double* freestream,
+                          double* vals, double* coef) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= nwall) return;
+  const int64_t f = walls[i];
+  const double* F = Facc + f * facc_stride;
+  const BCDev& bc = bcs[-fnei[f] - 1];
+  double P[3] = {0.0, 0.0, 0.0}, pn = 0.0, work = 0.0;
+  for (int d = 0; d < D; ++d) {
+    P[d] = F[1 + d] / dt;
+    pn += P[d] * fnormal[f * 3 + d];
+    work += bc.u[d] * F[1 + d];
+  }
+  double* v = vals + i * (D + 2);
+  v[0] = pn;
+  double t2 = 0.0;
+  for (int d = 0; d < D; ++d) {
+    v[1 + d] = P[d] - pn * fnormal[f * 3 + d];
+    t2 += v[1 + d] * v[1 + d];
+  }
+  v[D + 1] = (F[D + 1] - work) / dt;
+  if (freestream) {
+    double U2 = 0.0;
+    for (int d = 0; d < D; ++d) U2 += freestream[1 + d] * freestream[1 + d];
+    const double rho = freestream[0], T = freestream[D + 1], qdyn = 0.5 * rho * U2;
+    coef[i * 3 + 0] = (pn - 0.5 * rho * T) / qdyn;
+    coef[i * 3 + 1] = sqrt(t2) / qdyn;
+    coef[i * 3 + 2] = v[D + 1] / (qdyn * sqrt(U2));
+  }
+}
+
+void launch_surface(cudaStream_t s, int64_t nwall, int D, double dt, const int64_t* walls, const double* Facc,
+                    int facc_stride, const double* fnormal, const int64_t* fnei, const BCDev* bcs,
+                    const double* freestream, double* vals, double* coef) {
+  if (nwall <= 0) return;
+  k_surface<<<unsigned((nwall + 127) / 128), 128, 0, s>>>(nwall, D, dt, walls, Facc, facc_stride, fnormal, fnei, bcs,
+                                                   freestream, vals, coef);
+}
+
+// ---------------------------------------------------------------------------
 // Moments of the stored distribution: heat flux (Eq. 13) about U of W, and
 // the discrete conservative moments (Eq. 10, 21).  One warp per cell.
 // ---------------------------------------------------------------------------

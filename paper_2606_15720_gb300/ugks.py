@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
         "ugks_stats_enable": [P, I32],
         "ugks_stats": [P, I32, P, P, P, P],
         "ugks_solve": [P, P, P, P, I32, P, P],
+        "ugks_surface": [P, P, I64, P, P, P, P],
         "ugks_destroy": [P],
     }
     for name, args in sig.items():
@@ -204,6 +205,20 @@ class Solver:
         v = ctypes.c_double()
         self._c(self._lib.ugks_dt(self._ctx, ctypes.byref(v)))
         return v.value
+
+    def surface(self, freestream: Optional[Sequence[float]] = None):
+        """ugks_surface: (faces, vals[:, p_w, tau_w[dim], q_w], coef[:, C_p, C_t, C_h] or None)
+        of the diffuse-wall faces after the last step."""
+        n = ctypes.c_int64()
+        fs = None if freestream is None else np.ascontiguousarray(freestream, dtype=np.float64)
+        cap = sum(1 for j in self.mesh.face_neighbor if j < 0 and self.mesh.bc[-j - 1].type == 1)
+        faces = np.zeros(max(cap, 1), dtype=np.int64)
+        vals = np.zeros((max(cap, 1), self.dim + 2))
+        coef = np.zeros((max(cap, 1), 3))
+        self._c(self._lib.ugks_surface(self._ctx, _ptr(fs), cap, ctypes.byref(n), _ptr(faces), _ptr(vals),
+                                       _ptr(coef)))
+        k = n.value
+        return faces[:k], vals[:k], (coef[:k] if fs is not None else None)
 
     def get_f(self, cells: Sequence[int]) -> np.ndarray:
         cells = np.ascontiguousarray(cells, dtype=np.int64)

@@ -278,3 +278,41 @@ def test_nonphysical_state_is_reported(U):
         with pytest.raises(U.UGKSError) as e:
             s.moments()
         assert e.value.status == 6
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-11), ("f32", 1e-5)])
+@pytest.mark.parametrize("name", ["cavity_shakhov", "sphere_tet"])
+def test_surface_quantities_match_oracle(U, name, storage, tol):
+    """ugks_surface (reading R20: pressure, tangential stress and heat flux of
+    every diffuse-wall face from the moments of its flux, and C_p, C_t, C_h)
+    against the oracle's surface quantities after one step, element by element,
+    relative to each quantity's largest magnitude."""
+    mesh, grid, gas, prim = CASES[name]()
+    W0 = I.prim_to_conservative(prim, mesh.dim, gas.K)
+    far = [b for b in mesh.bc if b.type == I.BC_FARFIELD]
+    ref = far[0] if far else mesh.bc[0]
+    fs = [1.0] + [ref.u[d] if far else (0.14606 if d == 0 else 0.0) for d in range(mesh.dim)] + [1.0]
+    with U.Solver(mesh, grid, gas, W0, storage=storage) as s:
+        dt = s.dt
+        s.step(1)
+        faces, vals, coef = s.surface(fs)
+        f2, v2, c2 = s.surface()
+    _, _, _, _, F = O.run(mesh, grid, gas, W0, O.initial_f(mesh, grid, W0, gas.K), 1, dt=dt, face_flux=True)
+    of, ov, oc = O.surface(mesh, F, dt, fs)
+    assert len(faces) > 0 and np.array_equal(faces, of) and np.array_equal(f2, of) and c2 is None
+    np.testing.assert_array_equal(vals, v2)
+    for col in range(ov.shape[1]):
+        scale = max(np.max(np.abs(ov[:, col])), np.max(np.abs(ov[:, 0])) * 1e-3)
+        assert np.max(np.abs(vals[:, col] - ov[:, col])) <= tol * scale, (col, np.max(np.abs(vals[:, col] - ov[:, col])) / scale)
+    for col in range(3):
+        scale = np.max(np.abs(oc[:, col]))
+        assert np.max(np.abs(coef[:, col] - oc[:, col])) <= tol * scale, col
+
+
+def test_surface_is_refused_for_the_tiled_sweep(U):
+    mesh, grid, gas, prim = cavity_case(n=8, nvx=10)
+    with U.Solver(mesh, grid, gas, I.prim_to_conservative(prim, 2, 0), storage="f64", sweep="tiled") as s:
+        s.step(1)
+        with pytest.raises(U.UGKSError) as e:
+            s.surface()
+        assert e.value.status == 8

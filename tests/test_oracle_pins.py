@@ -552,3 +552,72 @@ def test_two_dimensional_shock_tube_is_rotation_invariant_and_matches_riemann():
     np.testing.assert_allclose(swapped, Wx, rtol=1e-11, atol=1e-12)
     exact = _exact_sod(xs[::2], 0.1)
     assert float(np.mean(np.abs(Wx[::2, 0] - exact))) < 3e-2
+
+
+def _half_moments(U, lam, kmax):
+    """I_k = int_0^inf u^k (lam/pi)^(1/2) exp(-lam (u - U)^2) du, k = 0..kmax, from
+    I_0 = erfc(-s)/2, I_1 = U I_0 + exp(-s^2)/(2 sqrt(pi lam)) (s = U sqrt(lam)) and
+    I_(k+1) = U I_k + k/(2 lam) I_(k-1) (integration by parts)."""
+    from scipy.special import erfc
+    s = U * math.sqrt(lam)
+    I = [0.5 * erfc(-s), U * 0.5 * erfc(-s) + math.exp(-s * s) / (2.0 * math.sqrt(math.pi * lam))]
+    for k in range(1, kmax):
+        I.append(U * I[k] + k / (2.0 * lam) * I[k - 1])
+    return I
+
+
+def test_surface_quantities_of_a_drifting_gas_at_a_diffuse_wall():
+    """Reading R20 (surface quantities from the moments of the wall flux, Sec. 2.1)
+    on one step of a uniform drifting gas in a closed box of stationary diffuse
+    walls: the gradients vanish, so each wall flux is dt times the incident half
+    of the Maxwellian plus the re-emitted wall Maxwellian with rho_w from
+    non-penetration (Eq. 36-38).  Pressure, tangential stress and heat flux
+    against the closed-form half-range Gaussian moments (midpoint quadrature of
+    spacing 0.1: agreement to 1e-3 of the momentum-flux scale)."""
+    rho, U, T, Tw, Kxi = 1.0, np.array([0.3, -0.2]), 1.2, 0.9, 1
+    mesh = I.cavity_mesh(4, lid_speed=0.0, T_wall=Tw)
+    grid = I.midpoint_grid(160, -8.0, 8.0, 2)
+    gas = I.Gas(model="bgk", K=0, omega=0.81, mu_ref=0.05, cfl=0.5)
+    prim = I.uniform_primitives(mesh, rho, (U[0], U[1], 0.0), T)
+    W0 = I.prim_to_conservative(prim, 2, 0)
+    f0 = O.initial_f(mesh, grid, W0, 0)
+    _, _, dt, _, F = O.run(mesh, grid, gas, W0, f0, 1, face_flux=True)
+    faces, vals, coef = O.surface(mesh, F, dt, freestream=[rho, U[0], U[1], T])
+    assert len(faces) == 16
+    lam, lw = 1.0 / T, 1.0 / Tw
+    J1 = -1.0 / (2.0 * math.sqrt(math.pi * lw))
+    J2 = 1.0 / (4.0 * lw)
+    J3 = -1.0 / (2.0 * lw * math.sqrt(math.pi * lw))
+    for fi, v, c in zip(faces, vals, coef):
+        n = mesh.face_normal[fi]
+        t = np.array([-n[1], n[0]])
+        Un, Ut = float(U @ n), float(U @ t)
+        Ik = _half_moments(Un, lam, 3)
+        rho_w = -rho * Ik[1] / J1
+        p_w = rho * Ik[2] + rho_w * J2
+        tau = rho * Ut * Ik[1] * t
+        q_w = 0.5 * rho * (Ik[3] + Ik[1] * (Ut * Ut + (1 + Kxi) / (2.0 * lam))) + \
+            0.5 * rho_w * (J3 + J1 * (1 + Kxi) / (2.0 * lw))
+        scale = rho * (Un * Un + Ut * Ut + T)
+        assert abs(v[0] - p_w) <= 1e-3 * scale, (fi, v[0], p_w)
+        assert np.max(np.abs(v[1:3] - tau)) <= 1e-3 * scale, (fi, v[1:3], tau)
+        assert abs(v[3] - q_w) <= 1e-3 * scale * math.sqrt(T), (fi, v[3], q_w)
+        qdyn = 0.5 * rho * float(U @ U)
+        assert c[0] == pytest.approx((v[0] - 0.5 * rho * T) / qdyn, rel=1e-12)
+        assert c[1] == pytest.approx(float(np.linalg.norm(v[1:3])) / qdyn, rel=1e-12)
+        assert c[2] == pytest.approx(v[3] / (qdyn * math.sqrt(float(U @ U))), rel=1e-12)
+
+
+def test_surface_quantities_of_a_gas_at_rest_in_equilibrium_with_the_wall():
+    """Gas at rest at the wall temperature: p_w = rho T / 2 (R = 1/2), no
+    tangential stress, no heat flux."""
+    rho, T = 1.3, 1.1
+    mesh = I.cavity_mesh(4, lid_speed=0.0, T_wall=T)
+    grid = I.midpoint_grid(120, -7.0, 7.0, 2)
+    gas = I.Gas(model="bgk", K=0, omega=0.81, mu_ref=0.05, cfl=0.5)
+    W0 = I.prim_to_conservative(I.uniform_primitives(mesh, rho, (0.0, 0.0, 0.0), T), 2, 0)
+    _, _, dt, _, F = O.run(mesh, grid, gas, W0, O.initial_f(mesh, grid, W0, 0), 1, face_flux=True)
+    faces, vals, _ = O.surface(mesh, F, dt)
+    np.testing.assert_allclose(vals[:, 0], 0.5 * rho * T, rtol=2e-3)
+    assert np.max(np.abs(vals[:, 1:3])) <= 1e-12
+    assert np.max(np.abs(vals[:, 3])) <= 2e-3 * rho * T ** 1.5
