@@ -89,6 +89,7 @@ def flops_stage1(inc):      # per cell-velocity
 
 FLOPS_STAGE2 = 34           # per cell-velocity
 BYTES_STAGE = 8             # per DOF and stage update: read + write of an FP32 f value
+BYTES_STAGE_SCALED = 2 * (2 + 4 / 32)   # FP16 / BF16 value + its row's FP32 scale, read + write
 
 
 def sweep_source_hash():
@@ -218,7 +219,7 @@ def run_reference(args):
     return 0
 
 
-def rooflines(stats, mesh, grid, dof, steps):
+def rooflines(stats, mesh, grid, dof, steps, bytes_stage=BYTES_STAGE):
     """Per-kernel rooflines of the blocked sweep from the library's event
     timings (CUDA events on the stream the kernels run on), the roofline of
     the dominant kernel, and the whole-step HBM and ALU views."""
@@ -228,7 +229,7 @@ def rooflines(stats, mesh, grid, dof, steps):
     nv = grid.n_v
     traffic = recorded_traffic()
     per_dof = {"block_reconstruction": (flops_recon(inc), 0), "block_fluxes": (FLOPS_FLUX * mesh.n_faces / mesh.n_cells, 0),
-               "block_stage1": (flops_stage1(inc), BYTES_STAGE), "stage2": (FLOPS_STAGE2, BYTES_STAGE)}
+               "block_stage1": (flops_stage1(inc), bytes_stage), "stage2": (FLOPS_STAGE2, bytes_stage)}
     kernels = {}
     for name, (fl, by) in per_dof.items():
         ms, n = stats.get(name, (0.0, 0))
@@ -265,9 +266,10 @@ def rooflines(stats, mesh, grid, dof, steps):
     if sweep_n:
         t = sweep_ms / sweep_n * 1e-3
         fl = sum(v["flops_per_dof"] for v in kernels.values())
+        bstep = 2 * bytes_stage
         step_views = {"sweep_ms": sweep_ms / sweep_n,
-                      "hbm": {"bytes_per_dof": 16, "achieved_gbs": 16 * dof / t / 1e9,
-                              "frac": 16 * dof / t / 1e9 / hbm_peak, "peak": hbm_peak, "peak_kind": peak_kind},
+                      "hbm": {"bytes_per_dof": bstep, "achieved_gbs": bstep * dof / t / 1e9,
+                              "frac": bstep * dof / t / 1e9 / hbm_peak, "peak": hbm_peak, "peak_kind": peak_kind},
                       "alu": {"flops_per_dof": fl, "achieved_tflops": fl * dof / t / 1e12,
                               "frac": fl * dof / t / 1e12 / fp32_peak, "peak": fp32_peak}}
     return roofline, kernels, step_views
@@ -309,8 +311,8 @@ def run_gpu(args):
             dist.barrier()
 
     with torch.cuda.stream(stream):
-        solver = U.Solver(mesh, grid, gas, W0, storage="f32", stream=int(stream.cuda_stream), sweep=args.sweep,
-                          block_velocities=args.block_velocities)
+        solver = U.Solver(mesh, grid, gas, W0, storage=args.storage, stream=int(stream.cuda_stream),
+                          sweep=args.sweep, block_velocities=args.block_velocities)
         assert solver.n_reduced == n_reduced
         solver.step(args.warmup)
         solver.residual()
@@ -346,7 +348,8 @@ def run_gpu(args):
     ms_per_step = ms_max / args.steps
     value = dof * world / (ms_per_step * 1e-3)
 
-    roofline, kernels, step_views = rooflines(stats, mesh, grid, dof, args.steps)
+    roofline, kernels, step_views = rooflines(stats, mesh, grid, dof, args.steps,
+                                              BYTES_STAGE if args.storage == "f32" else BYTES_STAGE_SCALED)
 
     # end to end through the one-shot C call with host buffers: mesh, grid and
     # W_init copied in, n steps, W and the residual copied out
@@ -354,7 +357,7 @@ def run_gpu(args):
         e2e = None
     barrier()
     t0 = time.perf_counter()
-    W_e2e, res_e2e = U.solve(mesh, grid, gas, W0, args.steps if not args.no_e2e else 0, storage="f32",
+    W_e2e, res_e2e = U.solve(mesh, grid, gas, W0, args.steps if not args.no_e2e else 0, storage=args.storage,
                              sweep=args.sweep, block_velocities=args.block_velocities)
     e2e_s = time.perf_counter() - t0
     barrier()
@@ -379,12 +382,15 @@ def run_gpu(args):
         cpu = cpu_baseline(mesh, grid, gas, W0)
     workload = WORKLOAD if (args.cells, args.nv_axis) == (MESH_CELLS, NV_AXIS) else \
         f"sphere_tet{args.cells // 1000}k_v{args.nv_axis}cube_shakhov_fp32 (reduced size for profiling)"
+    if args.storage != "f32":
+        workload = workload.replace("fp32", args.storage + "_scaled_storage")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "fp32" if args.storage == "f32" else f"fp32 arithmetic, {args.storage} storage",
+            "data": "synthetic",
             "config": {"workload": workload, "n_cells": mesh.n_cells, "n_faces": mesh.n_faces, "n_v": grid.n_v,
                        "n_reduced": n_reduced, "dof_per_step": dof, "parallelism": f"replicas x{world}",
-                       "sweep": args.sweep, "block_velocities": args.block_velocities,
+                       "sweep": args.sweep, "block_velocities": args.block_velocities, "storage": args.storage,
                        "l2": "inputs larger than L2 (two %.1f GB distribution buffers)" % (dof * 4 / 1e9),
                        "state_after": {"residual": [float(x) for x in res],
                                        "finite": bool(np.all(np.isfinite(W_end)))}},
@@ -400,6 +406,143 @@ def run_gpu(args):
     return 0
 
 
+def run_mixed_report(args):
+    """Per-field error of FP32 arithmetic with FP32, FP16 and BF16 storage
+    against the FP64 oracle after 100 and 1000 steps, on a reduced instance
+    of the sphere workload (the same generator at 2500 cells, 24^3 velocities
+    on [-12, 12]^3; the oracle cannot step the full one 1000 times).  Relative L-inf per field:
+    density, momentum (as a vector), energy, temperature."""
+    import oracle as O
+    from paper_2606_15720_gb300 import ugks as U
+    mesh = I.sphere_tet_mesh(2500, seed=MESH_SEED)
+    grid = I.midpoint_grid(24, -12.0, 12.0, 3)
+    gas = I.Gas(model="shakhov", K=0, Pr=2.0 / 3.0, omega=0.81, mu_ref=I.mu_ref_from_kn(0.05, 0.81), cfl=0.8)
+    W0 = I.prim_to_conservative(I.uniform_primitives(mesh, 1.0, mesh.bc[1].u, 1.0), 3, 0)
+    f0 = O.initial_f(mesh, grid, W0, gas.K)
+    with U.Solver(mesh, grid, gas, W0, storage="f64") as s:
+        dt = s.dt
+    t0 = time.perf_counter()
+    W100, f100, _, _ = O.run(mesh, grid, gas, W0, f0, 100, dt=dt)
+    W1000, _, _, _ = O.run(mesh, grid, gas, W100, f100, 900, dt=dt)
+    oracle_s = time.perf_counter() - t0
+    ref = {100: W100, 1000: W1000}
+
+    def fields(W):
+        rho = W[:, 0]
+        mom = W[:, 1:4]
+        E = W[:, 4]
+        T = 4.0 * (E - 0.5 * np.sum(mom ** 2, axis=1) / rho) / (3.0 * rho)   # K = 0, R = 1/2
+        return rho, mom, E, T
+
+    out = {}
+    for st in ("f32", "f16", "bf16"):
+        out[st] = {}
+        with U.Solver(mesh, grid, gas, W0, storage=st) as s:
+            done = 0
+            for n in (100, 1000):
+                s.step(n - done)
+                done = n
+                g, o = fields(s.moments()), fields(ref[n])
+                mom_scale = np.max(np.linalg.norm(o[1], axis=1))
+                out[st][str(n)] = {
+                    "rho": float(np.max(np.abs(g[0] - o[0])) / np.max(np.abs(o[0]))),
+                    "momentum": float(np.max(np.linalg.norm(g[1] - o[1], axis=1)) / mom_scale),
+                    "energy": float(np.max(np.abs(g[2] - o[2])) / np.max(np.abs(o[2]))),
+                    "temperature": float(np.max(np.abs(g[3] - o[3])) / np.max(np.abs(o[3])))}
+    print(json.dumps({"report": "mixed_precision_error", "metric": "relative L-inf per field vs the FP64 oracle",
+                      "config": {"workload": "sphere_tet2.5k_v24cube_shakhov_ma5_kn0.05", "n_cells": mesh.n_cells,
+                                 "n_v": grid.n_v, "dt": dt, "oracle_seconds": oracle_s},
+                      "errors": out}), flush=True)
+    return 0
+
+
+def batch_cases(n=64, seed=4, cells_range=(5e3, 4e4), nv_range=(20, 48), mach_range=(2.0, 8.0)):
+    """The 64 cylinder cases of the batch workload: Ma ~ U[2, 8], Kn ~
+    log-uniform [1e-3, 1], triangle meshes of 5k-40k cells (log-uniform),
+    velocity grids sized to Ma (20^2 .. 48^2 points, spacing ~1 thermal unit
+    of the free stream, range covering the stagnation temperature)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        mach = float(rng.uniform(*mach_range))
+        kn = float(10 ** rng.uniform(-3.0, 0.0))
+        cells = int(round(10 ** rng.uniform(math.log10(cells_range[0]), math.log10(cells_range[1]))))
+        mesh = I.cylinder_tri_mesh(cells, seed=seed * 1000 + i, mach=mach)
+        u_inf = mesh.bc[1].u[0]
+        T_stag = 1.0 + mach * mach / 3.0
+        vmax = max(u_inf + 4.0, 3.5 * math.sqrt(T_stag))
+        nvx = int(min(nv_range[1], max(nv_range[0], round(2.0 * vmax))))
+        grid = I.midpoint_grid(nvx, -vmax, vmax, 2)
+        gas = I.Gas(model="shakhov", K=0, Pr=2.0 / 3.0, omega=0.81, mu_ref=I.mu_ref_from_kn(kn, 0.81), cfl=0.8)
+        W0 = I.prim_to_conservative(I.uniform_primitives(mesh, 1.0, mesh.bc[1].u, 1.0), 2, 0)
+        out.append((mesh, grid, gas, W0, mach, kn))
+    return out
+
+
+def run_batch_report(args):
+    """Batch workload: 64 uneven 2-D cylinder cases advanced by one CUDA-graph
+    launch per two steps after the block-size autotuner, against the same
+    cases stepped one after another with ordinary launches; also 64 small
+    cases (Ma 1.5-3, 300-1500 cells, 20^2-24^2 velocities), where launch
+    overhead and idle SMs matter."""
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CUDA library has no CPU path)")
+    big = time_batch(args, batch_cases(), "cylinder_batch64_ma2-8_kn1e-3-1_tri5k-40k_v20-48sq_shakhov_fp32")
+    small = time_batch(args, batch_cases(seed=5, cells_range=(300, 1500), nv_range=(20, 24), mach_range=(1.5, 3.0)),
+                       "cylinder_batch64_small_ma1.5-3_tri300-1500_v20-24sq_shakhov_fp32")
+    print(json.dumps(dict(big, small_cases=small)), flush=True)
+    return 0
+
+
+def time_batch(args, cases, workload):
+    import torch
+    from paper_2606_15720_gb300 import ugks as U
+    dof = sum(c[0].n_cells * c[1].n_v * 2 for c in cases)   # Shakhov 2-D, K = 0: h and b
+    stream = torch.cuda.Stream()
+    steps = max(2, args.steps - args.steps % 2)
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        b = U.Batch([c[0] for c in cases], [c[1] for c in cases], [c[2] for c in cases], [c[3] for c in cases],
+                    storage="f32", stream=int(stream.cuda_stream))
+        create_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        b.autotune()
+        torch.cuda.synchronize()
+        tune_s = time.perf_counter() - t0
+        picks = [b.tuning(i)[0] for i in range(len(cases))]
+        b.step(max(2, args.warmup - args.warmup % 2))   # captures the graph
+        torch.cuda.synchronize()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        b.step(steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = start.elapsed_time(stop) / steps
+        # the same cases, one ordinary ugks_step after another
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            for s in b.cases:
+                s.step(1)
+        for s in b.cases:
+            s.residual()          # synchronises each case's stream
+        seq_ms = 1e3 * (time.perf_counter() - t0) / steps
+        finite = all(bool(np.all(np.isfinite(s.moments()))) for s in b.cases)
+        b.close()
+    return {
+        "report": "batch", "metric": "phase-space DOF updates/s per batch step", "unit": "DOF/s",
+        "config": {"workload": workload,
+                   "n_cases": len(cases), "dof_per_step": dof,
+                   "cells": [int(c[0].n_cells) for c in cases], "n_v": [int(c[1].n_v) for c in cases]},
+        "graph": {"value": dof / (graph_ms * 1e-3), "ms_per_step": graph_ms,
+                  "note": "one CUDA-graph launch per two steps of all cases, cases on forked streams"},
+        "sequential": {"value": dof / (seq_ms * 1e-3), "ms_per_step": seq_ms,
+                       "note": "ugks_step per case in turn, host wall clock"},
+        "autotune": {"seconds": tune_s, "block_velocities": {str(v): picks.count(v) for v in sorted(set(picks))}},
+        "setup_seconds": {"create": create_s}, "finite": finite, "steps": steps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -412,11 +555,20 @@ def main():
     ap.add_argument("--nv-axis", type=int, default=NV_AXIS, help="velocities per axis (profiling runs only)")
     ap.add_argument("--sweep", default="auto", choices=["auto", "blocked", "tiled"])
     ap.add_argument("--block-velocities", type=int, default=0, choices=[0, 32, 64, 128])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="storage of f (FP16 / BF16: deviations from a per-cell reference Maxwellian)")
+    ap.add_argument("--report", default=None, choices=["mixed", "batch"],
+                    help="mixed: per-field error of FP32/FP16/BF16 storage vs the oracle at 1e2 and 1e3 steps; "
+                         "batch: 64 uneven cylinder cases in one CUDA graph with the block-size autotuner")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.report == "mixed":
+        return run_mixed_report(args)
+    if args.report == "batch":
+        return run_batch_report(args)
     return run_gpu(args)
 
 

@@ -110,7 +110,12 @@ typedef struct {
  *   dt: dt_override if > 0, else cfl * min_i |Omega_i| / max_k sum_f S_f max(u_k . n_f, 0)
  *   limiter: slope limiter of the least-squares reconstruction, venkat_K its constant
  *   shock_tau_fix: add dt |p_l - p_r| / (p_l + p_r) to the interface relaxation time
- *   storage: precision of the stored distribution (F64, F32 supported)
+ *   storage: precision of the stored distribution: F64 (FP64 arithmetic),
+ *     F32 (FP32 arithmetic), or F16 / BF16: FP32 arithmetic with f stored as
+ *     deviations from a per-cell reference Maxwellian (the Maxwellian of the
+ *     cell's W when the row was written), scaled per row of 32 velocities by
+ *     the row's largest deviation, in FP16 / BF16; blocked sweep only, at most
+ *     8 faces per cell.  Moments, W and the interface coefficients stay FP64.
  *   tile_cells: cells per tile of the tiled sweep, 0 = automatic
  *   sweep: device organisation of the velocity-block sweep (Sec. 2.2.2,
  *     Table B.1), UGKS_SWEEP_*: BLOCKED runs gradients, fluxes and the first
@@ -219,6 +224,44 @@ ugks_status ugks_solve(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ugk
                        const double *W_init, int32_t n_steps, double *W_out, double *res_out);
 
 ugks_status ugks_destroy(ugks_ctx *ctx);
+
+/* ---- Batches of cases (uneven meshes and velocity grids) ----
+ * The paper steps one case over many ranks; a batch steps many independent
+ * cases on one GPU.  Each case is an ordinary context (its own mesh, grid,
+ * parameters, time step and coefficients; blocked sweep only).
+ * ugks_batch_step advances every case by n_steps: two steps of every case are
+ * captured once into one CUDA graph, each case on its own forked stream so
+ * that small cases run concurrently, and each graph launch advances all cases
+ * by two steps (an odd remainder runs as ordinary steps).  Work is queued on
+ * cuda_stream (NULL: a library-owned stream); the cases' own calls
+ * (ugks_moments, ...) are ordered after it. */
+typedef struct ugks_batch ugks_batch;
+
+/* Creates n contexts from meshes[i], vgrids[i], params[i] and W_init[i]
+ * (W_init or W_init[i] may be NULL as in ugks_create).  A case whose
+ * (cells, velocities, dim, reduced distributions, storage) was tuned earlier
+ * in this process reuses that block size. */
+ugks_status ugks_batch_create(int32_t n, const ugks_mesh *const *meshes, const ugks_vgrid *const *vgrids,
+                              const ugks_params *params, const double *const *W_init, void *cuda_stream,
+                              ugks_batch **out);
+
+/* Block-size autotuner: every case not tuned yet runs two steps at each
+ * block size of 32, 64 and 128 velocities that its buffers allow, timed on
+ * the device (the second step of each pair), and keeps the fastest.  These
+ * steps advance the cases (different block sizes change only the summation
+ * order of the moments).  The choice is cached for the process. */
+ugks_status ugks_batch_autotune(ugks_batch *batch);
+
+ugks_status ugks_batch_step(ugks_batch *batch, int32_t n_steps);
+
+/* The context of case i (owned by the batch; do not destroy it). */
+ugks_status ugks_batch_context(ugks_batch *batch, int32_t i, ugks_ctx **ctx);
+
+/* Block size in use for case i (velocities per block) and the autotuner's
+ * timings (ms per step at 32, 64, 128 velocities per block; 0 = not run). */
+ugks_status ugks_batch_tuning(ugks_batch *batch, int32_t i, int32_t *block_velocities, double *ms_per_step);
+
+ugks_status ugks_batch_destroy(ugks_batch *batch);
 
 /* Message of the last error of ctx, or of the calling thread when ctx is NULL. */
 const char *ugks_last_error(const ugks_ctx *ctx);

@@ -38,6 +38,7 @@
 #include "ugks_device.cuh"
 #include "ugks_internal.cuh"
 #include "ugks_kernels.cuh"
+#include "ugks_store.cuh"
 
 namespace ugks {
 
@@ -611,33 +612,80 @@ __device__ __forceinline__ void stage_bytes(unsigned char* dst, const void* src,
   for (int q = lane; q < bytes / 16; q += 32) cp_async16(dst + q * 16, s + q * 16);
 }
 
-// The NR x VB rows (one per reduced distribution and sub-block) of cell c.
-template <int NR, int VB, typename T>
-__device__ __forceinline__ void stage_cell_rows(unsigned char* dst, const BlockedArgs<T>& a, int64_t m0, int c,
-                                                int lane) {
-  constexpr int CH = BV * int(sizeof(T)) / 16;  // 16-byte chunks per row
-  const size_t sj = size_t(a.Nc) * BV, sr = size_t(a.M) * sj;
-  for (int q = lane; q < NR * VB * CH; q += 32) {
-    const int row = q / CH, part = q % CH, r = row / VB, j = row % VB;
-    const T* src = a.f_cur + r * sr + (size_t(m0) + j) * sj + size_t(c) * BV;
-    cp_async16(dst + q * 16, reinterpret_cast<const unsigned char*>(src) + part * 16);
-  }
-}
-
 template <int NR, int VB, typename T>
 struct CellStage {
-  static constexpr int ROW = NR * VB * BV * int(sizeof(T));  // rows of one cell or one face
+  static constexpr int ROW = NR * VB * BV * int(sizeof(T));  // rows of one face (flux buffer X)
   static constexpr int INC = int(sizeof(IncT<T>));
 };
 
-// Shared-memory bytes per warp of the pipelined kernels (3 record slots, 2 row slots).
-template <int NR, int VB, typename T>
-__host__ __device__ constexpr int recon_warp_bytes(int W) {
-  return 3 * (W * CellStage<NR, VB, T>::INC + 16) + 2 * ((W + 1) * CellStage<NR, VB, T>::ROW + W * 16);
+// One cell's stored rows in shared memory: the NR x VB rows in the storage
+// type S, then (scaled storage) their FP32 scales and the cell's reference
+// Maxwellian.
+template <int NR, int VB, typename S>
+struct CellSlot {
+  static constexpr bool SCALED = StoreTraits<S>::scaled;
+  static constexpr int ROWS = NR * VB * BV * int(sizeof(S));
+  static constexpr int SCL = SCALED ? ((NR * VB * 4 + 15) / 16) * 16 : 0;
+  static constexpr int REF = SCALED ? int(sizeof(RefMaxwell)) : 0;
+  static constexpr int BYTES = ROWS + SCL + REF;
+};
+
+// Stages cell c's slot of f^n for block m0.
+template <int NR, int VB, typename T, typename S>
+__device__ __forceinline__ void stage_cell(unsigned char* dst, const BlockedArgs<T>& a, int64_t m0, int c, int lane) {
+  using CS = CellSlot<NR, VB, S>;
+  constexpr int CH = BV * int(sizeof(S)) / 16;  // 16-byte chunks per row
+  const size_t sj = size_t(a.Nc) * BV, sr = size_t(a.M) * sj;
+  const S* f = reinterpret_cast<const S*>(a.f_cur);
+  for (int q = lane; q < NR * VB * CH; q += 32) {
+    const int row = q / CH, part = q % CH, r = row / VB, j = row % VB;
+    const S* src = f + r * sr + (size_t(m0) + j) * sj + size_t(c) * BV;
+    cp_async16(dst + q * 16, reinterpret_cast<const unsigned char*>(src) + part * 16);
+  }
+  if constexpr (CS::SCALED) {
+    for (int q = lane; q < NR * VB; q += 32) {
+      const int r = q / VB, j = q % VB;
+      cp_async_small<4>(dst + CS::ROWS + q * 4, a.sc_cur + (size_t(r) * a.M + m0 + j) * a.Nc + c);
+    }
+    if (lane < 2)
+      cp_async16(dst + CS::ROWS + CS::SCL + lane * 16, reinterpret_cast<const unsigned char*>(a.ref_cur + c) + lane * 16);
+  }
 }
-template <int NR, int VB, typename T>
+
+// Values of a staged cell slot: f of reduced distribution r at sub-block j for
+// this lane (decoded for scaled storage; g0[j] = the slot's reference
+// Maxwellian at the lane's velocity, computed by slot_refs).
+template <int D, int NR, int VB, typename T, typename S>
+__device__ __forceinline__ void slot_refs(const unsigned char* slot, const BlockVel<D, NR, VB, T>& v, T (&g0)[VB]) {
+  using CS = CellSlot<NR, VB, S>;
+  if constexpr (CS::SCALED) {
+    const RefMaxwell& R = *reinterpret_cast<const RefMaxwell*>(slot + CS::ROWS + CS::SCL);
+#pragma unroll
+    for (int j = 0; j < VB; ++j) g0[j] = ref_value<D>(R, 0, v.u[j], v.real[j]);
+  }
+}
+template <int NR, int VB, typename T, typename S>
+__device__ __forceinline__ T slot_value(const unsigned char* slot, int r, int j, int lane, const T (&g0)[VB]) {
+  using CS = CellSlot<NR, VB, S>;
+  const S d = reinterpret_cast<const S*>(slot)[(r * VB + j) * BV + lane];
+  if constexpr (CS::SCALED) {
+    const RefMaxwell& R = *reinterpret_cast<const RefMaxwell*>(slot + CS::ROWS + CS::SCL);
+    const float sc = reinterpret_cast<const float*>(slot + CS::ROWS)[r * VB + j];
+    return decode_value(d, sc, r == 0 ? g0[j] : R.kap * g0[j]);
+  } else {
+    return T(d);
+  }
+}
+
+// Shared-memory bytes per warp of the pipelined kernels (3 record slots, 2 row slots).
+template <int NR, int VB, typename T, typename S>
+__host__ __device__ constexpr int recon_warp_bytes(int W) {
+  return 3 * (W * CellStage<NR, VB, T>::INC + 16) + 2 * ((W + 1) * CellSlot<NR, VB, S>::BYTES + W * 16);
+}
+template <int NR, int VB, typename T, typename S>
 __host__ __device__ constexpr int stage1_warp_bytes(int W) {
-  return 3 * (W * CellStage<NR, VB, T>::INC + int(sizeof(CellEq<T>))) + 2 * ((W + 1) * CellStage<NR, VB, T>::ROW);
+  return 3 * (W * CellStage<NR, VB, T>::INC + int(sizeof(CellEq<T>))) +
+         2 * (W * CellStage<NR, VB, T>::ROW + CellSlot<NR, VB, S>::BYTES);
 }
 
 // byte offset of the 16-byte chunk of a FacePoly that holds G0 and G1
@@ -647,17 +695,18 @@ __host__ __device__ constexpr int g01_chunk() {
   return (int(offsetof(FP, G0)) / 16) * 16;
 }
 
-template <int D, int NR, int VB, typename T>
+template <int D, int NR, int VB, typename T, typename S>
 __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<T> a, const int64_t m0) {
   using CS = CellStage<NR, VB, T>;
+  using SL = CellSlot<NR, VB, S>;
   using FP = FacePoly<D, NR, T>;
   static_assert(offsetof(FP, G1) + sizeof(T) <= size_t(g01_chunk<D, NR, T>() + 16),
                 "G0 and G1 share one 16-byte chunk");
   extern __shared__ __align__(16) unsigned char cell_smem[];
   const int W = a.W;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int AB = W * CS::INC + 16, BB = (W + 1) * CS::ROW + W * 16;
-  unsigned char* const As = cell_smem + warp * recon_warp_bytes<NR, VB, T>(W);
+  const int AB = W * CS::INC + 16, BB = (W + 1) * SL::BYTES + W * 16;
+  unsigned char* const As = cell_smem + warp * recon_warp_bytes<NR, VB, T, S>(W);
   unsigned char* const Bs = As + 3 * AB;
   BlockVel<D, NR, VB, T> v;
   v.load(a, m0, lane);
@@ -677,13 +726,13 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<
       const int fl = inc[i].flags;
       if (fl & 3) continue;  // wall or padding: no neighbour row, no G0/G1
       const int o = inc[i].other;
-      if (o >= 0) stage_cell_rows<NR, VB, T>(dst + i * CS::ROW, a, m0, o, lane);
+      if (o >= 0) stage_cell<NR, VB, T, S>(dst + i * SL::BYTES, a, m0, o, lane);
       if (lane == 0)
-        cp_async16(dst + (W + 1) * CS::ROW + i * 16,
+        cp_async16(dst + (W + 1) * SL::BYTES + i * 16,
                    static_cast<const unsigned char*>(a.fpoly) + size_t(inc[i].face) * sizeof(FacePoly<D, NR, T>) +
                        g01_chunk<D, NR, T>());
     }
-    stage_cell_rows<NR, VB, T>(dst + W * CS::ROW, a, m0, c, lane);
+    stage_cell<NR, VB, T, S>(dst + W * SL::BYTES, a, m0, c, lane);
   };
 
   if (cbeg < a.Nc) issueA(cbeg, As);
@@ -705,14 +754,15 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<
     const unsigned char* A = As + (it % 3) * AB;
     const unsigned char* B = Bs + (it & 1) * BB;
     const IncT<T>* inc = reinterpret_cast<const IncT<T>*>(A);
-    const T* rows = reinterpret_cast<const T*>(B) + lane;  // [W+1][NR][VB][BV]
-    const T* own = rows + W * (NR * VB * BV);
+    const unsigned char* own = B + W * SL::BYTES;  // slots [W+1]: the neighbours, then this cell
+    T g0[VB];
+    slot_refs<D, NR, VB, T, S>(own, v, g0);
     T fc[NR][VB], g[NR][VB][D], fmx[NR][VB], fmn[NR][VB];
 #pragma unroll
     for (int r = 0; r < NR; ++r)
 #pragma unroll
       for (int j = 0; j < VB; ++j) {
-        fc[r][j] = own[(r * VB + j) * BV];
+        fc[r][j] = slot_value<NR, VB, T, S>(own, r, j, lane, g0);
         fmx[r][j] = fmn[r][j] = fc[r][j];
 #pragma unroll
         for (int d = 0; d < D; ++d) g[r][j][d] = T(0);
@@ -725,10 +775,13 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<
       for (int d = 0; d < D; ++d) wd[d] = inc[i].w[d];
       T fo[NR][VB];
       if (inc[i].other >= 0) {
+        const unsigned char* nb = B + i * SL::BYTES;
+        T gn[VB];
+        slot_refs<D, NR, VB, T, S>(nb, v, gn);
 #pragma unroll
         for (int r = 0; r < NR; ++r)
 #pragma unroll
-          for (int j = 0; j < VB; ++j) fo[r][j] = rows[(i * NR * VB + r * VB + j) * BV];
+          for (int j = 0; j < VB; ++j) fo[r][j] = slot_value<NR, VB, T, S>(nb, r, j, lane, gn);
       } else {
         T rho, lam, U[3];
         ghost_state<D, NR, T>(a, inc[i].bc, c, rho, lam, U);
@@ -811,7 +864,7 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<
         }
       }
     // free-transport part on every face for which this cell is upwind
-    const T* G01 = reinterpret_cast<const T*>(B + (W + 1) * CS::ROW);
+    const T* G01 = reinterpret_cast<const T*>(B + (W + 1) * SL::BYTES);
     constexpr int g0i = (int(offsetof(FP, G0)) - g01_chunk<D, NR, T>()) / int(sizeof(T));
     for (int i = 0; i < W; ++i) {
       const int fl = inc[i].flags;
@@ -852,14 +905,15 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<
   cp_async_wait<0>();
 }
 
-template <int D, int NR, int VB, typename T>
+template <int D, int NR, int VB, typename T, typename S>
 __global__ void __launch_bounds__(kBlockedThreads) k_bstage1_p(const BlockedArgs<T> a, const int64_t m0) {
   using CS = CellStage<NR, VB, T>;
+  using SL = CellSlot<NR, VB, S>;
   extern __shared__ __align__(16) unsigned char cell_smem[];
   const int W = a.W;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int AB = W * CS::INC + int(sizeof(CellEq<T>)), BB = (W + 1) * CS::ROW;
-  unsigned char* const As = cell_smem + warp * stage1_warp_bytes<NR, VB, T>(W);
+  const int AB = W * CS::INC + int(sizeof(CellEq<T>)), BB = W * CS::ROW + SL::BYTES;
+  unsigned char* const As = cell_smem + warp * stage1_warp_bytes<NR, VB, T, S>(W);
   unsigned char* const Bs = As + 3 * AB;
   BlockVel<D, NR, VB, T> v;
   v.load(a, m0, lane);
@@ -877,7 +931,7 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage1_p(const BlockedArgs
       if (inc[i].flags & 2) continue;
       stage_bytes(dst + i * CS::ROW, a.X + size_t(inc[i].face) * (NR * VB * BV), CS::ROW, lane);
     }
-    stage_cell_rows<NR, VB, T>(dst + W * CS::ROW, a, m0, c, lane);
+    stage_cell<NR, VB, T, S>(dst + W * CS::ROW, a, m0, c, lane);
   };
 
   if (cbeg < a.Nc) issueA(cbeg, As);
@@ -914,7 +968,9 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage1_p(const BlockedArgs
 #pragma unroll
         for (int j = 0; j < VB; ++j) flux[r][j] += sa * rows[(i * NR * VB + r * VB + j) * BV];
     }
-    const T* own = rows + W * (NR * VB * BV);
+    const unsigned char* own = B + W * CS::ROW;
+    T g0[VB];
+    slot_refs<D, NR, VB, T, S>(own, v, g0);
     const T lam = E.lam, beta0 = E.beta, pref = E.pref, s0 = E.s0, kap = E.kap, inv_vol = E.inv_vol;
     const size_t base = size_t(m0) * sj + size_t(c) * BV + lane;
 #pragma unroll
@@ -933,9 +989,18 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage1_p(const BlockedArgs
       if (NR == 2) fp[NR - 1] = kap * H * (T(1) + s * (T(2) * lam * c2 - T(D)));
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
-        const T f = own[(r * VB + j) * BV];
-        const T ft = f - flux[r][j] * inv_vol + beta0 * (fp[r] - f);
-        a.f_next[base + r * sr + j * sj] = v.real[j] ? ft : T(0);
+        const T f = slot_value<NR, VB, T, S>(own, r, j, lane, g0);
+        const T ft = v.real[j] ? f - flux[r][j] * inv_vol + beta0 * (fp[r] - f) : T(0);
+        if constexpr (SL::SCALED) {
+          // f~ is stored against the same reference as f^n
+          const RefMaxwell& R = *reinterpret_cast<const RefMaxwell*>(own + SL::ROWS + SL::SCL);
+          float scale;
+          const S d = encode_value<S>(ft, r == 0 ? g0[j] : R.kap * g0[j], scale);
+          reinterpret_cast<S*>(a.f_next)[base + r * sr + j * sj] = d;
+          if (lane == 0) a.sc_next[(size_t(r) * a.M + m0 + j) * a.Nc + c] = scale;
+        } else {
+          a.f_next[base + r * sr + j * sj] = ft;
+        }
       }
     }
     __syncwarp();
@@ -1029,11 +1094,13 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bW(const BlockedArgs<T> a) 
 // and each warp keeps its cell's 8 rows in flight.  Per-lane FP32 partial
 // sums of q are flushed to FP64 every 32 blocks and reduced over the warp once.
 // ---------------------------------------------------------------------------
+// Second stage of one block of one cell: ft holds f~ on entry and f^{n+1}
+// on exit; H receives the cell's Maxwellian of W^{n+1} at the lane's velocity.
 template <int D, int NR, bool WALL, typename T>
 __device__ __forceinline__ void stage2_block(const BlockedArgs<T>& a, int c, int e0, int e1, int64_t m,
-                                             int lane, const Vel4<T>& vq, T (&ft)[NR], const T (&Uc)[3], const T (&qc)[3], T pref, T lam,
-                                             T s0, T kap, T beta1, T inv1, T iv, T* fc, size_t sr, size_t sj,
-                                             T (&qp)[3]) {
+                                             int lane, const Vel4<T>& vq, T (&ft)[NR], const T (&Uc)[3],
+                                             const T (&qc)[3], T pref, T lam, T s0, T kap, T beta1, T inv1, T iv,
+                                             T (&qp)[3], T& H_out) {
   const T dt = T(a.g.dt);
   const int64_t k = m * BV + lane;
   T u[3];
@@ -1075,18 +1142,17 @@ __device__ __forceinline__ void stage2_block(const BlockedArgs<T>& a, int c, int
   f1[0] = (ft[0] + beta1 * H * (T(1) + s * (T(2) * lam * c2 - T(2 + D)))) * inv1;
   if (NR == 2) f1[NR - 1] = (ft[NR - 1] + beta1 * kap * H * (T(1) + s * (T(2) * lam * c2 - T(D)))) * inv1;
 #pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    if (!real_v) f1[r] = T(0);
-    fc[r * sr + m * sj] = f1[r];
-  }
+  for (int r = 0; r < NR; ++r) ft[r] = real_v ? f1[r] : T(0);
+  H_out = real_v ? H : T(0);
   const T wq = T(0.5) * vq.w;  // zero on padding
-  const T e_ = wq * (c2 * f1[0] + (NR == 2 ? f1[NR - 1] : T(0)));
+  const T e_ = wq * (c2 * ft[0] + (NR == 2 ? ft[NR - 1] : T(0)));
 #pragma unroll
   for (int d = 0; d < D; ++d) qp[d] += cc[d] * e_;
 }
 
-template <int D, int NR, typename T>
+template <int D, int NR, typename T, typename S>
 __global__ void __launch_bounds__(kBlockedThreads, sizeof(T) == 4 ? (NR == 1 ? 4 : 2) : 1) k_bstage2(const BlockedArgs<T> a) {
+  constexpr bool SCALED = StoreTraits<S>::scaled;
   constexpr int UNR = kBlockedThreads / BV;  // blocks per round: one velocity record per thread of the CTA
   __shared__ Vel4<T> sv[2][UNR * BV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1098,8 +1164,24 @@ __global__ void __launch_bounds__(kBlockedThreads, sizeof(T) == 4 ? (NR == 1 ? 4
   const int64_t mb = int64_t(chunk) * per;
   const int64_t me = mb + per < a.M ? mb + per : a.M;
   const size_t sj = size_t(a.Nc) * BV, sr = size_t(a.M) * sj;
-  T* fc = a.f_next + size_t(cc) * BV + lane;
+  S* fc = reinterpret_cast<S*>(a.f_next) + size_t(cc) * BV + lane;
   const CellEq<T> E = a.ceq1[cc];
+  RefMaxwell Rc{};  // reference of f~ (scaled storage)
+  if constexpr (SCALED) {
+    Rc = a.ref_cur[cc];
+    if (valid && chunk == 0 && lane == 0) {
+      // f^{n+1} is stored against the Maxwellian of W^{n+1}
+      RefMaxwell Rn;
+      Rn.pref = E.pref;
+      Rn.lam = E.lam;
+      Rn.U[0] = E.U[0];
+      Rn.U[1] = E.U[1];
+      Rn.U[2] = E.U[2];
+      Rn.kap = E.kap;
+      Rn.pad[0] = Rn.pad[1] = 0.f;
+      a.ref_next[c] = Rn;
+    }
+  }
   const T lam = E.lam, beta1 = E.beta, pref = E.pref, s0 = E.s0, kap = E.kap, iv = E.inv_vol;
   const T inv1 = T(1) / (T(1) + beta1);
   T Uc[3], qc[3];
@@ -1116,38 +1198,66 @@ __global__ void __launch_bounds__(kBlockedThreads, sizeof(T) == 4 ? (NR == 1 ? 4
 
   // round k covers blocks [m, m + UNR); its rows and velocity records are
   // requested during round k - 1
-  auto load_rows = [&](int64_t m, T (&ft)[UNR][NR]) {
+  auto load_rows = [&](int64_t m, S (&ft)[UNR][NR], float (&sc)[UNR][NR]) {
 #pragma unroll
     for (int i = 0; i < UNR; ++i)
       if (m + i < me)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) ft[i][r] = fc[r * sr + (m + i) * sj];
+        for (int r = 0; r < NR; ++r) {
+          ft[i][r] = fc[r * sr + (m + i) * sj];
+          if constexpr (SCALED) sc[i][r] = a.sc_next[(size_t(r) * a.M + m + i) * a.Nc + cc];
+        }
   };
-  T ft[UNR][NR], fn[UNR][NR];
+  S ft[UNR][NR], fn[UNR][NR];
+  float sc[UNR][NR], sn[UNR][NR];
   if (mb * BV + threadIdx.x < me * BV) sv[0][threadIdx.x] = a.vel[mb * BV + threadIdx.x];
-  if (valid) load_rows(mb, ft);
+  if (valid) load_rows(mb, ft, sc);
   int k = 0;
   for (int64_t m = mb; m < me; m += UNR, ++k) {
     __syncthreads();  // round k's records are visible; round k - 1's slot is free
     const int64_t mn = m + UNR;
     if (mn * BV + threadIdx.x < me * BV) sv[(k + 1) & 1][threadIdx.x] = a.vel[mn * BV + threadIdx.x];
     if (!valid) continue;
-    if (mn < me) load_rows(mn, fn);
+    if (mn < me) load_rows(mn, fn, sn);
 #pragma unroll
     for (int i = 0; i < UNR; ++i) {
       if (m + i >= me) break;
       const Vel4<T> vq = sv[k & 1][i * BV + lane];
+      const bool real_v = (m + i) * BV + lane < a.nv;
+      T f[NR], H;
+      if constexpr (SCALED) {
+        const float u[3] = {vq.x, vq.y, vq.z};
+        const float g = ref_value<D>(Rc, 0, u, real_v);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) f[r] = decode_value(ft[i][r], sc[i][r], r == 0 ? g : Rc.kap * g);
+      } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) f[r] = ft[i][r];
+      }
       if (has_wall)
-        stage2_block<D, NR, true, T>(a, cc, e0, e1, m + i, lane, vq, ft[i], Uc, qc, pref, lam, s0, kap, beta1, inv1,
-                                     iv, fc, sr, sj, qp);
+        stage2_block<D, NR, true, T>(a, cc, e0, e1, m + i, lane, vq, f, Uc, qc, pref, lam, s0, kap, beta1, inv1, iv,
+                                     qp, H);
       else
-        stage2_block<D, NR, false, T>(a, cc, e0, e1, m + i, lane, vq, ft[i], Uc, qc, pref, lam, s0, kap, beta1, inv1,
-                                      iv, fc, sr, sj, qp);
+        stage2_block<D, NR, false, T>(a, cc, e0, e1, m + i, lane, vq, f, Uc, qc, pref, lam, s0, kap, beta1, inv1, iv,
+                                      qp, H);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if constexpr (SCALED) {
+          float scale;
+          fc[r * sr + (m + i) * sj] = encode_value<S>(f[r], r == 0 ? H : kap * H, scale);
+          if (lane == 0) a.sc_next[(size_t(r) * a.M + m + i) * a.Nc + cc] = scale;
+        } else {
+          fc[r * sr + (m + i) * sj] = f[r];
+        }
+      }
     }
 #pragma unroll
     for (int i = 0; i < UNR; ++i)
 #pragma unroll
-      for (int r = 0; r < NR; ++r) ft[i][r] = fn[i][r];
+      for (int r = 0; r < NR; ++r) {
+        ft[i][r] = fn[i][r];
+        sc[i][r] = sn[i][r];
+      }
     if ((k & 3) == 3) {  // flush the FP32 partial sums every 32 blocks
 #pragma unroll
       for (int d = 0; d < D; ++d) {
@@ -1219,42 +1329,50 @@ cudaError_t launch_cell_pipelined(K kernel, int nsm, int bytes, int& warps_out, 
 // Per-warp shared memory above which the pipelined kernels are not used.
 constexpr int kPipelineWarpBytes = 24 * 1024;
 
-template <int D, int NR, int VB, typename T>
+template <int D, int NR, int VB, typename T, typename S>
 cudaError_t launch_brecon_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0) {
-  const int bytes = recon_warp_bytes<NR, VB, T>(a.W);
+  const int bytes = recon_warp_bytes<NR, VB, T, S>(a.W);
   if (a.W < 1 || a.W > kEllMax || bytes > kPipelineWarpBytes) {
-    k_brecon<D, NR, VB, T><<<blocked_warp_grid(a.Nc), kBlockedThreads, 0, s>>>(a, m0);
-    return cudaGetLastError();
+    if constexpr (StoreTraits<S>::scaled) {
+      return cudaErrorNotSupported;  // scaled storage runs only in the pipelined kernels
+    } else {
+      k_brecon<D, NR, VB, T><<<blocked_warp_grid(a.Nc), kBlockedThreads, 0, s>>>(a, m0);
+      return cudaGetLastError();
+    }
   }
   static int cached_bytes = -1, cached_warps = 0;
   static unsigned cached_grid = 0;
   if (cached_bytes != bytes) {
-    cudaError_t e = launch_cell_pipelined(k_brecon_p<D, NR, VB, T>, a.nsm, bytes, cached_warps, cached_grid);
+    cudaError_t e = launch_cell_pipelined(k_brecon_p<D, NR, VB, T, S>, a.nsm, bytes, cached_warps, cached_grid);
     if (e != cudaSuccess) return e;
     cached_bytes = bytes;
   }
   const unsigned grid = std::min<unsigned>(cached_grid, unsigned((a.Nc + cached_warps - 1) / cached_warps));
-  k_brecon_p<D, NR, VB, T><<<grid, cached_warps * 32, cached_warps * bytes, s>>>(a, m0);
+  k_brecon_p<D, NR, VB, T, S><<<grid, cached_warps * 32, cached_warps * bytes, s>>>(a, m0);
   return cudaGetLastError();
 }
 
-template <int D, int NR, int VB, typename T>
+template <int D, int NR, int VB, typename T, typename S>
 cudaError_t launch_bstage1_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0) {
-  const int bytes = stage1_warp_bytes<NR, VB, T>(a.W);
+  const int bytes = stage1_warp_bytes<NR, VB, T, S>(a.W);
   if (a.W < 1 || a.W > kEllMax || bytes > kPipelineWarpBytes) {
-    k_bstage1<D, NR, VB, T><<<blocked_warp_grid(a.Nc), kBlockedThreads, 0, s>>>(a, m0);
-    return cudaGetLastError();
+    if constexpr (StoreTraits<S>::scaled) {
+      return cudaErrorNotSupported;
+    } else {
+      k_bstage1<D, NR, VB, T><<<blocked_warp_grid(a.Nc), kBlockedThreads, 0, s>>>(a, m0);
+      return cudaGetLastError();
+    }
   }
   static int cached_bytes = -1, cached_warps = 0;
   static unsigned cached_grid = 0;
   if (cached_bytes != bytes) {
     cudaError_t e =
-        launch_cell_pipelined(k_bstage1_p<D, NR, VB, T>, a.nsm, bytes, cached_warps, cached_grid);
+        launch_cell_pipelined(k_bstage1_p<D, NR, VB, T, S>, a.nsm, bytes, cached_warps, cached_grid);
     if (e != cudaSuccess) return e;
     cached_bytes = bytes;
   }
   const unsigned grid = std::min<unsigned>(cached_grid, unsigned((a.Nc + cached_warps - 1) / cached_warps));
-  k_bstage1_p<D, NR, VB, T><<<grid, cached_warps * 32, cached_warps * bytes, s>>>(a, m0);
+  k_bstage1_p<D, NR, VB, T, S><<<grid, cached_warps * 32, cached_warps * bytes, s>>>(a, m0);
   return cudaGetLastError();
 }
 
@@ -1262,11 +1380,11 @@ cudaError_t launch_bstage1_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t 
   FN(1, 2, 1) FN(1, 2, 2) FN(1, 2, 4) FN(2, 2, 1) FN(2, 2, 2) FN(2, 2, 4) FN(3, 1, 1) FN(3, 1, 2) FN(3, 1, 4) \
   FN(3, 2, 1) FN(3, 2, 2) FN(3, 2, 4)
 
-template <typename T>
+template <typename T, typename S>
 cudaError_t launch_brecon(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb) {
   const int D = a.g.D, NR = a.g.NR;
 #define UGKS_RECON_CASE(d, nr, b) \
-  if (D == d && NR == nr && vb == b) return launch_brecon_tpl<d, nr, b, T>(s, a, m0);
+  if (D == d && NR == nr && vb == b) return launch_brecon_tpl<d, nr, b, T, S>(s, a, m0);
   UGKS_CELL_CASES(UGKS_RECON_CASE)
 #undef UGKS_RECON_CASE
   return cudaErrorInvalidValue;
@@ -1303,11 +1421,11 @@ cudaError_t launch_bflux(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, in
   return cudaErrorInvalidValue;
 }
 
-template <typename T>
+template <typename T, typename S>
 cudaError_t launch_bstage1(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb) {
   const int D = a.g.D, NR = a.g.NR;
 #define UGKS_STAGE1_CASE(d, nr, b) \
-  if (D == d && NR == nr && vb == b) return launch_bstage1_tpl<d, nr, b, T>(s, a, m0);
+  if (D == d && NR == nr && vb == b) return launch_bstage1_tpl<d, nr, b, T, S>(s, a, m0);
   UGKS_CELL_CASES(UGKS_STAGE1_CASE)
 #undef UGKS_STAGE1_CASE
   return cudaErrorInvalidValue;
@@ -1336,25 +1454,32 @@ cudaError_t launch_bconserve(cudaStream_t s, const BlockedArgs<T>& a) {
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, typename S>
 cudaError_t launch_bstage2(cudaStream_t s, const BlockedArgs<T>& a) {
   const dim3 grid(blocked_warp_grid(a.Nc), unsigned(a.nchunk));
   const int D = a.g.D, NR = a.g.NR;
-  if (D == 1 && NR == 2) k_bstage2<1, 2, T><<<grid, kBlockedThreads, 0, s>>>(a);
-  else if (D == 2 && NR == 2) k_bstage2<2, 2, T><<<grid, kBlockedThreads, 0, s>>>(a);
-  else if (D == 3 && NR == 1) k_bstage2<3, 1, T><<<grid, kBlockedThreads, 0, s>>>(a);
-  else if (D == 3 && NR == 2) k_bstage2<3, 2, T><<<grid, kBlockedThreads, 0, s>>>(a);
+  if (D == 1 && NR == 2) k_bstage2<1, 2, T, S><<<grid, kBlockedThreads, 0, s>>>(a);
+  else if (D == 2 && NR == 2) k_bstage2<2, 2, T, S><<<grid, kBlockedThreads, 0, s>>>(a);
+  else if (D == 3 && NR == 1) k_bstage2<3, 1, T, S><<<grid, kBlockedThreads, 0, s>>>(a);
+  else if (D == 3 && NR == 2) k_bstage2<3, 2, T, S><<<grid, kBlockedThreads, 0, s>>>(a);
   else return cudaErrorInvalidValue;
   k_bqsum<T><<<unsigned((int64_t(a.Nc) * 3 + 255) / 256), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 #define UGKS_INSTANTIATE_BLOCKED(T)                                                                  \
-  template cudaError_t launch_brecon<T>(cudaStream_t, const BlockedArgs<T>&, int64_t, int);          \
+  template cudaError_t launch_brecon<T, T>(cudaStream_t, const BlockedArgs<T>&, int64_t, int);       \
   template cudaError_t launch_bflux<T>(cudaStream_t, const BlockedArgs<T>&, int64_t, int, int);     \
-  template cudaError_t launch_bstage1<T>(cudaStream_t, const BlockedArgs<T>&, int64_t, int);        \
+  template cudaError_t launch_bstage1<T, T>(cudaStream_t, const BlockedArgs<T>&, int64_t, int);     \
   template cudaError_t launch_bcelleq<T>(cudaStream_t, const BlockedArgs<T>&);                       \
   template cudaError_t launch_bconserve<T>(cudaStream_t, const BlockedArgs<T>&);                     \
-  template cudaError_t launch_bstage2<T>(cudaStream_t, const BlockedArgs<T>&);
+  template cudaError_t launch_bstage2<T, T>(cudaStream_t, const BlockedArgs<T>&);
+
+// FP32 arithmetic with FP16 / BF16 scaled storage: the kernels that read or
+// write f (the flux kernel reads only the per-face buffer).
+#define UGKS_INSTANTIATE_SCALED(S)                                                                   \
+  template cudaError_t launch_brecon<float, S>(cudaStream_t, const BlockedArgs<float>&, int64_t, int);   \
+  template cudaError_t launch_bstage1<float, S>(cudaStream_t, const BlockedArgs<float>&, int64_t, int);  \
+  template cudaError_t launch_bstage2<float, S>(cudaStream_t, const BlockedArgs<float>&);
 
 }  // namespace ugks

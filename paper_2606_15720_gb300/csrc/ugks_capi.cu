@@ -12,11 +12,15 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "ugks.h"
 #include "ugks_internal.cuh"
 #include "ugks_kernels.cuh"
+#include "ugks_store.cuh"
 
 using namespace ugks;
 
@@ -70,8 +74,11 @@ struct ugks_ctx {
   void *d_uxT = nullptr, *d_uyT = nullptr, *d_uzT = nullptr, *d_wT = nullptr, *d_velT = nullptr;
   // distributions
   void* d_f[2] = {nullptr, nullptr};
+  // scaled (FP16 / BF16) storage: per-row scales and per-cell reference Maxwellians
+  float* d_sc[2] = {nullptr, nullptr};
+  RefMaxwell* d_ref[2] = {nullptr, nullptr};
   // sweep organisation: 1 tiled, 2 blocked; velocities per lane of the blocked sweep
-  int variant = 2, vb = 1;
+  int variant = 2, vb = 1, vb_max = 1;  // vb_max: the block size the per-face buffer was sized for
   // blocked sweep: 32-bit incidence records, per-block scratch
   int32_t* d_cf_off32 = nullptr;
   void* d_inc = nullptr;
@@ -129,6 +136,13 @@ ugks_status fail(ugks_ctx* ctx, ugks_status st, const char* fmt, ...) {
       return fail(ctx, UGKS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));            \
     }                                                                                             \
   } while (0)
+
+// Calls CALL(T, S) with the arithmetic type T and the storage type S of the context.
+#define UGKS_BY_STORAGE(ctx, CALL)                                          \
+  ((ctx)->storage == UGKS_STORAGE_F64    ? CALL(double, double)             \
+   : (ctx)->storage == UGKS_STORAGE_F16  ? CALL(float, __half)              \
+   : (ctx)->storage == UGKS_STORAGE_BF16 ? CALL(float, __nv_bfloat16)       \
+                                         : CALL(float, float))
 
 template <typename P>
 cudaError_t dalloc(ugks_ctx* ctx, P** ptr, size_t bytes) {
@@ -256,8 +270,10 @@ ugks_status validate(const ugks_mesh* m, const ugks_vgrid* v, const ugks_params*
   if (!(p->dt_override > 0.0) && !(p->cfl > 0.0))
     return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "need cfl > 0 or dt_override > 0");
   if (p->limiter < 0 || p->limiter > 2) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "unknown limiter");
-  if (p->storage != UGKS_STORAGE_F64 && p->storage != UGKS_STORAGE_F32)
-    return fail(nullptr, UGKS_ERR_UNSUPPORTED, "storage precision %d not implemented", p->storage);
+  if (p->storage < UGKS_STORAGE_F64 || p->storage > UGKS_STORAGE_BF16)
+    return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "unknown storage precision %d", p->storage);
+  if ((p->storage == UGKS_STORAGE_F16 || p->storage == UGKS_STORAGE_BF16) && p->sweep == UGKS_SWEEP_TILED)
+    return fail(nullptr, UGKS_ERR_UNSUPPORTED, "FP16 / BF16 storage runs in the blocked sweep only");
   if (p->tile_cells < 0) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "tile_cells must be >= 0");
   if (p->sweep < UGKS_SWEEP_AUTO || p->sweep > UGKS_SWEEP_BLOCKED)
     return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "unknown sweep %d", p->sweep);
@@ -311,7 +327,7 @@ size_t blocked_X_bytes(const ugks_ctx* ctx) {
 size_t blocked_Facc_bytes(const ugks_ctx* ctx) { return size_t(ctx->Nf) * FACC_W * sizeof(double); }
 size_t blocked_qpart_bytes(const ugks_ctx* ctx) { return size_t(ctx->nchunk) * ctx->Nc * 3 * sizeof(double); }
 
-template <typename T>
+template <typename T, typename S>
 ugks_status build_typed(ugks_ctx* ctx, const std::vector<int64_t>& cf_off, const std::vector<CellFace>& cf,
                         const std::vector<double>& eps2,
                         const std::vector<FaceGeom<double>>& fg64, const double* ux, const double* uy,
@@ -429,17 +445,38 @@ ugks_status build_typed(ugks_ctx* ctx, const std::vector<int64_t>& cf_off, const
     ctx->last_facc = ctx->d_Facc_b;
     CUDA_TRY(ctx, dalloc(ctx, &ctx->d_qpart, blocked_qpart_bytes(ctx)));
   }
-  const size_t fsz = size_t(ctx->NR) * ctx->M * ctx->Nc * BV * sizeof(T);
+  const size_t fsz = size_t(ctx->NR) * ctx->M * ctx->Nc * BV * sizeof(S);
   for (int s = 0; s < 2; ++s) {
-    T* f;
+    S* f;
     CUDA_TRY(ctx, dalloc(ctx, &f, fsz));
     ctx->d_f[s] = f;
+  }
+  if (StoreTraits<S>::scaled) {
+    if (ctx->W > 8)
+      return fail(ctx, UGKS_ERR_UNSUPPORTED, "FP16 / BF16 storage needs at most 8 faces per cell (this mesh has %d)",
+                  ctx->W);
+    for (int s = 0; s < 2; ++s) {
+      CUDA_TRY(ctx, dalloc(ctx, &ctx->d_sc[s], size_t(ctx->NR) * ctx->M * ctx->Nc * sizeof(float)));
+      CUDA_TRY(ctx, dalloc(ctx, &ctx->d_ref[s], size_t(ctx->Nc) * sizeof(RefMaxwell)));
+    }
   }
   return UGKS_OK;
 }
 
-template <typename T>
+template <typename T, typename S>
 ugks_status init_state_typed(ugks_ctx* ctx) {
+  if constexpr (StoreTraits<S>::scaled) {
+    // f^0 = the discrete Maxwellian of W_init = its reference: zero deviations and scales
+    launch_sref(ctx->stream, ctx->Nc, ctx->gas, ctx->d_W[0], ctx->d_ref[0]);
+    CUDA_TRY(ctx, cudaGetLastError());
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_f[0], 0, size_t(ctx->NR) * ctx->M * ctx->Nc * BV * sizeof(S), ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_sc[0], 0, size_t(ctx->NR) * ctx->M * ctx->Nc * sizeof(float), ctx->stream));
+    launch_smoments<S>(ctx->stream, ctx->Nc, ctx->M, ctx->nv, ctx->gas, static_cast<const S*>(ctx->d_f[0]),
+                       ctx->d_sc[0], ctx->d_ref[0], ctx->d_W[0], ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp,
+                       ctx->d_q[0], nullptr);
+    CUDA_TRY(ctx, cudaGetLastError());
+    return UGKS_OK;
+  }
   launch_init_f<T>(ctx->stream, ctx->Nc, ctx->M, ctx->nv, ctx->gas, ctx->d_W[0], ctx->d_ux, ctx->d_uy, ctx->d_uz,
                    static_cast<T*>(ctx->d_f[0]));
   CUDA_TRY(ctx, cudaGetLastError());
@@ -459,7 +496,7 @@ ugks_status init_state_typed(ugks_ctx* ctx) {
 // of vb x 32 velocities gradients -> fluxes -> first stage, then the
 // conservative update and the second stage.  The last M mod vb blocks run
 // with one velocity per lane.
-template <typename T>
+template <typename T, typename S>
 ugks_status sweep_blocked(ugks_ctx* ctx, int cur, void* X, double* Facc, double* qpart) {
   const int nxt = 1 - cur;
   BlockedArgs<T> a;
@@ -492,6 +529,10 @@ ugks_status sweep_blocked(ugks_ctx* ctx, int cur, void* X, double* Facc, double*
   a.qpart = qpart;
   a.nchunk = ctx->nchunk;
   a.nsm = ctx->nsm;
+  a.sc_cur = ctx->d_sc[cur];
+  a.sc_next = ctx->d_sc[nxt];
+  a.ref_cur = ctx->d_ref[cur];
+  a.ref_next = ctx->d_ref[nxt];
   a.res_acc = ctx->d_res_acc;
   a.status = ctx->d_status;
   cudaStream_t s = ctx->stream;
@@ -504,13 +545,13 @@ ugks_status sweep_blocked(ugks_ctx* ctx, int cur, void* X, double* Facc, double*
     const int vb = pass == 0 ? ctx->vb : 1;
     for (; m0 + vb <= M; m0 += vb) {
       record_start(ctx, kTGrad, &ev);
-      LAUNCH_TRY(ctx, launch_brecon<T>(s, a, m0, vb));
+      LAUNCH_TRY(ctx, (launch_brecon<T, S>(s, a, m0, vb)));
       record_stop(ctx, kTGrad, ev);
       record_start(ctx, kTFlux, &ev);
       LAUNCH_TRY(ctx, launch_bflux<T>(s, a, m0, vb, m0 == 0 ? 1 : 0));
       record_stop(ctx, kTFlux, ev);
       record_start(ctx, kTStage1, &ev);
-      LAUNCH_TRY(ctx, launch_bstage1<T>(s, a, m0, vb));
+      LAUNCH_TRY(ctx, (launch_bstage1<T, S>(s, a, m0, vb)));
       record_stop(ctx, kTStage1, ev);
     }
   }
@@ -518,13 +559,13 @@ ugks_status sweep_blocked(ugks_ctx* ctx, int cur, void* X, double* Facc, double*
   LAUNCH_TRY(ctx, launch_bconserve<T>(s, a));
   record_stop(ctx, kTConserve, ev);
   record_start(ctx, kTStage2, &ev);
-  LAUNCH_TRY(ctx, launch_bstage2<T>(s, a));
+  LAUNCH_TRY(ctx, (launch_bstage2<T, S>(s, a)));
   record_stop(ctx, kTStage2, ev);
   record_stop(ctx, kTSweep, ev_all);
   return UGKS_OK;
 }
 
-template <typename T>
+template <typename T, typename S>
 ugks_status step_typed(ugks_ctx* ctx) {
   const int cur = ctx->cur, nxt = 1 - cur;
   cudaEvent_t ev;
@@ -541,7 +582,7 @@ ugks_status step_typed(ugks_ctx* ctx) {
   CUDA_TRY(ctx, cudaGetLastError());
   record_stop(ctx, 1, ev);
   if (ctx->variant == 2) {
-    ugks_status st = sweep_blocked<T>(ctx, cur, ctx->d_X, ctx->d_Facc_b, ctx->d_qpart);
+    ugks_status st = sweep_blocked<T, S>(ctx, cur, ctx->d_X, ctx->d_Facc_b, ctx->d_qpart);
     if (st != UGKS_OK) return st;
     ctx->last_facc = ctx->d_Facc_b;
     record_start(ctx, kTRes, &ev);
@@ -614,7 +655,7 @@ size_t static_scratch_need(const ugks_ctx* ctx) {
   return align256(size_t(ctx->ntiles) * ctx->Facc_stride * sizeof(double));
 }
 
-template <typename T>
+template <typename T, typename S>
 ugks_status step_typed_static(ugks_ctx* ctx, unsigned char* base) {
   const int cur = ctx->cur, nxt = 1 - cur;
   CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_res_acc, 0, NWP * sizeof(double), ctx->stream));
@@ -631,7 +672,7 @@ ugks_status step_typed_static(ugks_ctx* ctx, unsigned char* base) {
     unsigned char* qpart = Facc + align256(blocked_Facc_bytes(ctx));
     const bool was_on = ctx->stats_on;
     ctx->stats_on = false;
-    ugks_status st = sweep_blocked<T>(ctx, cur, X, reinterpret_cast<double*>(Facc), reinterpret_cast<double*>(qpart));
+    ugks_status st = sweep_blocked<T, S>(ctx, cur, X, reinterpret_cast<double*>(Facc), reinterpret_cast<double*>(qpart));
     ctx->stats_on = was_on;
     if (st != UGKS_OK) return st;
     ctx->last_facc = reinterpret_cast<double*>(Facc);
@@ -857,6 +898,7 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
   }
   ctx->vb = p->block_velocities > 0 ? p->block_velocities / BV : 4;
   while (ctx->vb > ctx->M) ctx->vb /= 2;
+  ctx->vb_max = ctx->vb;
   ctx->nchunk = int(std::min<int64_t>(ctx->M, 8));
 
   // ---- tiles of the tiled sweep ----
@@ -1078,11 +1120,13 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
   }
   g.dt = ctx->dt;
 
-  ugks_status st = ctx->storage == UGKS_STORAGE_F64
-                       ? build_typed<double>(ctx, cf_off, cf, eps2, fg, ux.data(), uy.data(), uz.data(), wp.data())
-                       : build_typed<float>(ctx, cf_off, cf, eps2, fg, ux.data(), uy.data(), uz.data(), wp.data());
+#define UGKS_BUILD(T, S) build_typed<T, S>(ctx, cf_off, cf, eps2, fg, ux.data(), uy.data(), uz.data(), wp.data())
+  ugks_status st = UGKS_BY_STORAGE(ctx, UGKS_BUILD);
+#undef UGKS_BUILD
   if (st != UGKS_OK) return st;
-  st = ctx->storage == UGKS_STORAGE_F64 ? init_state_typed<double>(ctx) : init_state_typed<float>(ctx);
+#define UGKS_INIT(T, S) init_state_typed<T, S>(ctx)
+  st = UGKS_BY_STORAGE(ctx, UGKS_INIT);
+#undef UGKS_INIT
   if (st != UGKS_OK) return st;
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return UGKS_OK;
@@ -1120,7 +1164,9 @@ ugks_status ugks_step(ugks_ctx* ctx, int32_t n_steps) {
   if (!ctx) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL context");
   if (n_steps < 0) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "n_steps must be >= 0");
   for (int32_t s = 0; s < n_steps; ++s) {
-    ugks_status st = ctx->storage == UGKS_STORAGE_F64 ? step_typed<double>(ctx) : step_typed<float>(ctx);
+#define UGKS_STEP(T, S) step_typed<T, S>(ctx)
+    ugks_status st = UGKS_BY_STORAGE(ctx, UGKS_STEP);
+#undef UGKS_STEP
     if (st != UGKS_OK) return st;
   }
   return UGKS_OK;
@@ -1131,7 +1177,7 @@ ugks_status ugks_step_static_scratch(ugks_ctx* ctx, int32_t n_steps) {
   if (!ctx) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL context");
   if (n_steps < 0) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "n_steps must be >= 0");
   const size_t need = ctx->storage == UGKS_STORAGE_F64 ? static_scratch_need<double>(ctx)
-                                                       : static_scratch_need<float>(ctx);
+                                                       : static_scratch_need<float>(ctx);  // FP32 arithmetic otherwise
   if (need > kStaticScratchBytes)
     return fail(ctx, UGKS_ERR_INVALID_ARGUMENT,
                 "ugks_step_static_scratch: this context needs %zu bytes of sweep scratch, more than the static "
@@ -1139,9 +1185,9 @@ ugks_status ugks_step_static_scratch(ugks_ctx* ctx, int32_t n_steps) {
   void* base = nullptr;
   CUDA_TRY(ctx, static_scratch_address(&base));
   for (int32_t s = 0; s < n_steps; ++s) {
-    ugks_status st = ctx->storage == UGKS_STORAGE_F64
-                         ? step_typed_static<double>(ctx, static_cast<unsigned char*>(base))
-                         : step_typed_static<float>(ctx, static_cast<unsigned char*>(base));
+#define UGKS_STEP_STATIC(T, S) step_typed_static<T, S>(ctx, static_cast<unsigned char*>(base))
+    ugks_status st = UGKS_BY_STORAGE(ctx, UGKS_STEP_STATIC);
+#undef UGKS_STEP_STATIC
     if (st != UGKS_OK) return st;
   }
   return UGKS_OK;
@@ -1238,9 +1284,18 @@ ugks_status ugks_get_f(ugks_ctx* ctx, const int64_t* cells, int64_t n, double* o
   cudaError_t e = cudaMalloc(&d_out, nout * sizeof(double));
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_sel, sel.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) {
+    const int c = ctx->cur;
     if (ctx->storage == UGKS_STORAGE_F64)
       launch_gather_f<double>(ctx->stream, ctx->Nc, ctx->M, ctx->NR, ctx->nv,
                               static_cast<const double*>(ctx->d_f[ctx->cur]), d_sel, n, d_out);
+    else if (ctx->storage == UGKS_STORAGE_F16)
+      launch_sgather<__half>(ctx->stream, ctx->Nc, ctx->M, ctx->D, ctx->NR, ctx->nv,
+                             static_cast<const __half*>(ctx->d_f[c]), ctx->d_sc[c], ctx->d_ref[c], ctx->d_ux,
+                             ctx->d_uy, ctx->d_uz, d_sel, n, d_out);
+    else if (ctx->storage == UGKS_STORAGE_BF16)
+      launch_sgather<__nv_bfloat16>(ctx->stream, ctx->Nc, ctx->M, ctx->D, ctx->NR, ctx->nv,
+                                    static_cast<const __nv_bfloat16*>(ctx->d_f[c]), ctx->d_sc[c], ctx->d_ref[c],
+                                    ctx->d_ux, ctx->d_uy, ctx->d_uz, d_sel, n, d_out);
     else
       launch_gather_f<float>(ctx->stream, ctx->Nc, ctx->M, ctx->NR, ctx->nv,
                              static_cast<const float*>(ctx->d_f[ctx->cur]), d_sel, n, d_out);
@@ -1297,10 +1352,20 @@ ugks_status ugks_set_state(ugks_ctx* ctx, const double* W, const double* f, int6
   if (e == cudaSuccess) e = cudaMemcpy(d_in, f, nin * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_map, ctx->old_of_new.data(), ctx->Nc * sizeof(int64_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    if (ctx->storage == UGKS_STORAGE_F64)
+    if (ctx->storage == UGKS_STORAGE_F64) {
       launch_scatter_f<double>(ctx->stream, ctx->Nc, ctx->M, ctx->NR, ctx->nv, d_in, d_map,
                                static_cast<double*>(ctx->d_f[c]));
-    else
+    } else if (ctx->storage == UGKS_STORAGE_F16 || ctx->storage == UGKS_STORAGE_BF16) {
+      // references from the given W, then deviations against them
+      launch_sref(ctx->stream, ctx->Nc, ctx->gas, ctx->d_W[c], ctx->d_ref[c]);
+      if (ctx->storage == UGKS_STORAGE_F16)
+        launch_sscatter<__half>(ctx->stream, ctx->Nc, ctx->M, ctx->D, ctx->NR, ctx->nv, d_in, d_map, ctx->d_ref[c],
+                                ctx->d_ux, ctx->d_uy, ctx->d_uz, static_cast<__half*>(ctx->d_f[c]), ctx->d_sc[c]);
+      else
+        launch_sscatter<__nv_bfloat16>(ctx->stream, ctx->Nc, ctx->M, ctx->D, ctx->NR, ctx->nv, d_in, d_map,
+                                       ctx->d_ref[c], ctx->d_ux, ctx->d_uy, ctx->d_uz,
+                                       static_cast<__nv_bfloat16*>(ctx->d_f[c]), ctx->d_sc[c]);
+    } else
       launch_scatter_f<float>(ctx->stream, ctx->Nc, ctx->M, ctx->NR, ctx->nv, d_in, d_map,
                               static_cast<float*>(ctx->d_f[c]));
     e = cudaGetLastError();
@@ -1309,6 +1374,14 @@ ugks_status ugks_set_state(ugks_ctx* ctx, const double* W, const double* f, int6
     if (ctx->storage == UGKS_STORAGE_F64)
       launch_moments<double>(ctx->stream, ctx->Nc, ctx->M, ctx->gas, static_cast<const double*>(ctx->d_f[c]),
                              ctx->d_W[c], ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp, ctx->d_q[c], nullptr);
+    else if (ctx->storage == UGKS_STORAGE_F16)
+      launch_smoments<__half>(ctx->stream, ctx->Nc, ctx->M, ctx->nv, ctx->gas, static_cast<const __half*>(ctx->d_f[c]),
+                              ctx->d_sc[c], ctx->d_ref[c], ctx->d_W[c], ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp,
+                              ctx->d_q[c], nullptr);
+    else if (ctx->storage == UGKS_STORAGE_BF16)
+      launch_smoments<__nv_bfloat16>(ctx->stream, ctx->Nc, ctx->M, ctx->nv, ctx->gas,
+                                     static_cast<const __nv_bfloat16*>(ctx->d_f[c]), ctx->d_sc[c], ctx->d_ref[c],
+                                     ctx->d_W[c], ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp, ctx->d_q[c], nullptr);
     else
       launch_moments<float>(ctx->stream, ctx->Nc, ctx->M, ctx->gas, static_cast<const float*>(ctx->d_f[c]),
                             ctx->d_W[c], ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp, ctx->d_q[c], nullptr);
@@ -1383,6 +1456,281 @@ ugks_status ugks_destroy(ugks_ctx* ctx) {
 const char* ugks_last_error(const ugks_ctx* ctx) {
   if (ctx) return ctx->err.c_str();
   return g_thread_err.c_str();
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of cases: one CUDA-graph launch advances every case by two steps
+// (the graph holds two steps of each case, so the double buffers return to
+// their starting parity), each case on its own forked stream so that small
+// cases run concurrently; a block-size autotuner per case.
+// ---------------------------------------------------------------------------
+struct ugks_batch {
+  std::vector<ugks_ctx*> cases;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t fork = nullptr, done = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> tuned_bv;                 // velocities per block chosen by the autotuner (0: not tuned)
+  std::vector<std::vector<double>> tune_ms;  // ms per step of each candidate (32, 64, 128 velocities)
+  std::string err;
+};
+
+namespace {
+
+using TuneKey = std::tuple<int64_t, int64_t, int, int, int>;  // cells, velocities, dim, reduced, storage
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_cache;                            // -> velocities per block lane (1, 2 or 4)
+
+ugks_status bfail(ugks_batch* b, ugks_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (b) b->err = buf;
+  g_thread_err = buf;
+  return st;
+}
+
+void batch_release(ugks_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  b->join.clear();
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+  for (ugks_ctx* c : b->cases) ugks_destroy(c);
+  b->cases.clear();
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+ugks_status ctx_step(ugks_ctx* ctx) {
+#define UGKS_STEP(T, S) step_typed<T, S>(ctx)
+  return UGKS_BY_STORAGE(ctx, UGKS_STEP);
+#undef UGKS_STEP
+}
+
+// The batch stream waits for the work queued on every case stream, or the
+// case streams wait for the batch stream.
+cudaError_t batch_join_cases(ugks_batch* b) {
+  for (size_t i = 0; i < b->cases.size(); ++i) {
+    cudaError_t e = cudaEventRecord(b->join[i], b->cases[i]->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+cudaError_t batch_release_cases(ugks_batch* b) {
+  cudaError_t e = cudaEventRecord(b->done, b->stream);
+  for (size_t i = 0; e == cudaSuccess && i < b->cases.size(); ++i) e = cudaStreamWaitEvent(b->cases[i]->stream, b->done, 0);
+  return e;
+}
+
+ugks_status batch_capture(ugks_batch* b) {
+  const size_t n = b->cases.size();
+  std::vector<int> cur(n);
+  std::vector<int64_t> step(n);
+  std::vector<bool> stats(n);
+  for (size_t i = 0; i < n; ++i) {
+    cur[i] = b->cases[i]->cur;
+    step[i] = b->cases[i]->step;
+    stats[i] = b->cases[i]->stats_on;
+    b->cases[i]->stats_on = false;
+  }
+  ugks_status st = UGKS_OK;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
+  for (size_t i = 0; e == cudaSuccess && st == UGKS_OK && i < n; ++i) {
+    ugks_ctx* c = b->cases[i];
+    e = cudaStreamWaitEvent(c->stream, b->fork, 0);
+    for (int k = 0; e == cudaSuccess && st == UGKS_OK && k < 2; ++k) st = ctx_step(c);
+    if (e == cudaSuccess && st == UGKS_OK) e = cudaEventRecord(b->join[i], c->stream);
+    if (e == cudaSuccess && st == UGKS_OK) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e_end = cudaStreamEndCapture(b->stream, &g);
+  for (size_t i = 0; i < n; ++i) {  // the capture recorded the steps; none ran
+    b->cases[i]->cur = cur[i];
+    b->cases[i]->step = step[i];
+    b->cases[i]->stats_on = stats[i];
+  }
+  if (st != UGKS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return bfail(b, st, "capturing the batch step failed: %s", ugks_last_error(nullptr));
+  }
+  if (e == cudaSuccess) e = e_end;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    b->exec = nullptr;
+    return bfail(b, UGKS_ERR_CUDA, "capturing the batch step failed: %s", cudaGetErrorString(e));
+  }
+  b->graph = g;
+  return UGKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ugks_status ugks_batch_create(int32_t n, const ugks_mesh* const* meshes, const ugks_vgrid* const* vgrids,
+                              const ugks_params* params, const double* const* W_init, void* cuda_stream,
+                              ugks_batch** out) {
+  if (!out) return bfail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "out must not be NULL");
+  *out = nullptr;
+  if (n < 1 || !meshes || !vgrids || !params)
+    return bfail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "a batch needs n >= 1 meshes, grids and parameter sets");
+  for (int32_t i = 0; i < n; ++i)
+    if (params[i].sweep == UGKS_SWEEP_TILED)
+      return bfail(nullptr, UGKS_ERR_UNSUPPORTED, "case %d: batches run the blocked sweep", i);
+  ugks_batch* b = new (std::nothrow) ugks_batch();
+  if (!b) return bfail(nullptr, UGKS_ERR_OUT_OF_MEMORY, "host allocation failed");
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    b->own_stream = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    batch_release(b);
+    delete b;
+    return bfail(nullptr, UGKS_ERR_CUDA, "batch set-up: %s", cudaGetErrorString(e));
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    ugks_ctx* c = nullptr;
+    ugks_status st = ugks_create(meshes[i], vgrids[i], &params[i], W_init ? W_init[i] : nullptr, nullptr, &c);
+    if (st != UGKS_OK) {
+      std::string msg = g_thread_err;
+      batch_release(b);
+      delete b;
+      return bfail(nullptr, st, "case %d: %s", i, msg.c_str());
+    }
+    b->cases.push_back(c);
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      batch_release(b);
+      delete b;
+      return bfail(nullptr, UGKS_ERR_CUDA, "batch set-up: %s", cudaGetErrorString(e));
+    }
+    b->join.push_back(ev);
+    // a shape tuned earlier in this process needs no tuning steps
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(TuneKey(c->Nc, c->nv, c->D, c->NR, c->storage));
+    b->tuned_bv.push_back(0);
+    b->tune_ms.push_back(std::vector<double>(3, 0.0));
+    if (it != g_tune_cache.end() && it->second <= c->vb_max) {
+      c->vb = it->second;
+      b->tuned_bv.back() = it->second * BV;
+    }
+  }
+  *out = b;
+  return UGKS_OK;
+}
+
+ugks_status ugks_batch_autotune(ugks_batch* b) {
+  if (!b) return bfail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL batch");
+  if (b->exec) {  // a new block size changes the kernels: recapture on the next step
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+  if (batch_release_cases(b) != cudaSuccess) return bfail(b, UGKS_ERR_CUDA, "autotune: stream ordering failed");
+  cudaEvent_t t0, t1;
+  if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
+    return bfail(b, UGKS_ERR_CUDA, "autotune: event creation failed");
+  ugks_status st = UGKS_OK;
+  for (size_t i = 0; st == UGKS_OK && i < b->cases.size(); ++i) {
+    ugks_ctx* c = b->cases[i];
+    if (b->tuned_bv[i]) continue;
+    int best = c->vb;
+    double best_ms = 1e300;
+    for (int v = 1, slot = 0; v <= c->vb_max && st == UGKS_OK; v *= 2, ++slot) {
+      c->vb = v;
+      st = ctx_step(c);  // first use of this block size: set-up outside the timing
+      if (st != UGKS_OK) break;
+      cudaEventRecord(t0, c->stream);
+      st = ctx_step(c);
+      cudaEventRecord(t1, c->stream);
+      if (st != UGKS_OK) break;
+      float ms = 0.f;
+      if (cudaEventSynchronize(t1) != cudaSuccess || cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) {
+        st = bfail(b, UGKS_ERR_CUDA, "autotune: timing failed");
+        break;
+      }
+      b->tune_ms[i][slot] = ms;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = v;
+      }
+    }
+    if (st != UGKS_OK) break;
+    c->vb = best;
+    b->tuned_bv[i] = best * BV;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[TuneKey(c->Nc, c->nv, c->D, c->NR, c->storage)] = best;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (st != UGKS_OK && b->err.empty()) b->err = g_thread_err;
+  return st;
+}
+
+ugks_status ugks_batch_step(ugks_batch* b, int32_t n_steps) {
+  if (!b) return bfail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL batch");
+  if (n_steps < 0) return bfail(b, UGKS_ERR_INVALID_ARGUMENT, "n_steps must be >= 0");
+  if (n_steps >= 2 && !b->exec) {
+    ugks_status st = batch_capture(b);
+    if (st != UGKS_OK) return st;
+  }
+  cudaError_t e = batch_join_cases(b);
+  for (int32_t k = 0; e == cudaSuccess && k + 1 < n_steps; k += 2) {
+    e = cudaGraphLaunch(b->exec, b->stream);
+    for (ugks_ctx* c : b->cases) c->step += 2;
+  }
+  if (e == cudaSuccess) e = batch_release_cases(b);
+  if (e != cudaSuccess) return bfail(b, UGKS_ERR_CUDA, "batch step: %s", cudaGetErrorString(e));
+  if (n_steps % 2) {
+    for (ugks_ctx* c : b->cases) {
+      ugks_status st = ctx_step(c);
+      if (st != UGKS_OK) return bfail(b, st, "batch step: %s", c->err.c_str());
+    }
+  }
+  return UGKS_OK;
+}
+
+ugks_status ugks_batch_context(ugks_batch* b, int32_t i, ugks_ctx** ctx_out) {
+  if (!b || !ctx_out || i < 0 || i >= int32_t(b->cases.size()))
+    return bfail(b, UGKS_ERR_INVALID_ARGUMENT, "no case %d in this batch", i);
+  *ctx_out = b->cases[i];
+  return UGKS_OK;
+}
+
+ugks_status ugks_batch_tuning(ugks_batch* b, int32_t i, int32_t* block_velocities, double* ms_per_step) {
+  if (!b || i < 0 || i >= int32_t(b->cases.size()))
+    return bfail(b, UGKS_ERR_INVALID_ARGUMENT, "no case %d in this batch", i);
+  if (block_velocities) *block_velocities = b->tuned_bv[i] ? b->tuned_bv[i] : b->cases[i]->vb * BV;
+  if (ms_per_step)
+    for (int k = 0; k < 3; ++k) ms_per_step[k] = b->tune_ms[i][k];
+  return UGKS_OK;
+}
+
+ugks_status ugks_batch_destroy(ugks_batch* b) {
+  if (!b) return UGKS_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_release(b);
+  delete b;
+  return UGKS_OK;
 }
 
 }  // extern "C"

@@ -145,6 +145,14 @@ struct __align__(16) CellEq {
   T inv_vol;
 };
 
+// Reference Maxwellian of one cell for scaled (FP16 / BF16) storage of f:
+// g_ref = pref exp(-lam |u - U|^2) for h and kap g_ref for b.  Each stored
+// row of 32 values holds (f - g_ref) / s in the storage type, s = the row's
+// largest |f - g_ref| in FP32.
+struct __align__(16) RefMaxwell {
+  float pref, lam, U[3], kap, pad[2];
+};
+
 struct BCDev {
   int32_t type;
   int32_t pad;

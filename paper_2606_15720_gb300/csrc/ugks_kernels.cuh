@@ -116,6 +116,12 @@ struct BlockedArgs {
   T* X;                          // per face, one block [Nf][NR][VB][BV]: the upwind
                                  // reconstruction, then the micro flux
   double* Facc;                  // face accumulators [Nf][FACC_W]
+  // scaled storage only (FP16 / BF16 rows): f_cur / f_next then point to the
+  // stored deviations, and
+  const float* sc_cur;           // per-row scales of f^n [NR][M][Nc]
+  float* sc_next;                // per-row scales of f~, then of f^{n+1}
+  const RefMaxwell* ref_cur;     // reference Maxwellian of f^n and f~ per cell
+  RefMaxwell* ref_next;          // reference Maxwellian of f^{n+1}
   double* qpart;                 // heat-flux partial sums [nchunk][Nc][3]
   int nchunk;                    // velocity chunks of the second stage
   int nsm;                       // multiprocessors of the device (persistent grids)
@@ -123,18 +129,33 @@ struct BlockedArgs {
   int* status;
 };
 
-template <typename T>
+template <typename T, typename S>
 cudaError_t launch_brecon(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb);
 template <typename T>
 cudaError_t launch_bflux(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb, int first);
-template <typename T>
+template <typename T, typename S>
 cudaError_t launch_bstage1(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb);
 template <typename T>
 cudaError_t launch_bcelleq(cudaStream_t s, const BlockedArgs<T>& a);
 template <typename T>
 cudaError_t launch_bconserve(cudaStream_t s, const BlockedArgs<T>& a);
-template <typename T>
+template <typename T, typename S>
 cudaError_t launch_bstage2(cudaStream_t s, const BlockedArgs<T>& a);
+
+// Scaled (FP16 / BF16) storage of f, ugks_store_util.cu.
+void launch_sref(cudaStream_t s, int64_t Nc, const Gas& g, const double* W, RefMaxwell* ref);
+template <typename S>
+void launch_smoments(cudaStream_t s, int64_t Nc, int64_t M, int64_t nv, const Gas& g, const S* f, const float* sc,
+                     const RefMaxwell* ref, const double* W, const double* ux, const double* uy, const double* uz,
+                     const double* w, double* q_out, double* Wf_out);
+template <typename S>
+void launch_sgather(cudaStream_t s, int64_t Nc, int64_t M, int D, int NR, int64_t nv, const S* f, const float* sc,
+                    const RefMaxwell* ref, const double* ux, const double* uy, const double* uz, const int64_t* sel,
+                    int64_t n, double* out);
+template <typename S>
+void launch_sscatter(cudaStream_t s, int64_t Nc, int64_t M, int D, int NR, int64_t nv, const double* in,
+                     const int64_t* old_of_new, const RefMaxwell* ref, const double* ux, const double* uy,
+                     const double* uz, S* f, float* sc);
 
 // Size of the file-scope device scratch used by ugks_step_static_scratch.
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB

@@ -86,6 +86,12 @@ def load(build_if_missing: bool = True):
         "ugks_stats": [P, I32, P, P, P, P],
         "ugks_solve": [P, P, P, P, I32, P, P],
         "ugks_surface": [P, P, I64, P, P, P, P],
+        "ugks_batch_create": [I32, P, P, P, P, P, P],
+        "ugks_batch_autotune": [P],
+        "ugks_batch_step": [P, I32],
+        "ugks_batch_context": [P, I32, P],
+        "ugks_batch_tuning": [P, I32, P, P],
+        "ugks_batch_destroy": [P],
         "ugks_destroy": [P],
     }
     for name, args in sig.items():
@@ -179,6 +185,17 @@ class Solver:
         self.n_reduced = nr.value
         self.n_v_padded = nvp.value
 
+    @classmethod
+    def _view(cls, lib, ctx, mesh: Mesh, grid: VelocityGrid, gas: Gas) -> "Solver":
+        """A Solver over a context owned by someone else (a batch case)."""
+        self = cls.__new__(cls)
+        self._lib, self._ctx, self._owned = lib, ctx, False
+        self.mesh, self.grid, self.gas, self.dim = mesh, grid, gas, mesh.dim
+        nr, nvp = ctypes.c_int32(), ctypes.c_int64()
+        lib.ugks_sizes(ctx, ctypes.byref(nr), ctypes.byref(nvp))
+        self.n_reduced, self.n_v_padded = nr.value, nvp.value
+        return self
+
     def _c(self, st):
         _check(self._lib, st, self._ctx)
 
@@ -252,9 +269,73 @@ class Solver:
         return {names[i].decode(): (float(ms[i]), int(cnt[i])) for i in range(n.value)}
 
     def close(self) -> None:
-        if getattr(self, "_ctx", None):
+        if getattr(self, "_ctx", None) and getattr(self, "_owned", True):
             self._lib.ugks_destroy(self._ctx)
-            self._ctx = None
+        self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """ugks_batch_*: many cases stepped by one CUDA-graph launch per two steps."""
+
+    def __init__(self, meshes, grids, gases, W_inits=None, storage: str = "f32", block_velocities: int = 0,
+                 stream: Optional[int] = None):
+        self._lib = load()
+        n = len(meshes)
+        self._args = [_MeshArgs(m, g) for m, g in zip(meshes, grids)]
+        self.meshes, self.grids, self.gases = list(meshes), list(grids), list(gases)
+        mptr = (ctypes.c_void_p * n)(*[ctypes.addressof(a.mesh) for a in self._args])
+        gptr = (ctypes.c_void_p * n)(*[ctypes.addressof(a.grid) for a in self._args])
+        prms = (ugks_params * n)(*[make_params(gs, storage, 0, "blocked", block_velocities) for gs in gases])
+        self._W = None
+        wptr = None
+        if W_inits is not None:
+            self._W = [np.ascontiguousarray(W, dtype=np.float64) for W in W_inits]
+            wptr = (ctypes.c_void_p * n)(*[_ptr(W) for W in self._W])
+        if stream is None:
+            stream = current_stream_handle()
+        b = ctypes.c_void_p()
+        _check(self._lib, self._lib.ugks_batch_create(n, mptr, gptr, prms, wptr, stream, ctypes.byref(b)))
+        self._b = b
+        self.cases = []
+        for i in range(n):
+            c = ctypes.c_void_p()
+            self._c(self._lib.ugks_batch_context(self._b, i, ctypes.byref(c)))
+            self.cases.append(Solver._view(self._lib, c, meshes[i], grids[i], gases[i]))
+
+    def _c(self, st):
+        if st != 0:
+            raise UGKSError(st, self._lib.ugks_last_error(None).decode(errors="replace"))
+
+    def autotune(self) -> None:
+        self._c(self._lib.ugks_batch_autotune(self._b))
+
+    def step(self, n: int = 1) -> None:
+        self._c(self._lib.ugks_batch_step(self._b, int(n)))
+
+    def tuning(self, i: int):
+        bv = ctypes.c_int32()
+        ms = np.zeros(3)
+        self._c(self._lib.ugks_batch_tuning(self._b, int(i), ctypes.byref(bv), _ptr(ms)))
+        return bv.value, ms
+
+    def close(self) -> None:
+        if getattr(self, "_b", None):
+            for c in self.cases:
+                c._ctx = None
+            self._lib.ugks_batch_destroy(self._b)
+            self._b = None
 
     def __del__(self):
         try:

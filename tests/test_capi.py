@@ -36,10 +36,12 @@ def test_library_exports_every_declared_entry_point(lib):
     assert not missing, missing
 
 
-def _status_of(mesh, grid, gas, storage="f32"):
+def _status_of(mesh, grid, gas, storage="f32", sweep="auto", raw_storage=None):
     lib = ugks.load()
     args = ugks._MeshArgs(mesh, grid)
-    prm = ugks.make_params(gas, storage)
+    prm = ugks.make_params(gas, storage, sweep=sweep)
+    if raw_storage is not None:
+        prm.storage = raw_storage
     ctx = ctypes.c_void_p()
     st = lib.ugks_create(ctypes.byref(args.mesh), ctypes.byref(args.grid), ctypes.byref(prm), None, None,
                          ctypes.byref(ctx))
@@ -68,8 +70,10 @@ def test_validation_errors_are_reported_before_any_device_work(lib):
     assert _status_of(mesh, g2, gas)[0] == 3                         # UGKS_ERR_VGRID
     assert _status_of(mesh, grid, I.Gas(model="shakhov", Pr=2 / 3, K=1))[0] == 8   # UNSUPPORTED
     assert _status_of(mesh, grid, I.Gas(model="bgk", Pr=0.7))[0] == 1             # INVALID
-    st, msg = _status_of(mesh, grid, gas, storage="f16")
+    st, msg = _status_of(mesh, grid, gas, storage="f16", sweep="tiled")   # FP16 runs in the blocked sweep only
     assert st == 8 and "storage" in msg
+    st, msg = _status_of(mesh, grid, gas, raw_storage=7)
+    assert st == 1 and "storage" in msg
     out = ctypes.c_void_p()
     assert lib.ugks_create(None, None, None, None, None, ctypes.byref(out)) == 1
     assert lib.ugks_create(None, None, None, None, None, None) == 1

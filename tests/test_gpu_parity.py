@@ -61,6 +61,7 @@ SWEEPS = {
     "blocked32": dict(sweep="blocked", block_velocities=32),
     "blocked128": dict(sweep="blocked", block_velocities=128),
     "tiled": dict(sweep="tiled", tile_cells=48),
+    "scaled": dict(sweep="blocked"),   # the storage argument selects FP16 / BF16
 }
 _oracle_cache = {}
 
@@ -147,7 +148,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("sweep", sorted(SWEEPS))
+@pytest.mark.parametrize("sweep", sorted(k for k in SWEEPS if k != "scaled"))
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_fp64_matches_oracle(U, name, sweep):
     mesh, grid, gas, prim = CASES[name]()
@@ -157,7 +158,7 @@ def test_fp64_matches_oracle(U, name, sweep):
     np.testing.assert_allclose(res, diag[-1, :mesh.dim + 2], rtol=1e-9, atol=1e-300)
 
 
-@pytest.mark.parametrize("sweep", sorted(SWEEPS))
+@pytest.mark.parametrize("sweep", sorted(k for k in SWEEPS if k != "scaled"))
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_fp32_one_step_matches_oracle(U, name, sweep):
     mesh, grid, gas, prim = CASES[name]()
@@ -216,10 +217,12 @@ def test_sweep_organisations_agree(U):
     W0 = I.prim_to_conservative(prim, 3, 0)
     outs = {}
     for name, kw in SWEEPS.items():
+        if name == "scaled":
+            continue
         with U.Solver(mesh, grid, gas, W0, storage="f64", **kw) as s:
             s.step(4)
             outs[name] = s.moments()
-    for name in SWEEPS:
+    for name in outs:
         assert w_err(outs[name], outs["tiled"]) <= 1e-13, name
 
 
@@ -316,3 +319,65 @@ def test_surface_is_refused_for_the_tiled_sweep(U):
         with pytest.raises(U.UGKSError) as e:
             s.surface()
         assert e.value.status == 8
+
+
+# Unit round-off of the scaled storage formats (11 and 8 significant bits).
+STORAGE_EPS = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+def _deviation_ratio(mesh, grid, gas, W, f):
+    """max |f - g(W)| / max |f| per reduced distribution, g = the discrete
+    Maxwellian of W (the reference the scaled storage encodes against)."""
+    g = O.initial_f(mesh, grid, W, gas.K)
+    return np.array([np.max(np.abs(f[r] - g[r])) / np.max(np.abs(f[r])) for r in range(f.shape[0])])
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_scaled_storage_one_step_matches_oracle(U, name, storage):
+    """FP16 / BF16 deviations from a per-cell reference Maxwellian, FP32
+    arithmetic.  f^0 is its own reference (zero deviations), so W after one step
+    carries FP32 rounding only (<= 1e-5).  f^1 carries two storage roundings,
+    each at most eps of the value's deviation from its reference (f~ against the
+    Maxwellian of W^0, f^1 against that of W^1): per reduced distribution the
+    error is within 1e-5 + 2 eps (D0 + D1) of max |f|, D0 and D1 the oracle's
+    largest deviations from the two references."""
+    mesh, grid, gas, prim = CASES[name]()
+    Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 1, storage, "scaled", key=name)
+    W0 = I.prim_to_conservative(prim, mesh.dim, gas.K)
+    assert w_err(Wg, Wo) <= 1e-5, w_err(Wg, Wo)
+    dev = _deviation_ratio(mesh, grid, gas, W0, fo) + _deviation_ratio(mesh, grid, gas, Wo, fo)
+    for r in range(fo.shape[0]):
+        err = np.max(np.abs(fg[r] - fo[r])) / np.max(np.abs(fo[r]))
+        assert err <= 1e-5 + 2 * STORAGE_EPS[storage] * dev[r], (r, err, dev[r])
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("name", ["cavity_bgk", "periodic3d_bgk_K2", "strip1d_farfield_outflow"])
+def test_scaled_storage_hundred_steps_matches_oracle(U, name, storage):
+    """100 steps: each step adds to f at most eps times its deviation from the
+    reference (at most 0.1 of max |f| in these cases), which moves W by at most
+    that much per step (CFL < 1); accumulated linearly: W within 100 eps 0.1."""
+    mesh, grid, gas, prim = CASES[name]()
+    Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 100, storage, "scaled", key="long_" + name)
+    assert w_err(Wg, Wo) <= 100 * STORAGE_EPS[storage] * 0.1, w_err(Wg, Wo)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_scaled_storage_checkpoint_roundtrip(U, storage):
+    """get_state / set_state re-encode f against the Maxwellian of the given W:
+    a restart reproduces the continued run to the storage rounding of f."""
+    mesh, grid, gas, prim = cavity_case(n=8, nvx=10)
+    W0 = I.prim_to_conservative(prim, 2, 0)
+    with U.Solver(mesh, grid, gas, W0, storage=storage) as s:
+        s.step(3)
+        W3, f3, k = s.get_state()
+        s.step(4)
+        W7 = s.moments()
+    with U.Solver(mesh, grid, gas, W0, storage=storage) as s2:
+        s2.set_state(W3, f3, 3)
+        Wr, fr, _ = s2.get_state()
+        np.testing.assert_array_equal(Wr, W3)
+        assert np.max(np.abs(fr - f3)) <= STORAGE_EPS[storage] * np.max(np.abs(f3))
+        s2.step(4)
+        assert w_err(s2.moments(), W7) <= 4 * STORAGE_EPS[storage] * 0.1
