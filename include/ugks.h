@@ -197,6 +197,24 @@ ugks_status ugks_residual(ugks_ctx *ctx, double *res_out);
 ugks_status ugks_surface(ugks_ctx *ctx, const double *freestream, int64_t cap, int64_t *n_wall, int64_t *faces,
                          double *vals, double *coef);
 
+/* Thirteen-moment fields of the current state, per cell (original order),
+ * out[n_cells][n13] with n13 = 2 dim + 2 + dim (dim + 1) / 2:
+ *   rho, U[dim], T (of W), the deviatoric stress sigma_ij = sum_k w c_i c_j h
+ *   - p delta_ij (p = rho T / 2) in the order xx, xy, (xz), yy, (yz), zz, and
+ *   the heat flux q[dim] (Eq. 13), all about U of W.  The paper has no such
+ * call: these are the fields of the learned warm start.  FP64 or FP32
+ * storage (else UGKS_ERR_UNSUPPORTED); synchronises the context stream. */
+ugks_status ugks_moments13(ugks_ctx *ctx, double *out);
+
+/* Resets the state to the Chapman-Enskog (Grad 13-moment) distribution of
+ * the given fields (layout of ugks_moments13; rho, T > 0), reduced over xi:
+ *   h = H [1 + 2 lam^2/rho sigma_ij c_i c_j + 4 lam^2/((K+5) rho) (q.c)(2 lam |c|^2 - (dim+2))]
+ *   b = kappa H [1 + 2 lam^2/rho sigma_ij c_i c_j + 4 lam^2/((K+5) rho) (q.c)(2 lam |c|^2 - dim)]
+ * (H the Maxwellian of rho, U, lam = 1/T; kappa = K_xi/(2 lam)), W from
+ * rho, U, T; the step counter restarts at 0.  A warm start for steady
+ * solves; the paper has no such call.  FP64 or FP32 storage. */
+ugks_status ugks_init_moments13(ugks_ctx *ctx, const double *fields);
+
 /* Time step in use. */
 ugks_status ugks_dt(const ugks_ctx *ctx, double *dt_out);
 

@@ -71,6 +71,8 @@ def load():
         lib.orc_run.restype = ctypes.c_int
         lib.orc_run.argtypes = [P, ctypes.c_int64, P, P, P, P, P, ctypes.c_int32, P, P, P]
         lib.orc_surface.argtypes = [P, P, ctypes.c_double, P, P, P, P]
+        lib.orc_moments13.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P]
+        lib.orc_chapman_enskog.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P, P, P]
         lib.orc_surface.restype = ctypes.c_int64
         lib.orc_time_step.restype = ctypes.c_double
         lib.orc_time_step.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_double]
@@ -243,6 +245,31 @@ def reduced_equilibrium(dim: int, K: int, Pr: float, rho: float, U, lam: float, 
     out = np.zeros(4)
     lib.orc_reduced_equilibrium(dim, K, float(Pr), _p(prim), _p(q), _p(u), _p(out))
     return out
+
+
+def n13(dim: int) -> int:
+    """Entries of the thirteen-moment fields per cell: rho, U, T, sigma, q."""
+    return 2 * dim + 2 + dim * (dim + 1) // 2
+
+
+def moments13(dim: int, K: int, vgrid, W: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """Thirteen-moment fields [cell, n13(dim)] of (W, f) (reading R21)."""
+    lib = load()
+    W, f = _f64(W), _f64(f)
+    nc = W.shape[0]
+    out = np.zeros((nc, n13(dim)))
+    lib.orc_moments13(dim, K, nc, vgrid.n_v, _p(_f64(vgrid.u)), _p(_f64(vgrid.weight)), _p(W), _p(f), _p(out))
+    return out
+
+
+def chapman_enskog(dim: int, K: int, vgrid, fields: np.ndarray) -> np.ndarray:
+    """Chapman-Enskog distribution f[r, cell, k] of thirteen-moment fields (reading R21)."""
+    lib = load()
+    fields = _f64(fields)
+    nc = fields.shape[0]
+    f = np.zeros((n_reduced(dim, K), nc, vgrid.n_v))
+    lib.orc_chapman_enskog(dim, K, nc, vgrid.n_v, _p(_f64(vgrid.u)), _p(fields), _p(f))
+    return f
 
 
 def num_threads() -> int:

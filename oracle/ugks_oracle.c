@@ -36,6 +36,14 @@
  *      p_w = P.n, tau_w = P - p_w n, q_w = (F_energy - U_w.F_momentum) / dt;
  *      coefficients against a free stream (rho, U, T): C_p = (p_w - rho T/2)
  *      / (rho|U|^2/2), C_t = |tau_w| / (rho|U|^2/2), C_h = q_w / (rho|U|^3/2).
+ *   R21 thirteen-moment fields of a cell: rho, U, T = 1/lambda of W, the
+ *      deviatoric stress sigma_ij = sum_k w c_i c_j h - p delta_ij (p = rho /
+ *      (2 lambda)) and q (Eq. 13), c = u - U of W; their Chapman-Enskog
+ *      (Grad 13-moment) distribution, reduced over xi:
+ *        h = H [1 + 2 lam^2/rho sigma_ij c_i c_j + 4 lam^2/((K+5) rho) (q.c)(2 lam c^2 - (D+2))]
+ *        b = kappa H [1 + 2 lam^2/rho sigma_ij c_i c_j + 4 lam^2/((K+5) rho) (q.c)(2 lam c^2 - D)]
+ *      (K + 5 = N + 2 for N = D + K_xi degrees of freedom; at K = 0 the
+ *      heat-flux term has the form of the Shakhov term of Eq. 18-19).
  * Parity: every function below is pinned by tests/test_oracle_pins.py.
  */
 #include <math.h>
@@ -546,6 +554,73 @@ void orc_reduced_equilibrium(int D, int K, double Pr, const double *prim /*rho,U
   out[0] = H;
   out[1] = Kxi / (2.0 * p.lam) * H;
   shakhov_plus(D, Kxi, Pr, &p, q, u, H, &out[2], &out[3]);
+}
+
+/* Thirteen-moment fields of every cell (reading R21): out[cell] = (rho,
+ * U[D], T, sigma[D(D+1)/2] in the order xx, xy, (xz), yy, (yz), zz, q[D]). */
+void orc_moments13(int D, int K, int64_t nc, int64_t nv, const double *u, const double *w, const double *W,
+                   const double *f, double *out) {
+  const int Kxi = K + 3 - D, nr = Kxi > 0 ? 2 : 1, ns = D * (D + 1) / 2, n13 = 2 * D + 2 + ns;
+  for (int64_t i = 0; i < nc; ++i) {
+    prim_t p;
+    prim_from_W(D, K, W + i * (D + 2), &p);
+    const double *h = f + i * nv, *b = nr == 2 ? f + (nc + i) * nv : NULL;
+    double P[MAXD][MAXD], q[MAXD];
+    for (int a = 0; a < D; ++a) {
+      q[a] = 0.0;
+      for (int c = 0; c < D; ++c) P[a][c] = 0.0;
+    }
+    for (int64_t k = 0; k < nv; ++k) {
+      double c[MAXD], c2 = 0.0;
+      for (int d = 0; d < D; ++d) {
+        c[d] = u[k * D + d] - p.U[d];
+        c2 += c[d] * c[d];
+      }
+      for (int a = 0; a < D; ++a) {
+        q[a] += 0.5 * w[k] * c[a] * (c2 * h[k] + (b ? b[k] : 0.0));
+        for (int e = 0; e < D; ++e) P[a][e] += w[k] * c[a] * c[e] * h[k];
+      }
+    }
+    double *o = out + i * n13;
+    const double pr = p.rho / (2.0 * p.lam);
+    o[0] = p.rho;
+    for (int d = 0; d < D; ++d) o[1 + d] = p.U[d];
+    o[D + 1] = 1.0 / p.lam;
+    int s = 0;
+    for (int a = 0; a < D; ++a)
+      for (int e = a; e < D; ++e) o[D + 2 + s++] = P[a][e] - (a == e ? pr : 0.0);
+    for (int d = 0; d < D; ++d) o[D + 2 + ns + d] = q[d];
+  }
+}
+
+/* Chapman-Enskog distribution of given thirteen-moment fields (reading R21):
+ * fields[cell] as written by orc_moments13; f[r][cell][k]. */
+void orc_chapman_enskog(int D, int K, int64_t nc, int64_t nv, const double *u, const double *fields, double *f) {
+  const int Kxi = K + 3 - D, nr = Kxi > 0 ? 2 : 1, ns = D * (D + 1) / 2, n13 = 2 * D + 2 + ns;
+  for (int64_t i = 0; i < nc; ++i) {
+    const double *x = fields + i * n13;
+    prim_t p;
+    p.rho = x[0];
+    for (int d = 0; d < D; ++d) p.U[d] = x[1 + d];
+    p.lam = 1.0 / x[D + 1];
+    const double *sig = x + D + 2, *q = x + D + 2 + ns;
+    const double a2 = 2.0 * p.lam * p.lam / p.rho, a3 = 4.0 * p.lam * p.lam / ((K + 5.0) * p.rho);
+    for (int64_t k = 0; k < nv; ++k) {
+      double c[MAXD], c2 = 0.0, qc = 0.0, scc = 0.0;
+      for (int d = 0; d < D; ++d) {
+        c[d] = u[k * D + d] - p.U[d];
+        c2 += c[d] * c[d];
+        qc += q[d] * c[d];
+      }
+      int s = 0;
+      for (int a = 0; a < D; ++a)
+        for (int e = a; e < D; ++e) scc += (a == e ? 1.0 : 2.0) * sig[s++] * c[a] * c[e];
+      const double H = maxwell_H(D, &p, u + k * D);
+      f[i * nv + k] = H * (1.0 + a2 * scc + a3 * qc * (2.0 * p.lam * c2 - (D + 2)));
+      if (nr == 2)
+        f[(nc + i) * nv + k] = Kxi / (2.0 * p.lam) * H * (1.0 + a2 * scc + a3 * qc * (2.0 * p.lam * c2 - D));
+    }
+  }
 }
 
 /* Initial distribution: discrete reduced Maxwellian of W (reading R18). */

@@ -1255,6 +1255,86 @@ ugks_status ugks_surface(ugks_ctx* ctx, const double* freestream, int64_t cap, i
   return UGKS_OK;
 }
 
+ugks_status ugks_moments13(ugks_ctx* ctx, double* out) {
+  if (!ctx || !out) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "NULL argument");
+  if (ctx->storage != UGKS_STORAGE_F64 && ctx->storage != UGKS_STORAGE_F32)
+    return fail(ctx, UGKS_ERR_UNSUPPORTED, "ugks_moments13 needs FP64 or FP32 storage");
+  ugks_status st = check_status(ctx);
+  if (st != UGKS_OK) return st;
+  const int D = ctx->D, n13 = 2 * D + 2 + D * (D + 1) / 2;
+  double* d_out = nullptr;
+  CUDA_TRY(ctx, cudaMalloc(&d_out, size_t(ctx->Nc) * n13 * sizeof(double)));
+  const int c = ctx->cur;
+  if (ctx->storage == UGKS_STORAGE_F64)
+    launch_moments13<double>(ctx->stream, ctx->Nc, ctx->M, ctx->gas, static_cast<const double*>(ctx->d_f[c]),
+                             ctx->d_W[c], ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp, d_out);
+  else
+    launch_moments13<float>(ctx->stream, ctx->Nc, ctx->M, ctx->gas, static_cast<const float*>(ctx->d_f[c]),
+                            ctx->d_W[c], ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp, d_out);
+  cudaError_t e = cudaGetLastError();
+  std::vector<double> tmp(size_t(ctx->Nc) * n13);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp.data(), d_out, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                            ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d_out);
+  if (e != cudaSuccess) return fail(ctx, UGKS_ERR_CUDA, "ugks_moments13: %s", cudaGetErrorString(e));
+  for (int64_t i = 0; i < ctx->Nc; ++i)
+    std::memcpy(out + size_t(ctx->old_of_new[i]) * n13, &tmp[size_t(i) * n13], n13 * sizeof(double));
+  return UGKS_OK;
+}
+
+ugks_status ugks_init_moments13(ugks_ctx* ctx, const double* fields) {
+  if (!ctx || !fields) return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "NULL argument");
+  if (ctx->storage != UGKS_STORAGE_F64 && ctx->storage != UGKS_STORAGE_F32)
+    return fail(ctx, UGKS_ERR_UNSUPPORTED, "ugks_init_moments13 needs FP64 or FP32 storage");
+  const int D = ctx->D, n13 = 2 * D + 2 + D * (D + 1) / 2;
+  std::vector<double> fl(size_t(ctx->Nc) * n13), Wn(size_t(ctx->Nc) * NWP, 0.0);
+  for (int64_t i = 0; i < ctx->Nc; ++i) {
+    const double* x = fields + size_t(ctx->old_of_new[i]) * n13;
+    for (int t = 0; t < n13; ++t)
+      if (!std::isfinite(x[t]))
+        return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "cell %lld: non-finite field", (long long)ctx->old_of_new[i]);
+    if (!(x[0] > 0.0) || !(x[D + 1] > 0.0))
+      return fail(ctx, UGKS_ERR_INVALID_ARGUMENT, "cell %lld: rho and T must be > 0", (long long)ctx->old_of_new[i]);
+    std::memcpy(&fl[size_t(i) * n13], x, n13 * sizeof(double));
+    double u2 = 0.0;
+    Wn[size_t(i) * NWP] = x[0];
+    for (int d = 0; d < D; ++d) {
+      Wn[size_t(i) * NWP + 1 + d] = x[0] * x[1 + d];
+      u2 += x[1 + d] * x[1 + d];
+    }
+    Wn[size_t(i) * NWP + D + 1] = 0.5 * x[0] * u2 + (ctx->K + 3) * x[0] * x[D + 1] / 4.0;
+  }
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  const int c = ctx->cur;
+  double* d_fields = nullptr;
+  CUDA_TRY(ctx, cudaMalloc(&d_fields, fl.size() * sizeof(double)));
+  cudaError_t e = cudaMemcpyAsync(d_fields, fl.data(), fl.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                  ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->d_W[c], Wn.data(), Wn.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) {
+    if (ctx->storage == UGKS_STORAGE_F64) {
+      launch_init_ce<double>(ctx->stream, ctx->Nc, ctx->M, ctx->nv, ctx->gas, d_fields, ctx->d_ux, ctx->d_uy,
+                             ctx->d_uz, static_cast<double*>(ctx->d_f[c]));
+      launch_moments<double>(ctx->stream, ctx->Nc, ctx->M, ctx->gas, static_cast<const double*>(ctx->d_f[c]),
+                             ctx->d_W[c], ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp, ctx->d_q[c], nullptr);
+    } else {
+      launch_init_ce<float>(ctx->stream, ctx->Nc, ctx->M, ctx->nv, ctx->gas, d_fields, ctx->d_ux, ctx->d_uy,
+                            ctx->d_uz, static_cast<float*>(ctx->d_f[c]));
+      launch_moments<float>(ctx->stream, ctx->Nc, ctx->M, ctx->gas, static_cast<const float*>(ctx->d_f[c]),
+                            ctx->d_W[c], ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp, ctx->d_q[c], nullptr);
+    }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_res, 0, NWP * sizeof(double), ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d_fields);
+  if (e != cudaSuccess) return fail(ctx, UGKS_ERR_CUDA, "ugks_init_moments13: %s", cudaGetErrorString(e));
+  ctx->step = 0;
+  return UGKS_OK;
+}
+
 ugks_status ugks_dt(const ugks_ctx* ctx, double* dt_out) {
   if (!ctx || !dt_out) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL argument");
   *dt_out = ctx->dt;

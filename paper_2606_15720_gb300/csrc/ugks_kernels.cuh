@@ -39,6 +39,13 @@ void launch_scatter_f(cudaStream_t s, int64_t Nc, int64_t M, int NR, int64_t nv,
 
 void launch_residual_finalize(cudaStream_t s, int nw, int64_t Nc, const double* acc, double* res);
 
+template <typename T>
+void launch_moments13(cudaStream_t s, int64_t Nc, int64_t M, const Gas& g, const T* f, const double* W,
+                      const double* ux, const double* uy, const double* uz, const double* w, double* out);
+template <typename T>
+void launch_init_ce(cudaStream_t s, int64_t Nc, int64_t M, int64_t nv, const Gas& g, const double* fields,
+                    const double* ux, const double* uy, const double* uz, T* f);
+
 void launch_surface(cudaStream_t s, int64_t nwall, int D, double dt, const int64_t* walls, const double* Facc,
                     int facc_stride, const double* fnormal, const int64_t* fnei, const BCDev* bcs,
                     const double* freestream, double* vals, double* coef);

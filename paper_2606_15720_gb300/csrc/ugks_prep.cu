@@ -773,6 +773,116 @@ __global__ void k_gather_f(int64_t Nc, int64_t M, int NR, int64_t nv, const T* f
   out[idx] = double(f[(size_t(r) * M + m) * Nc * BV + size_t(c) * BV + lane]);
 }
 
+// ---------------------------------------------------------------------------
+// Thirteen-moment fields of each cell: rho, U, T of W, the deviatoric stress
+// sigma_ij = sum_k w c_i c_j h - p delta_ij (p = rho/(2 lambda)) in the order
+// xx, xy, (xz), yy, (yz), zz, and the heat flux (Eq. 13), about U of W.
+// One warp per cell, FP64 sums.
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__global__ void k_moments13(int64_t Nc, int64_t M, Gas g, const T* f, const double* W, const double* ux,
+                            const double* uy, const double* uz, const double* w, double* out) {
+  constexpr int NS = D * (D + 1) / 2, N13 = 2 * D + 2 + NS;
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= Nc) return;
+  bool ok;
+  const Prim p = prim_of<D>(load5<D>(W + i * NWP), g.K, ok);
+  double P[NS], q[D];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) P[s] = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) q[d] = 0.0;
+  const size_t plane = size_t(M) * Nc * BV;
+  for (int64_t m = 0; m < M; ++m) {
+    const int64_t k = m * BV + lane;
+    const double h = double(f[size_t(m) * Nc * BV + size_t(i) * BV + lane]);
+    const double b = g.NR == 2 ? double(f[plane + size_t(m) * Nc * BV + size_t(i) * BV + lane]) : 0.0;
+    const double uu[3] = {ux[k], uy[k], uz[k]}, wk = w[k];
+    double c[3] = {0.0, 0.0, 0.0}, c2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      c[d] = uu[d] - p.U[d];
+      c2 += c[d] * c[d];
+    }
+    int s = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      q[a] += 0.5 * wk * c[a] * (c2 * h + b);
+#pragma unroll
+      for (int e = a; e < D; ++e) P[s++] += wk * c[a] * c[e] * h;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) P[s] += __shfl_xor_sync(0xffffffffu, P[s], o);
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q[d] += __shfl_xor_sync(0xffffffffu, q[d], o);
+  if (lane == 0) {
+    double* o = out + i * N13;
+    const double pr = p.rho / (2.0 * p.lam);
+    o[0] = p.rho;
+#pragma unroll
+    for (int d = 0; d < D; ++d) o[1 + d] = p.U[d];
+    o[D + 1] = 1.0 / p.lam;
+    int s = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int e = a; e < D; ++e) {
+        o[D + 2 + s] = P[s] - (a == e ? pr : 0.0);
+        ++s;
+      }
+#pragma unroll
+    for (int d = 0; d < D; ++d) o[D + 2 + NS + d] = q[d];
+  }
+}
+
+// Chapman-Enskog (Grad 13-moment) distribution of given fields, reduced over
+// xi (N = D + K_xi = K + 3 degrees of freedom):
+//   h = H [1 + 2 lam^2/rho sigma_ij c_i c_j + 4 lam^2/((N+2) rho) (q.c)(2 lam |c|^2 - (D+2))]
+//   b = kappa H [1 + 2 lam^2/rho sigma_ij c_i c_j + 4 lam^2/((N+2) rho) (q.c)(2 lam |c|^2 - D)]
+// with H the Maxwellian of (rho, U, lam = 1/T); FP64, one thread per value.
+template <int D, typename T>
+__global__ void k_init_ce(int64_t Nc, int64_t M, int64_t nv, Gas g, const double* fields, const double* ux,
+                          const double* uy, const double* uz, T* f) {
+  constexpr int NS = D * (D + 1) / 2, N13 = 2 * D + 2 + NS;
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= M * Nc * BV) return;
+  const int lane = int(idx & 31);
+  const int64_t row = idx >> 5;
+  const int64_t c = row % Nc, m = row / Nc;
+  const int64_t k = m * BV + lane;
+  double h = 0.0, b = 0.0;
+  if (k < nv) {
+    const double* x = fields + c * N13;
+    const double rho = x[0], lam = 1.0 / x[D + 1];
+    const double uu[3] = {ux[k], uy[k], uz[k]};
+    double cc[3] = {0.0, 0.0, 0.0}, c2 = 0.0, qc = 0.0, scc = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      cc[d] = uu[d] - x[1 + d];
+      c2 += cc[d] * cc[d];
+      qc += x[D + 2 + NS + d] * cc[d];
+    }
+    int s = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int e = a; e < D; ++e) scc += (a == e ? 1.0 : 2.0) * x[D + 2 + s++] * cc[a] * cc[e];
+    const double H = rho * pow(lam / M_PI, 0.5 * D) * exp(-lam * c2);
+    const double a2 = 2.0 * lam * lam / rho, a3 = 4.0 * lam * lam / ((g.K + 5.0) * rho);
+    h = H * (1.0 + a2 * scc + a3 * qc * (2.0 * lam * c2 - (D + 2)));
+    b = g.Kxi / (2.0 * lam) * H * (1.0 + a2 * scc + a3 * qc * (2.0 * lam * c2 - D));
+  }
+  const size_t plane = size_t(M) * Nc * BV;
+  f[size_t(m) * Nc * BV + size_t(c) * BV + lane] = T(h);
+  if (g.NR == 2) f[plane + size_t(m) * Nc * BV + size_t(c) * BV + lane] = T(b);
+}
+
 // Scatter of a full FP64 state in[NR][Nc_orig][nv] (original order) into f.
 template <typename T>
 __global__ void k_scatter_f(int64_t Nc, int64_t M, int NR, int64_t nv, const double* in, const int64_t* old_of_new,
@@ -853,11 +963,33 @@ void launch_scatter_f(cudaStream_t s, int64_t Nc, int64_t M, int NR, int64_t nv,
   k_scatter_f<T><<<blocks_for(int64_t(NR) * M * Nc * BV, 256), 256, 0, s>>>(Nc, M, NR, nv, in, old_of_new, f);
 }
 
+template <typename T>
+void launch_moments13(cudaStream_t s, int64_t Nc, int64_t M, const Gas& g, const T* f, const double* W,
+                      const double* ux, const double* uy, const double* uz, const double* w, double* out) {
+  const unsigned nb = blocks_for(Nc * 32, 256);
+  if (g.D == 1) k_moments13<1, T><<<nb, 256, 0, s>>>(Nc, M, g, f, W, ux, uy, uz, w, out);
+  if (g.D == 2) k_moments13<2, T><<<nb, 256, 0, s>>>(Nc, M, g, f, W, ux, uy, uz, w, out);
+  if (g.D == 3) k_moments13<3, T><<<nb, 256, 0, s>>>(Nc, M, g, f, W, ux, uy, uz, w, out);
+}
+
+template <typename T>
+void launch_init_ce(cudaStream_t s, int64_t Nc, int64_t M, int64_t nv, const Gas& g, const double* fields,
+                    const double* ux, const double* uy, const double* uz, T* f) {
+  const unsigned nb = blocks_for(M * Nc * BV, 256);
+  if (g.D == 1) k_init_ce<1, T><<<nb, 256, 0, s>>>(Nc, M, nv, g, fields, ux, uy, uz, f);
+  if (g.D == 2) k_init_ce<2, T><<<nb, 256, 0, s>>>(Nc, M, nv, g, fields, ux, uy, uz, f);
+  if (g.D == 3) k_init_ce<3, T><<<nb, 256, 0, s>>>(Nc, M, nv, g, fields, ux, uy, uz, f);
+}
+
 void launch_residual_finalize(cudaStream_t s, int nw, int64_t Nc, const double* acc, double* res) {
   k_residual_finalize<<<1, 32, 0, s>>>(nw, Nc, acc, res);
 }
 
 #define UGKS_INSTANTIATE(T)                                                                                      \
+  template void launch_moments13<T>(cudaStream_t, int64_t, int64_t, const Gas&, const T*, const double*,         \
+                                    const double*, const double*, const double*, const double*, double*);         \
+  template void launch_init_ce<T>(cudaStream_t, int64_t, int64_t, int64_t, const Gas&, const double*,             \
+                                  const double*, const double*, const double*, T*);                               \
   template void launch_init_f<T>(cudaStream_t, int64_t, int64_t, int64_t, const Gas&, const double*,             \
                                  const double*, const double*, const double*, T*);                              \
   template void launch_face<T>(cudaStream_t, int64_t, const Gas&, const double*, const double*, const double*,   \

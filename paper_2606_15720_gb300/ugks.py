@@ -86,6 +86,8 @@ def load(build_if_missing: bool = True):
         "ugks_stats": [P, I32, P, P, P, P],
         "ugks_solve": [P, P, P, P, I32, P, P],
         "ugks_surface": [P, P, I64, P, P, P, P],
+        "ugks_moments13": [P, P],
+        "ugks_init_moments13": [P, P],
         "ugks_batch_create": [I32, P, P, P, P, P, P],
         "ugks_batch_autotune": [P],
         "ugks_batch_step": [P, I32],
@@ -236,6 +238,22 @@ class Solver:
                                        _ptr(coef)))
         k = n.value
         return faces[:k], vals[:k], (coef[:k] if fs is not None else None)
+
+    @property
+    def n13(self) -> int:
+        return 2 * self.dim + 2 + self.dim * (self.dim + 1) // 2
+
+    def moments13(self) -> np.ndarray:
+        """ugks_moments13: [n_cells, n13] = rho, U, T, sigma (xx, xy, (xz), yy, (yz), zz), q."""
+        out = np.zeros((self.mesh.n_cells, self.n13))
+        self._c(self._lib.ugks_moments13(self._ctx, _ptr(out)))
+        return out
+
+    def init_moments13(self, fields: np.ndarray) -> None:
+        """ugks_init_moments13: Chapman-Enskog state of the given fields."""
+        fields = np.ascontiguousarray(fields, dtype=np.float64)
+        assert fields.shape == (self.mesh.n_cells, self.n13)
+        self._c(self._lib.ugks_init_moments13(self._ctx, _ptr(fields)))
 
     def get_f(self, cells: Sequence[int]) -> np.ndarray:
         cells = np.ascontiguousarray(cells, dtype=np.int64)

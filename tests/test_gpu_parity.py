@@ -381,3 +381,45 @@ def test_scaled_storage_checkpoint_roundtrip(U, storage):
         assert np.max(np.abs(fr - f3)) <= STORAGE_EPS[storage] * np.max(np.abs(f3))
         s2.step(4)
         assert w_err(s2.moments(), W7) <= 4 * STORAGE_EPS[storage] * 0.1
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-11), ("f32", 1e-5)])
+@pytest.mark.parametrize("name", ["cavity_shakhov", "periodic3d_bgk_K2", "cylinder_tri_K2"])
+def test_moments13_and_chapman_enskog_start_match_oracle(U, name, storage, tol):
+    """ugks_moments13 after two steps against the oracle's (reading R21), then
+    ugks_init_moments13 of those fields against the oracle's Chapman-Enskog
+    distribution and one further step."""
+    mesh, grid, gas, prim = CASES[name]()
+    W0 = I.prim_to_conservative(prim, mesh.dim, gas.K)
+    with U.Solver(mesh, grid, gas, W0, storage=storage) as s:
+        dt = s.dt
+        s.step(2)
+        m13 = s.moments13()
+        s.init_moments13(m13)
+        W1 = s.moments()
+        fce = np.transpose(s.get_f(np.arange(mesh.n_cells)), (1, 0, 2))
+        s.step(1)
+        W2 = s.moments()
+    Wo, fo, _, _ = O.run(mesh, grid, gas, W0, O.initial_f(mesh, grid, W0, gas.K), 2, dt=dt)
+    mo = O.moments13(mesh.dim, gas.K, grid, Wo, fo)
+    # rho, U, T relative to their largest magnitude; the stress P_ij - p delta_ij
+    # and the heat flux are differences of O(p) moments, so their rounding is
+    # relative to p (and p sqrt(T) for q)
+    d, p = mesh.dim, 0.5 * mo[:, 0] * mo[:, mesh.dim + 1]
+    for col in range(mo.shape[1]):
+        if col <= d + 1:
+            scale = np.max(np.abs(mo[:, col]))
+        elif col < mo.shape[1] - d:
+            scale = np.max(p)
+        else:
+            scale = np.max(p * np.sqrt(mo[:, d + 1]))
+        assert np.max(np.abs(m13[:, col] - mo[:, col])) <= tol * scale, col
+    fo_ce = O.chapman_enskog(mesh.dim, gas.K, grid, m13)
+    assert rel_linf(fce, fo_ce, axis_fields=0) <= (1e-12 if storage == "f64" else 1e-6)
+    Wc = np.zeros_like(W1)
+    Wc[:, 0] = m13[:, 0]
+    Wc[:, 1:1 + mesh.dim] = m13[:, :1][:, [0] * mesh.dim] * m13[:, 1:1 + mesh.dim]
+    Wc[:, -1] = 0.5 * m13[:, 0] * np.sum(m13[:, 1:1 + mesh.dim] ** 2, axis=1) + (gas.K + 3) * m13[:, 0] * m13[:, mesh.dim + 1] / 4
+    np.testing.assert_allclose(W1, Wc, rtol=1e-13)
+    Wo2, _, _, _ = O.run(mesh, grid, gas, Wc, fo_ce, 1, dt=dt)
+    assert w_err(W2, Wo2) <= tol, w_err(W2, Wo2)

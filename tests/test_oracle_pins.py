@@ -621,3 +621,56 @@ def test_surface_quantities_of_a_gas_at_rest_in_equilibrium_with_the_wall():
     np.testing.assert_allclose(vals[:, 0], 0.5 * rho * T, rtol=2e-3)
     assert np.max(np.abs(vals[:, 1:3])) <= 1e-12
     assert np.max(np.abs(vals[:, 3])) <= 2e-3 * rho * T ** 1.5
+
+
+def _fields13(rng, dim, n):
+    """Random thirteen-moment fields with moderate stress and heat flux."""
+    ns = dim * (dim + 1) // 2
+    out = np.zeros((n, O.n13(dim)))
+    out[:, 0] = rng.uniform(0.7, 1.3, n)
+    out[:, 1:1 + dim] = rng.uniform(-0.4, 0.4, (n, dim))
+    out[:, dim + 1] = rng.uniform(0.8, 1.3, n)
+    sig = rng.uniform(-0.03, 0.03, (n, ns))
+    # traceless stress: remove the mean of the diagonal entries
+    diag = [s for s, (a, e) in enumerate((a, e) for a in range(dim) for e in range(a, dim)) if a == e]
+    sig[:, diag] -= sig[:, diag].mean(axis=1, keepdims=True)
+    out[:, dim + 2:dim + 2 + ns] = sig
+    out[:, dim + 2 + ns:] = rng.uniform(-0.03, 0.03, (n, dim))
+    return out
+
+
+@pytest.mark.parametrize("dim,K", [(2, 0), (3, 0), (2, 2)])
+def test_chapman_enskog_moments_reproduce_the_fields(dim, K):
+    """Reading R21: the discrete moments of the Chapman-Enskog distribution of
+    (rho, U, T, sigma, q) give back rho, rho U, E (Eq. 10), sigma and q on a fine
+    velocity grid (Gaussian moments: quadrature error below 1e-9)."""
+    rng = np.random.default_rng(7)
+    fields = _fields13(rng, dim, 5)
+    grid = I.midpoint_grid(56 if dim == 2 else 40, -9.0, 9.0, dim)
+    f = O.chapman_enskog(dim, K, grid, fields)
+    rho, U, T = fields[:, 0], fields[:, 1:1 + dim], fields[:, dim + 1]
+    W = np.zeros((len(fields), dim + 2))
+    W[:, 0] = rho
+    W[:, 1:1 + dim] = rho[:, None] * U
+    W[:, dim + 1] = 0.5 * rho * np.sum(U * U, axis=1) + (K + 3) * rho * T / 4.0
+    u, w = grid.u, grid.weight
+    h = f[0]
+    b = f[1] if f.shape[0] == 2 else 0.0 * h
+    Wf = np.stack([h @ w] + [(h * u[:, d]) @ w for d in range(dim)] +
+                  [0.5 * ((np.sum(u * u, axis=1) * h + b) @ w)], axis=1)
+    np.testing.assert_allclose(Wf, W, rtol=1e-9, atol=1e-10)
+    back = O.moments13(dim, K, grid, W, f)
+    np.testing.assert_allclose(back, fields, rtol=1e-8, atol=1e-10)
+
+
+def test_moments13_of_a_maxwellian_have_no_stress_and_no_heat_flux():
+    dim, K = 3, 0
+    grid = I.midpoint_grid(40, -9.0, 9.0, dim)
+    mesh = I.periodic_box((2, 2, 1))
+    prim = I.smooth_random_primitives(mesh, seed=3, amp=0.2, U0=(0.3, -0.2, 0.1))
+    W = I.prim_to_conservative(prim, dim, K)
+    f = O.initial_f(mesh, grid, W, K)
+    m = O.moments13(dim, K, grid, W, f)
+    ns = 6
+    assert np.max(np.abs(m[:, dim + 2:])) <= 1e-10
+    np.testing.assert_allclose(m[:, 0], W[:, 0], rtol=1e-14)
