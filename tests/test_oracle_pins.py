@@ -674,3 +674,39 @@ def test_moments13_of_a_maxwellian_have_no_stress_and_no_heat_flux():
     ns = 6
     assert np.max(np.abs(m[:, dim + 2:])) <= 1e-10
     np.testing.assert_allclose(m[:, 0], W[:, 0], rtol=1e-14)
+
+
+def test_mlp_reference_gradient_matches_central_differences():
+    """The hand-derived back-propagation of oracle/mlp_oracle.py against central
+    finite differences of the loss (FP64, step 1e-6: agreement to 1e-7)."""
+    from oracle import mlp_oracle as M
+    sizes = [6, 12, 12, 9]
+    params = M.init_params(sizes, seed=3)
+    params = [(W, b + 0.1 * np.random.default_rng(l).normal(size=b.shape)) for l, (W, b) in enumerate(params)]
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(7, 6))
+    t = rng.normal(size=(7, 9))
+    g = M.flatten([(gW, gb) for gW, gb in M.gradients(params, x, t)])
+    p0 = M.flatten(params)
+    num = np.zeros_like(p0)
+    h = 1e-6
+    for i in range(p0.size):
+        e = np.zeros_like(p0)
+        e[i] = h
+        num[i] = (M.loss(M.unflatten(p0 + e, sizes), x, t) - M.loss(M.unflatten(p0 - e, sizes), x, t)) / (2 * h)
+    assert np.max(np.abs(g - num)) <= 1e-7 * max(1.0, np.max(np.abs(num)))
+
+
+def test_mlp_reference_adam_step_on_a_quadratic():
+    """One Adam step moves each parameter by lr in the direction of -sign(gradient)
+    (bias-corrected first step: m/c1 = g, sqrt(v/c2) = |g|)."""
+    from oracle import mlp_oracle as M
+    params = M.init_params([3, 4, 2], seed=1)
+    rng = np.random.default_rng(2)
+    x, t = rng.normal(size=(5, 3)), rng.normal(size=(5, 2))
+    grads = M.gradients(params, x, t)
+    new, state = M.adam_step(params, grads, None, lr=1e-3)
+    for (W, b), (W2, b2), (gW, gb) in zip(params, new, grads):
+        np.testing.assert_allclose(W2 - W, -1e-3 * gW / (np.abs(gW) + 1e-8), rtol=1e-6, atol=1e-12)
+        np.testing.assert_allclose(b2 - b, -1e-3 * gb / (np.abs(gb) + 1e-8), rtol=1e-6, atol=1e-12)
+    assert state[0] == 1
