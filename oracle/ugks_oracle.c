@@ -40,10 +40,18 @@
  *      deviatoric stress sigma_ij = sum_k w c_i c_j h - p delta_ij (p = rho /
  *      (2 lambda)) and q (Eq. 13), c = u - U of W; their Chapman-Enskog
  *      (Grad 13-moment) distribution, reduced over xi:
- *        h = H [1 + 2 lam^2/rho sigma_ij c_i c_j + 4 lam^2/((K+5) rho) (q.c)(2 lam c^2 - (D+2))]
- *        b = kappa H [1 + 2 lam^2/rho sigma_ij c_i c_j + 4 lam^2/((K+5) rho) (q.c)(2 lam c^2 - D)]
+ *        h = H [1 + 2 lam^2/rho sigma_ij c_i c_j - lam tr(sigma)/rho
+ *               + 4 lam^2/((K+5) rho) (q.c)(2 lam c^2 - (D+2))]
+ *        b = kappa H [1 + 2 lam^2/rho sigma_ij c_i c_j - lam (K_xi+2) tr(sigma)/(K_xi rho)
+ *               + 4 lam^2/((K+5) rho) (q.c)(2 lam c^2 - D)]
  *      (K + 5 = N + 2 for N = D + K_xi degrees of freedom; at K = 0 the
- *      heat-flux term has the form of the Shakhov term of Eq. 18-19).
+ *      heat-flux term has the form of the Shakhov term of Eq. 18-19).  The
+ *      trace terms: the full stress over all D + K_xi degrees of freedom is
+ *      trace-free, so the K_xi components of xi share -tr(sigma) equally
+ *      (for D = 2, K = 0 this is sigma_zz = -(sigma_xx + sigma_yy)); reducing
+ *      that xi-stress term over xi gives the two constants, with which the
+ *      moments of (h, b) return rho, E and sigma for any in-plane trace.
+ *      At K_xi = 0 sigma must be trace-free.
  * Parity: every function below is pinned by tests/test_oracle_pins.py.
  */
 #include <math.h>
@@ -605,6 +613,11 @@ void orc_chapman_enskog(int D, int K, int64_t nc, int64_t nv, const double *u, c
     p.lam = 1.0 / x[D + 1];
     const double *sig = x + D + 2, *q = x + D + 2 + ns;
     const double a2 = 2.0 * p.lam * p.lam / p.rho, a3 = 4.0 * p.lam * p.lam / ((K + 5.0) * p.rho);
+    double tr = 0.0;
+    for (int a = 0, s = 0; a < D; ++a)
+      for (int e = a; e < D; ++e, ++s)
+        if (a == e) tr += sig[s];
+    const double th = -p.lam * tr / p.rho, tb = Kxi > 0 ? -p.lam * (Kxi + 2.0) * tr / (Kxi * p.rho) : 0.0;
     for (int64_t k = 0; k < nv; ++k) {
       double c[MAXD], c2 = 0.0, qc = 0.0, scc = 0.0;
       for (int d = 0; d < D; ++d) {
@@ -616,9 +629,9 @@ void orc_chapman_enskog(int D, int K, int64_t nc, int64_t nv, const double *u, c
       for (int a = 0; a < D; ++a)
         for (int e = a; e < D; ++e) scc += (a == e ? 1.0 : 2.0) * sig[s++] * c[a] * c[e];
       const double H = maxwell_H(D, &p, u + k * D);
-      f[i * nv + k] = H * (1.0 + a2 * scc + a3 * qc * (2.0 * p.lam * c2 - (D + 2)));
+      f[i * nv + k] = H * (1.0 + a2 * scc + th + a3 * qc * (2.0 * p.lam * c2 - (D + 2)));
       if (nr == 2)
-        f[(nc + i) * nv + k] = Kxi / (2.0 * p.lam) * H * (1.0 + a2 * scc + a3 * qc * (2.0 * p.lam * c2 - D));
+        f[(nc + i) * nv + k] = Kxi / (2.0 * p.lam) * H * (1.0 + a2 * scc + tb + a3 * qc * (2.0 * p.lam * c2 - D));
     }
   }
 }

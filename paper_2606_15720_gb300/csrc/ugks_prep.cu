@@ -874,9 +874,19 @@ __global__ void k_init_ce(int64_t Nc, int64_t M, int64_t nv, Gas g, const double
 #pragma unroll
       for (int e = a; e < D; ++e) scc += (a == e ? 1.0 : 2.0) * x[D + 2 + s++] * cc[a] * cc[e];
     const double H = rho * pow(lam / M_PI, 0.5 * D) * exp(-lam * c2);
+    // the K_xi components of xi carry -tr(sigma) / K_xi each (trace-free
+    // stress over all degrees of freedom); reduced over xi that gives the
+    // constants th (in h) and tb (in b)
+    double tr = 0.0;
+#pragma unroll
+    for (int a = 0, s2 = 0; a < D; ++a)
+#pragma unroll
+      for (int e = a; e < D; ++e, ++s2)
+        if (a == e) tr += x[D + 2 + s2];
     const double a2 = 2.0 * lam * lam / rho, a3 = 4.0 * lam * lam / ((g.K + 5.0) * rho);
-    h = H * (1.0 + a2 * scc + a3 * qc * (2.0 * lam * c2 - (D + 2)));
-    b = g.Kxi / (2.0 * lam) * H * (1.0 + a2 * scc + a3 * qc * (2.0 * lam * c2 - D));
+    const double th = -lam * tr / rho, tb = g.Kxi > 0 ? -lam * (g.Kxi + 2.0) * tr / (g.Kxi * rho) : 0.0;
+    h = H * (1.0 + a2 * scc + th + a3 * qc * (2.0 * lam * c2 - (D + 2)));
+    b = g.Kxi / (2.0 * lam) * H * (1.0 + a2 * scc + tb + a3 * qc * (2.0 * lam * c2 - D));
   }
   const size_t plane = size_t(M) * Nc * BV;
   f[size_t(m) * Nc * BV + size_t(c) * BV + lane] = T(h);

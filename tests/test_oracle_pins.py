@@ -623,8 +623,9 @@ def test_surface_quantities_of_a_gas_at_rest_in_equilibrium_with_the_wall():
     assert np.max(np.abs(vals[:, 3])) <= 2e-3 * rho * T ** 1.5
 
 
-def _fields13(rng, dim, n):
-    """Random thirteen-moment fields with moderate stress and heat flux."""
+def _fields13(rng, dim, n, traceless=True):
+    """Random thirteen-moment fields with moderate stress and heat flux (an
+    in-plane stress with a trace unless traceless)."""
     ns = dim * (dim + 1) // 2
     out = np.zeros((n, O.n13(dim)))
     out[:, 0] = rng.uniform(0.7, 1.3, n)
@@ -633,20 +634,23 @@ def _fields13(rng, dim, n):
     sig = rng.uniform(-0.03, 0.03, (n, ns))
     # traceless stress: remove the mean of the diagonal entries
     diag = [s for s, (a, e) in enumerate((a, e) for a in range(dim) for e in range(a, dim)) if a == e]
-    sig[:, diag] -= sig[:, diag].mean(axis=1, keepdims=True)
+    if traceless:
+        sig[:, diag] -= sig[:, diag].mean(axis=1, keepdims=True)
     out[:, dim + 2:dim + 2 + ns] = sig
     out[:, dim + 2 + ns:] = rng.uniform(-0.03, 0.03, (n, dim))
     return out
 
 
-@pytest.mark.parametrize("dim,K", [(2, 0), (3, 0), (2, 2)])
-def test_chapman_enskog_moments_reproduce_the_fields(dim, K):
+@pytest.mark.parametrize("dim,K,traceless", [(2, 0, True), (3, 0, True), (2, 2, True), (2, 0, False),
+                                             (1, 0, False), (3, 2, False)])
+def test_chapman_enskog_moments_reproduce_the_fields(dim, K, traceless):
     """Reading R21: the discrete moments of the Chapman-Enskog distribution of
     (rho, U, T, sigma, q) give back rho, rho U, E (Eq. 10), sigma and q on a fine
-    velocity grid (Gaussian moments: quadrature error below 1e-9)."""
+    velocity grid (Gaussian moments: quadrature error below 1e-9), also for an
+    in-plane stress with a trace where K_xi > 0 (the xi components absorb it)."""
     rng = np.random.default_rng(7)
-    fields = _fields13(rng, dim, 5)
-    grid = I.midpoint_grid(56 if dim == 2 else 40, -9.0, 9.0, dim)
+    fields = _fields13(rng, dim, 5, traceless)
+    grid = I.midpoint_grid({1: 200, 2: 56, 3: 40}[dim], -9.0, 9.0, dim)
     f = O.chapman_enskog(dim, K, grid, fields)
     rho, U, T = fields[:, 0], fields[:, 1:1 + dim], fields[:, dim + 1]
     W = np.zeros((len(fields), dim + 2))
