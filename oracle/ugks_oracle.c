@@ -20,7 +20,14 @@
  *   R2 gradient: unweighted least squares over face neighbours, M^-1 sum d df.
  *   R3 stencil: far-field / outflow ghosts included (ghost centroid mirrored
  *      across the face, ghost distribution = Maxwellian of the ghost state);
- *      walls excluded from the least squares but included in the limiter.
+ *      a wall contributes a mirrored ghost that carries the cell's own value
+ *      (zero gradient): its offset enters the least-squares matrix, nothing
+ *      enters the right-hand side or the limiter's max/min; the wall face is
+ *      one of the faces the limiter checks.  (With walls left out of the
+ *      matrix, wall cells with two interior neighbours extrapolate: some
+ *      outflow face values then weigh the cell's own value negatively, the
+ *      transport of that velocity amplifies instead of damping, and the
+ *      limiter alone bounds it, so steady states depended on the start.)
  *   R4 time step: dt = CFL min_i |Omega_i| / max_k sum_f S_f max(u_k.n_f, 0).
  *   R5 tau = mu/p with mu = mu_ref T^omega.
  *   R6 W0 = half-range moments of the two reconstructed Maxwellians.
@@ -756,7 +763,13 @@ int orc_step(const orc_mesh *m, int64_t nv, const double *u, const double *w, co
       int64_t j = face_view(m, fidx, i, nout, xfc, xo);
       if (j < 0) {
         const orc_bc *bc = &m->bc[-j - 1];
-        if (bc->type == 1) continue;
+        if (bc->type == 1) {
+          /* wall: zero-gradient ghost, offset in the matrix only (reading R3) */
+          for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b)
+              Mm[a * D + b] += (xo[a] - m->xc[i * D + a]) * (xo[b] - m->xc[i * D + b]);
+          continue;
+        }
         ghost_W(D, K, bc, Wi, Wo);
       } else {
         for (int t = 0; t < nw; ++t) Wo[t] = W[j * nw + t];
@@ -868,7 +881,12 @@ int orc_step(const orc_mesh *m, int64_t nv, const double *u, const double *w, co
       for (int64_t s = adj.off[i]; s < adj.off[i + 1]; ++s) {
         double nout[MAXD], xfc[MAXD], xo[MAXD];
         int64_t j = face_view(m, adj.face[s], i, nout, xfc, xo);
-        if (j < 0 && m->bc[-j - 1].type == 1) continue;
+        if (j < 0 && m->bc[-j - 1].type == 1) {
+          /* wall: zero-gradient ghost, offset in the matrix only (reading R3) */
+          for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b) Mm[a * D + b] += (xo[a] - xi[a]) * (xo[b] - xi[b]);
+          continue;
+        }
         sidx[nst] = s;
         for (int d = 0; d < D; ++d) dxs[nst][d] = xo[d] - xi[d];
         for (int a = 0; a < D; ++a)

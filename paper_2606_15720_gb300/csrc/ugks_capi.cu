@@ -849,7 +849,11 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
       CellFace& s = cf[e];
       double* d_ = dx[e - cf_off[i]];
       for (int d = 0; d < 3; ++d) d_[d] = 0.0;
-      if (s.bc_type == UGKS_BC_WALL) continue;
+      // A wall is a mirrored ghost holding the cell's own value (zero
+      // gradient): its offset enters M, its weight stays 0 (nothing enters the
+      // right-hand side).  Left out of M, wall cells with two interior
+      // neighbours extrapolate and some outflow face values weigh the cell's
+      // own value negatively (transport then amplifies that velocity).
       const double* n = &fnormal[s.face * 3];
       if (s.other >= 0) {
         double sh = s.sign > 0 ? 1.0 : -1.0;
@@ -1345,6 +1349,14 @@ ugks_status ugks_sizes(const ugks_ctx* ctx, int32_t* n_reduced, int64_t* n_v_pad
   if (!ctx) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL context");
   if (n_reduced) *n_reduced = ctx->NR;
   if (n_v_padded) *n_v_padded = ctx->M * BV;
+  return UGKS_OK;
+}
+
+ugks_status ugks_mesh_sizes(const ugks_ctx* ctx, int32_t* dim, int64_t* n_cells, int64_t* n_faces) {
+  if (!ctx) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "NULL context");
+  if (dim) *dim = ctx->D;
+  if (n_cells) *n_cells = ctx->Nc;
+  if (n_faces) *n_faces = ctx->Nf;
   return UGKS_OK;
 }
 
