@@ -543,6 +543,31 @@ def time_batch(args, cases, workload):
         "setup_seconds": {"create": create_s}, "finite": finite, "steps": steps}
 
 
+WARM_TRAIN = [(ma, kn) for ma in (1.5, 2.0, 2.5, 3.0) for kn in (0.05, 0.15, 0.5)]
+WARM_HELD_OUT = [(1.75, 0.09), (2.25, 0.3), (2.75, 0.12), (2.1, 0.7)]
+
+
+def run_warm_report(args):
+    """Learned warm start: 12 converged cylinder cases (Ma 1.5-3, Kn 0.05-0.5,
+    about 2000 triangles, 28^2 velocities, Shakhov) train the 6x256 network;
+    4 held-out cases (new meshes, Ma and Kn between the training values) are
+    solved to residual 1e-6 from the freestream and from the warm start, and
+    both results are compared with the freestream solve continued to 1e-8."""
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CUDA library has no CPU path)")
+    from paper_2606_15720_gb300 import warmstart as WS
+    res = WS.experiment(WARM_TRAIN, WARM_HELD_OUT, cells=2000, nvx=28, ref_tol=1e-8,
+                        log=lambda m: print(m, file=sys.stderr, flush=True))
+    ratios = [c["time_ratio"] for c in res["cases"] if "time_ratio" in c]
+    res["workload"] = "cylinder_warmstart_ma1.5-3_kn0.05-0.5_tri2k_v28sq_shakhov_fp32"
+    res["metric"] = "time_to_residual_1e-6_speedup"
+    res["value"] = float(np.exp(np.mean(np.log(ratios)))) if ratios else None
+    res["unit"] = "x (geometric mean over held-out cases, freestream seconds / warm-start seconds)"
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -557,9 +582,10 @@ def main():
     ap.add_argument("--block-velocities", type=int, default=0, choices=[0, 32, 64, 128])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="storage of f (FP16 / BF16: deviations from a per-cell reference Maxwellian)")
-    ap.add_argument("--report", default=None, choices=["mixed", "batch"],
+    ap.add_argument("--report", default=None, choices=["mixed", "batch", "warmstart"],
                     help="mixed: per-field error of FP32/FP16/BF16 storage vs the oracle at 1e2 and 1e3 steps; "
-                         "batch: 64 uneven cylinder cases in one CUDA graph with the block-size autotuner")
+                         "batch: 64 uneven cylinder cases in one CUDA graph with the block-size autotuner; "
+                         "warmstart: time to steady residual 1e-6 from the learned warm start vs the freestream")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -569,6 +595,8 @@ def main():
         return run_mixed_report(args)
     if args.report == "batch":
         return run_batch_report(args)
+    if args.report == "warmstart":
+        return run_warm_report(args)
     return run_gpu(args)
 
 

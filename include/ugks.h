@@ -208,9 +208,14 @@ ugks_status ugks_moments13(ugks_ctx *ctx, double *out);
 
 /* Resets the state to the Chapman-Enskog (Grad 13-moment) distribution of
  * the given fields (layout of ugks_moments13; rho, T > 0), reduced over xi:
- *   h = H [1 + 2 lam^2/rho sigma_ij c_i c_j + 4 lam^2/((K+5) rho) (q.c)(2 lam |c|^2 - (dim+2))]
- *   b = kappa H [1 + 2 lam^2/rho sigma_ij c_i c_j + 4 lam^2/((K+5) rho) (q.c)(2 lam |c|^2 - dim)]
- * (H the Maxwellian of rho, U, lam = 1/T; kappa = K_xi/(2 lam)), W from
+ *   h = H [1 + 2 lam^2/rho sigma_ij c_i c_j - lam tr(sigma)/rho
+ *          + 4 lam^2/((K+5) rho) (q.c)(2 lam |c|^2 - (dim+2))]
+ *   b = kappa H [1 + 2 lam^2/rho sigma_ij c_i c_j - lam (K_xi+2) tr(sigma)/(K_xi rho)
+ *          + 4 lam^2/((K+5) rho) (q.c)(2 lam |c|^2 - dim)]
+ * (H the Maxwellian of rho, U, lam = 1/T; kappa = K_xi/(2 lam); the trace
+ * terms give the K_xi components of xi the stress -tr(sigma)/K_xi each, so
+ * that the full stress is trace-free and the moments of f return rho, E and
+ * sigma; with K_xi = 0, sigma must be trace-free), W from
  * rho, U, T; the step counter restarts at 0.  A warm start for steady
  * solves; the paper has no such call.  FP64 or FP32 storage. */
 ugks_status ugks_init_moments13(ugks_ctx *ctx, const double *fields);
@@ -220,6 +225,9 @@ ugks_status ugks_dt(const ugks_ctx *ctx, double *dt_out);
 
 /* Number of reduced distributions (2 when K_xi > 0, else 1) and padded grid size. */
 ugks_status ugks_sizes(const ugks_ctx *ctx, int32_t *n_reduced, int64_t *n_v_padded);
+
+/* Spatial dimension, number of cells and of faces of the context's mesh. */
+ugks_status ugks_mesh_sizes(const ugks_ctx *ctx, int32_t *dim, int64_t *n_cells, int64_t *n_faces);
 
 /* Copies the distribution of selected cells (original indices) as FP64:
  * out[n][n_reduced][n_v] (h then b). */
@@ -280,6 +288,83 @@ ugks_status ugks_batch_context(ugks_batch *batch, int32_t i, ugks_ctx **ctx);
 ugks_status ugks_batch_tuning(ugks_batch *batch, int32_t i, int32_t *block_velocities, double *ms_per_step);
 
 ugks_status ugks_batch_destroy(ugks_batch *batch);
+
+/* ---- Learned warm start ----
+ * The paper has no learned component; its conclusion lists steady-state
+ * acceleration as future work.  This interface addition starts steady solves
+ * from a learned prediction of the converged fields instead of the
+ * freestream.  The predictor is a multilayer perceptron
+ *   y = W_L tanh(... tanh(W_1 x + b_1) ...) + b_L
+ * (hidden_layers tanh layers of `width` units, linear output) whose input is
+ * the per-cell feature vector of ugks_mlp_features and whose output is the
+ * thirteen-moment fields of ugks_moments13 (n_out = 2 dim + 2 + dim (dim+1)/2).
+ * Inputs and outputs are normalised x' = (x - shift) / scale with the
+ * network's scaling (ugks_mlp_set_scaling / ugks_mlp_fit_scaling).  Weights
+ * and activations are BF16 with FP32 accumulation on the tensor cores;
+ * master weights, biases, gradients and Adam moments are FP32.  Training
+ * minimises the mean-squared error over samples and outputs (normalised) by
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).  All calls are
+ * synchronous on the network's stream and take host arrays, row-major. */
+typedef struct ugks_mlp ugks_mlp;
+
+/* Glorot-uniform weights drawn from splitmix64(seed), zero biases, unit
+ * scaling.  1 <= n_in, n_out, width <= 4096, hidden_layers >= 1. */
+ugks_status ugks_mlp_create(int32_t n_in, int32_t n_out, int32_t width, int32_t hidden_layers, uint64_t seed,
+                            void *cuda_stream, ugks_mlp **out);
+
+/* Scaling of inputs ([n_in] shift and scale) and outputs ([n_out]); scales > 0. */
+ugks_status ugks_mlp_set_scaling(ugks_mlp *net, const float *in_shift, const float *in_scale,
+                                 const float *out_shift, const float *out_scale);
+ugks_status ugks_mlp_get_scaling(const ugks_mlp *net, float *in_shift, float *in_scale, float *out_shift,
+                                 float *out_scale);
+
+/* Sets the scaling to the mean and standard deviation (floored at 1e-6 times
+ * the largest magnitude, else 1) of each column of X[n][n_in] and Y[n][n_out]. */
+ugks_status ugks_mlp_fit_scaling(ugks_mlp *net, const float *X, const float *Y, int64_t n);
+
+/* Number of parameters; get / set them as FP32, layer by layer W_l
+ * ([out][in], row-major) then b_l.  Setting resets the Adam state. */
+ugks_status ugks_mlp_param_count(const ugks_mlp *net, int64_t *count);
+ugks_status ugks_mlp_get_params(ugks_mlp *net, float *params);
+ugks_status ugks_mlp_set_params(ugks_mlp *net, const float *params);
+
+/* Gradient of the loss on n <= 4096 samples (X[n][n_in], Y[n][n_out],
+ * unnormalised) with respect to the parameters (layout of get_params), and
+ * the loss itself (normalised units) if loss is not NULL. */
+ugks_status ugks_mlp_gradients(ugks_mlp *net, const float *X, const float *Y, int64_t n, float *grads,
+                               double *loss);
+
+/* `epochs` passes of Adam with learning rate lr over X, Y in mini-batches of
+ * `batch` <= 4096 samples, shuffled each epoch by splitmix64(seed); *loss_out
+ * receives the mean batch loss of the last epoch.  UGKS_ERR_NONFINITE if the
+ * loss stops being finite. */
+ugks_status ugks_mlp_train(ugks_mlp *net, const float *X, const float *Y, int64_t n, int32_t epochs,
+                           int32_t batch, float lr, uint64_t seed, double *loss_out);
+
+/* Y[n][n_out] (unnormalised) of X[n][n_in]. */
+ugks_status ugks_mlp_predict(ugks_mlp *net, const float *X, int64_t n, float *Y);
+
+/* Feature vectors of a mesh's cells, out[n_cells][6] =
+ *   (mach, log10 kn, centroid x, y, z (0 beyond dim), wall distance),
+ * the wall distance being the distance from the cell centroid to the nearest
+ * centroid of a face with a WALL boundary condition (0 without walls),
+ * computed on the device. */
+ugks_status ugks_mlp_features(ugks_mlp *net, const ugks_mesh *mesh, double mach, double kn, float *out);
+
+/* Warm start of a context: predicts the thirteen-moment fields of
+ * every cell from its features and resets the context to their
+ * Chapman-Enskog distribution (ugks_init_moments13).  Freestream fallback:
+ * a cell whose prediction is not finite or has rho <= 0 or T <= 0 gets the
+ * fields of freestream = (rho, U[dim], T) with zero stress and heat flux;
+ * *n_fallback (if not NULL) receives their number.  mesh must be the mesh the
+ * context was created from; net must have n_in = 6 and the n_out of its dim. */
+ugks_status ugks_mlp_warm_start(ugks_mlp *net, ugks_ctx *ctx, const ugks_mesh *mesh, double mach, double kn,
+                                const double *freestream, int64_t *n_fallback);
+
+ugks_status ugks_mlp_destroy(ugks_mlp *net);
+
+/* Message of the last error of net, or of the calling thread when net is NULL. */
+const char *ugks_mlp_last_error(const ugks_mlp *net);
 
 /* Message of the last error of ctx, or of the calling thread when ctx is NULL. */
 const char *ugks_last_error(const ugks_ctx *ctx);

@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libugks.so")
-SOURCES = ["ugks_blocked_f32.cu", "ugks_blocked_f64.cu", "ugks_blocked_f16.cu", "ugks_blocked_bf16.cu", "ugks_store_util.cu", "ugks_sweep.cu", "ugks_prep.cu", "ugks_capi.cu"]
+SOURCES = ["ugks_blocked_f32.cu", "ugks_blocked_f64.cu", "ugks_blocked_f16.cu", "ugks_blocked_bf16.cu", "ugks_store_util.cu",
+           "ugks_sweep.cu", "ugks_prep.cu", "ugks_capi.cu", "ugks_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -95,6 +95,20 @@ def load(build_if_missing: bool = True):
         "ugks_batch_tuning": [P, I32, P, P],
         "ugks_batch_destroy": [P],
         "ugks_destroy": [P],
+        "ugks_mesh_sizes": [P, P, P, P],
+        "ugks_mlp_create": [I32, I32, I32, I32, ctypes.c_uint64, P, P],
+        "ugks_mlp_set_scaling": [P, P, P, P, P],
+        "ugks_mlp_get_scaling": [P, P, P, P, P],
+        "ugks_mlp_fit_scaling": [P, P, P, I64],
+        "ugks_mlp_param_count": [P, P],
+        "ugks_mlp_get_params": [P, P],
+        "ugks_mlp_set_params": [P, P],
+        "ugks_mlp_gradients": [P, P, P, I64, P, P],
+        "ugks_mlp_train": [P, P, P, I64, I32, I32, ctypes.c_float, ctypes.c_uint64, P],
+        "ugks_mlp_predict": [P, P, I64, P],
+        "ugks_mlp_features": [P, P, ctypes.c_double, ctypes.c_double, P],
+        "ugks_mlp_warm_start": [P, P, P, ctypes.c_double, ctypes.c_double, P, P],
+        "ugks_mlp_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -102,6 +116,8 @@ def load(build_if_missing: bool = True):
         fn.restype = ctypes.c_int
     lib.ugks_last_error.argtypes = [P]
     lib.ugks_last_error.restype = ctypes.c_char_p
+    lib.ugks_mlp_last_error.argtypes = [P]
+    lib.ugks_mlp_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -130,9 +146,10 @@ class _MeshArgs:
         a = self.arrays
         self.mesh = ugks_mesh(mesh.dim, mesh.n_cells, mesh.n_faces, *[_ptr(x) for x in a], len(mesh.bc),
                               ctypes.addressof(self.bcs))
-        self.u = f64(grid.u)
-        self.w = f64(grid.weight)
-        self.grid = ugks_vgrid(grid.n_v, _ptr(self.u), _ptr(self.w))
+        if grid is not None:
+            self.u = f64(grid.u)
+            self.w = f64(grid.weight)
+            self.grid = ugks_vgrid(grid.n_v, _ptr(self.u), _ptr(self.w))
 
 
 def make_params(gas: Gas, storage: str = "f32", tile_cells: int = 0, sweep: str = "auto",
@@ -366,6 +383,117 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class WarmStartNet:
+    """ugks_mlp_*: the warm-start network (BF16 weights and activations, FP32
+    accumulation, master weights and Adam state), trained and evaluated by the
+    library's kernels.  Arrays are host numpy arrays (converted to FP32)."""
+
+    N_FEATURES = 6
+
+    def __init__(self, n_in: int, n_out: int, width: int = 256, hidden_layers: int = 6, seed: int = 0,
+                 stream: Optional[int] = None):
+        self._lib = load()
+        self.n_in, self.n_out, self.width, self.hidden_layers = int(n_in), int(n_out), int(width), int(hidden_layers)
+        self.sizes = [self.n_in] + [self.width] * self.hidden_layers + [self.n_out]
+        net = ctypes.c_void_p()
+        st = self._lib.ugks_mlp_create(self.n_in, self.n_out, self.width, self.hidden_layers,
+                                       ctypes.c_uint64(int(seed)), stream, ctypes.byref(net))
+        if st != 0:
+            raise UGKSError(st, self._lib.ugks_mlp_last_error(None).decode(errors="replace"))
+        self._net = net
+
+    def _c(self, st):
+        if st != 0:
+            raise UGKSError(st, self._lib.ugks_mlp_last_error(self._net).decode(errors="replace"))
+
+    @staticmethod
+    def _f32(a, cols):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        if a.ndim != 2 or a.shape[1] != cols:
+            raise ValueError(f"expected an array of shape (n, {cols}), got {a.shape}")
+        return a
+
+    def param_count(self) -> int:
+        n = ctypes.c_int64()
+        self._c(self._lib.ugks_mlp_param_count(self._net, ctypes.byref(n)))
+        return n.value
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.param_count(), dtype=np.float32)
+        self._c(self._lib.ugks_mlp_get_params(self._net, _ptr(out)))
+        return out
+
+    def set_params(self, params: np.ndarray) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.param_count():
+            raise ValueError("wrong number of parameters")
+        self._c(self._lib.ugks_mlp_set_params(self._net, _ptr(p)))
+
+    def set_scaling(self, in_shift, in_scale, out_shift, out_scale) -> None:
+        a = [np.ascontiguousarray(x, dtype=np.float32) for x in (in_shift, in_scale, out_shift, out_scale)]
+        if a[0].size != self.n_in or a[1].size != self.n_in or a[2].size != self.n_out or a[3].size != self.n_out:
+            raise ValueError("scaling arrays have the wrong sizes")
+        self._c(self._lib.ugks_mlp_set_scaling(self._net, *[_ptr(x) for x in a]))
+
+    def get_scaling(self):
+        a = [np.zeros(k, dtype=np.float32) for k in (self.n_in, self.n_in, self.n_out, self.n_out)]
+        self._c(self._lib.ugks_mlp_get_scaling(self._net, *[_ptr(x) for x in a]))
+        return tuple(a)
+
+    def fit_scaling(self, X, Y) -> None:
+        X, Y = self._f32(X, self.n_in), self._f32(Y, self.n_out)
+        self._c(self._lib.ugks_mlp_fit_scaling(self._net, _ptr(X), _ptr(Y), X.shape[0]))
+
+    def gradients(self, X, Y):
+        X, Y = self._f32(X, self.n_in), self._f32(Y, self.n_out)
+        g = np.zeros(self.param_count(), dtype=np.float32)
+        loss = ctypes.c_double()
+        self._c(self._lib.ugks_mlp_gradients(self._net, _ptr(X), _ptr(Y), X.shape[0], _ptr(g), ctypes.byref(loss)))
+        return g, loss.value
+
+    def train(self, X, Y, epochs: int, batch: int = 1024, lr: float = 1e-3, seed: int = 0) -> float:
+        X, Y = self._f32(X, self.n_in), self._f32(Y, self.n_out)
+        loss = ctypes.c_double()
+        self._c(self._lib.ugks_mlp_train(self._net, _ptr(X), _ptr(Y), X.shape[0], int(epochs), int(batch),
+                                         ctypes.c_float(lr), ctypes.c_uint64(int(seed)), ctypes.byref(loss)))
+        return loss.value
+
+    def predict(self, X) -> np.ndarray:
+        X = self._f32(X, self.n_in)
+        Y = np.zeros((X.shape[0], self.n_out), dtype=np.float32)
+        self._c(self._lib.ugks_mlp_predict(self._net, _ptr(X), X.shape[0], _ptr(Y)))
+        return Y
+
+    def features(self, mesh: Mesh, mach: float, kn: float) -> np.ndarray:
+        args = _MeshArgs(mesh, None)
+        out = np.zeros((mesh.n_cells, self.N_FEATURES), dtype=np.float32)
+        self._c(self._lib.ugks_mlp_features(self._net, ctypes.byref(args.mesh), float(mach), float(kn), _ptr(out)))
+        return out
+
+    def warm_start(self, solver: "Solver", mesh: Mesh, mach: float, kn: float, freestream) -> int:
+        """Resets the solver to the Chapman-Enskog start of the predicted
+        fields; returns the number of cells that fell back to the freestream."""
+        args = _MeshArgs(mesh, None)
+        fs = np.ascontiguousarray(freestream, dtype=np.float64)
+        if fs.size != mesh.dim + 2:
+            raise ValueError("freestream = (rho, U[dim], T)")
+        nf = ctypes.c_int64()
+        self._c(self._lib.ugks_mlp_warm_start(self._net, solver._ctx, ctypes.byref(args.mesh), float(mach),
+                                              float(kn), _ptr(fs), ctypes.byref(nf)))
+        return nf.value
+
+    def close(self) -> None:
+        if getattr(self, "_net", None):
+            self._lib.ugks_mlp_destroy(self._net)
+            self._net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve(mesh: Mesh, grid: VelocityGrid, gas: Gas, W_init: np.ndarray, n_steps: int, storage: str = "f32",

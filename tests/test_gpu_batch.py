@@ -3,7 +3,8 @@
 Heterogeneous cases (2-D quads, 2-D triangles with K = 2, 3-D periodic box)
 in one batch: a graph launch advances every case by two steps on forked
 streams.  The per-case arithmetic is the ordinary step's, so batch results
-equal the cases stepped one by one (bitwise, at the same block size) and
+equal the cases stepped one by one (W bitwise at the same block size; the
+residual up to the summation order of its atomics) and
 match the oracle; the block-size autotuner picks one of the allowed sizes and
 caches it per case shape."""
 import numpy as np
@@ -37,7 +38,8 @@ def test_batch_graph_steps_equal_single_case_steps(nsteps):
         with U.Solver(mesh, grid, gas, W0, storage="f32", sweep="blocked", block_velocities=64) as s:
             s.step(nsteps)
             np.testing.assert_array_equal(W, s.moments())
-            np.testing.assert_array_equal(r, s.residual())
+            # the residual's cross-CTA sum uses atomics: equal up to summation order
+            np.testing.assert_allclose(r, s.residual(), rtol=1e-13, atol=0)
 
 
 def test_batch_fp64_matches_oracle():
