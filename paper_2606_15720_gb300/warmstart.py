@@ -124,9 +124,17 @@ def experiment(train, held_out, cells: int, nvx: int, width: int = 256, hidden_l
     for i, (epochs, lr) in enumerate(schedule):
         losses.append(net.train(X, Y, epochs=epochs, batch=batch, lr=lr, seed=seed + i))
         say("epochs", epochs, "lr", lr, "loss", losses[-1])
-    out["training"] = {"samples": int(X.shape[0]), "epochs": sum(e for e, _ in schedule), "batch": batch,
-                       "schedule": [list(s) for s in schedule], "loss": losses,
-                       "seconds": time.perf_counter() - t0}
+    secs = time.perf_counter() - t0
+    epochs = sum(e for e, _ in schedule)
+    # tensor-core work: forward, data gradient and weight gradient GEMMs of
+    # every layer (padded widths, the first layer has no data gradient)
+    pad = lambda n: (n + 15) // 16 * 16  # noqa: E731
+    sizes = [pad(n) for n in net.sizes]
+    macs = sum(a * b for a, b in zip(sizes[:-1], sizes[1:]))
+    flops = 2.0 * (3 * macs - sizes[0] * sizes[1]) * X.shape[0] * epochs
+    out["training"] = {"samples": int(X.shape[0]), "epochs": epochs, "batch": batch,
+                       "schedule": [list(s) for s in schedule], "loss": losses, "seconds": secs,
+                       "gemm_tflops": flops / secs / 1e12}
     out["cases"] = []
     for j, (ma, kn) in enumerate(held_out):
         mesh, grid, gas, W0 = cylinder_case(ma, kn, cells, nvx, seed=5000 + j)
