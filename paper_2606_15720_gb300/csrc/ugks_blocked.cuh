@@ -695,7 +695,7 @@ __host__ __device__ constexpr int g01_chunk() {
   return (int(offsetof(FP, G0)) / 16) * 16;
 }
 
-template <int D, int NR, int VB, typename T, typename S>
+template <int D, int NR, int VB, int WT, typename T, typename S>
 __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<T> a, const int64_t m0) {
   using CS = CellStage<NR, VB, T>;
   using SL = CellSlot<NR, VB, S>;
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<
   static_assert(offsetof(FP, G1) + sizeof(T) <= size_t(g01_chunk<D, NR, T>() + 16),
                 "G0 and G1 share one 16-byte chunk");
   extern __shared__ __align__(16) unsigned char cell_smem[];
-  const int W = a.W;
+  constexpr int W = WT;  // ELL slots per cell (the table is padded to WT)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int AB = W * CS::INC + 16, BB = (W + 1) * SL::BYTES + W * 16;
   unsigned char* const As = cell_smem + warp * recon_warp_bytes<NR, VB, T, S>(W);
@@ -767,6 +767,7 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<
 #pragma unroll
         for (int d = 0; d < D; ++d) g[r][j][d] = T(0);
       }
+#pragma unroll
     for (int i = 0; i < W; ++i) {
       const int fl = inc[i].flags;
       if (fl & 3) continue;  // walls: one-sided stencil; padding
@@ -824,6 +825,16 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<
           dmx[r][j] = fmx[r][j] - fc[r][j];
           dmn[r][j] = fmn[r][j] - fc[r][j];
         }
+      // Both limiters are non-increasing in |d2| on each side (Venkatakrishnan's
+      // psi(dp, d2) is >= 1 for d2/dp <= 1/2 and decreasing beyond), so the
+      // minimum over faces is taken at the largest positive and the most
+      // negative face increment: two evaluations instead of one per face.
+      T d2p[NR][VB], d2n[NR][VB];
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int j = 0; j < VB; ++j) d2p[r][j] = d2n[r][j] = T(0);
+#pragma unroll
       for (int i = 0; i < W; ++i) {
         if (inc[i].flags & 2) continue;  // padding
         T rr[D];
@@ -836,19 +847,30 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<
             T d2 = T(0);
 #pragma unroll
             for (int d = 0; d < D; ++d) d2 += g[r][j][d] * rr[d];
-            const T dp = d2 > T(0) ? dmx[r][j] : dmn[r][j];
+            d2p[r][j] = fmax(d2p[r][j], d2);
+            d2n[r][j] = fmin(d2n[r][j], d2);
+          }
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int j = 0; j < VB; ++j)
+#pragma unroll
+          for (int side = 0; side < 2; ++side) {
+            const T d2 = side == 0 ? d2p[r][j] : d2n[r][j];
+            const T dp = side == 0 ? dmx[r][j] : dmn[r][j];
+            if (d2 == T(0)) continue;
             T ph;
             if (limiter == 2) {
-              ph = d2 != T(0) ? fast_div(dp, d2) : T(1);
+              ph = fast_div(dp, d2);
             } else {
-              // (dp^2 + eps + 2 d2 dp) / (dp^2 + 2 d2^2 + dp d2 + eps); equals 1 at d2 = 0
+              // (dp^2 + eps + 2 d2 dp) / (dp^2 + 2 d2^2 + dp d2 + eps)
               const T num = fma(dp, dp + T(2) * d2, eps2[r][j]);
               const T den = fma(dp + d2, dp, fma(T(2) * d2, d2, eps2[r][j]));
               ph = fast_div(num, den);
             }
-            phi[r][j] = fmin(phi[r][j], ph);  // fmin ignores a NaN from 0/0 (then d2 = 0, phi stays)
+            phi[r][j] = fmin(phi[r][j], ph);
           }
-      }
     }
     T ug[NR][VB];  // u . (limited gradient), the same on every face
 #pragma unroll
@@ -866,6 +888,7 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<
     // free-transport part on every face for which this cell is upwind
     const T* G01 = reinterpret_cast<const T*>(B + (W + 1) * SL::BYTES);
     constexpr int g0i = (int(offsetof(FP, G0)) - g01_chunk<D, NR, T>()) / int(sizeof(T));
+#pragma unroll
     for (int i = 0; i < W; ++i) {
       const int fl = inc[i].flags;
       if (fl & 2) continue;
@@ -905,12 +928,12 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<
   cp_async_wait<0>();
 }
 
-template <int D, int NR, int VB, typename T, typename S>
+template <int D, int NR, int VB, int WT, typename T, typename S>
 __global__ void __launch_bounds__(kBlockedThreads) k_bstage1_p(const BlockedArgs<T> a, const int64_t m0) {
   using CS = CellStage<NR, VB, T>;
   using SL = CellSlot<NR, VB, S>;
   extern __shared__ __align__(16) unsigned char cell_smem[];
-  const int W = a.W;
+  constexpr int W = WT;  // ELL slots per cell (the table is padded to WT)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int AB = W * CS::INC + int(sizeof(CellEq<T>)), BB = W * CS::ROW + SL::BYTES;
   unsigned char* const As = cell_smem + warp * stage1_warp_bytes<NR, VB, T, S>(W);
@@ -960,6 +983,7 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage1_p(const BlockedArgs
     for (int r = 0; r < NR; ++r)
 #pragma unroll
       for (int j = 0; j < VB; ++j) flux[r][j] = T(0);
+#pragma unroll
     for (int i = 0; i < W; ++i) {
       if (inc[i].flags & 2) continue;
       const T sa = inc[i].sarea;
@@ -1329,10 +1353,28 @@ cudaError_t launch_cell_pipelined(K kernel, int nsm, int bytes, int& warps_out, 
 // Per-warp shared memory above which the pipelined kernels are not used.
 constexpr int kPipelineWarpBytes = 24 * 1024;
 
+// Launch of a pipelined per-cell kernel: warps per CTA and the persistent grid
+// are worked out once per instantiation and per-warp size.
+template <typename T, typename K>
+cudaError_t launch_cell_cached(K kernel, cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int bytes,
+                               int& cached_bytes, int& cached_warps, unsigned& cached_grid) {
+  if (cached_bytes != bytes) {
+    cudaError_t e = launch_cell_pipelined(kernel, a.nsm, bytes, cached_warps, cached_grid);
+    if (e != cudaSuccess) return e;
+    cached_bytes = bytes;
+  }
+  const unsigned grid = std::min<unsigned>(cached_grid, unsigned((a.Nc + cached_warps - 1) / cached_warps));
+  kernel<<<grid, cached_warps * 32, cached_warps * bytes, s>>>(a, m0);
+  return cudaGetLastError();
+}
+
+// The pipelined kernels are compiled for ELL widths 4 and 8 (the host pads
+// the table to one of them); other widths and oversize stages use the plain
+// kernels.
 template <int D, int NR, int VB, typename T, typename S>
 cudaError_t launch_brecon_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0) {
   const int bytes = recon_warp_bytes<NR, VB, T, S>(a.W);
-  if (a.W < 1 || a.W > kEllMax || bytes > kPipelineWarpBytes) {
+  if ((a.W != 4 && a.W != 8) || bytes > kPipelineWarpBytes) {
     if constexpr (StoreTraits<S>::scaled) {
       return cudaErrorNotSupported;  // scaled storage runs only in the pipelined kernels
     } else {
@@ -1340,22 +1382,16 @@ cudaError_t launch_brecon_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t m
       return cudaGetLastError();
     }
   }
-  static int cached_bytes = -1, cached_warps = 0;
-  static unsigned cached_grid = 0;
-  if (cached_bytes != bytes) {
-    cudaError_t e = launch_cell_pipelined(k_brecon_p<D, NR, VB, T, S>, a.nsm, bytes, cached_warps, cached_grid);
-    if (e != cudaSuccess) return e;
-    cached_bytes = bytes;
-  }
-  const unsigned grid = std::min<unsigned>(cached_grid, unsigned((a.Nc + cached_warps - 1) / cached_warps));
-  k_brecon_p<D, NR, VB, T, S><<<grid, cached_warps * 32, cached_warps * bytes, s>>>(a, m0);
-  return cudaGetLastError();
+  static int cb4 = -1, cw4 = 0, cb8 = -1, cw8 = 0;
+  static unsigned cg4 = 0, cg8 = 0;
+  if (a.W == 4) return launch_cell_cached<T>(k_brecon_p<D, NR, VB, 4, T, S>, s, a, m0, bytes, cb4, cw4, cg4);
+  return launch_cell_cached<T>(k_brecon_p<D, NR, VB, 8, T, S>, s, a, m0, bytes, cb8, cw8, cg8);
 }
 
 template <int D, int NR, int VB, typename T, typename S>
 cudaError_t launch_bstage1_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0) {
   const int bytes = stage1_warp_bytes<NR, VB, T, S>(a.W);
-  if (a.W < 1 || a.W > kEllMax || bytes > kPipelineWarpBytes) {
+  if ((a.W != 4 && a.W != 8) || bytes > kPipelineWarpBytes) {
     if constexpr (StoreTraits<S>::scaled) {
       return cudaErrorNotSupported;
     } else {
@@ -1363,17 +1399,10 @@ cudaError_t launch_bstage1_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t 
       return cudaGetLastError();
     }
   }
-  static int cached_bytes = -1, cached_warps = 0;
-  static unsigned cached_grid = 0;
-  if (cached_bytes != bytes) {
-    cudaError_t e =
-        launch_cell_pipelined(k_bstage1_p<D, NR, VB, T, S>, a.nsm, bytes, cached_warps, cached_grid);
-    if (e != cudaSuccess) return e;
-    cached_bytes = bytes;
-  }
-  const unsigned grid = std::min<unsigned>(cached_grid, unsigned((a.Nc + cached_warps - 1) / cached_warps));
-  k_bstage1_p<D, NR, VB, T, S><<<grid, cached_warps * 32, cached_warps * bytes, s>>>(a, m0);
-  return cudaGetLastError();
+  static int cb4 = -1, cw4 = 0, cb8 = -1, cw8 = 0;
+  static unsigned cg4 = 0, cg8 = 0;
+  if (a.W == 4) return launch_cell_cached<T>(k_bstage1_p<D, NR, VB, 4, T, S>, s, a, m0, bytes, cb4, cw4, cg4);
+  return launch_cell_cached<T>(k_bstage1_p<D, NR, VB, 8, T, S>, s, a, m0, bytes, cb8, cw8, cg8);
 }
 
 #define UGKS_CELL_CASES(FN)                                                                               \

@@ -422,9 +422,12 @@ ugks_status build_typed(ugks_ctx* ctx, const std::vector<int64_t>& cf_off, const
     IncT<T>* di;
     CUDA_TRY(ctx, upload(ctx, &di, inc.data(), inc.size() * sizeof(IncT<T>)));
     ctx->d_inc = di;
-    // the same records as a padded table [Nc][W], W = the most faces of a cell
+    // the same records as a padded table [Nc][W]: W = the most faces of a
+    // cell, rounded up to 4 or 8 (the widths the pipelined kernels are
+    // compiled for; padding slots are flagged)
     int W = 1;
     for (int64_t c = 0; c < ctx->Nc; ++c) W = std::max<int>(W, int(cf_off[c + 1] - cf_off[c]));
+    W = W <= 4 ? 4 : W <= 8 ? 8 : W;
     ctx->W = W;
     IncT<T> pad{};
     pad.face = 0;
