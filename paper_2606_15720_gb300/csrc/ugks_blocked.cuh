@@ -21,7 +21,8 @@
 // velocity's upwind cell writes its lane (the two cells of a face write
 // complementary lanes), the flux kernel overwrites it with the flux.  It is
 // rewritten by every block and stays mostly in L2.  After the last block:
-//   k_bwall    wall density from non-penetration (Eq. 38)
+//   k_bwall    face accumulators to FP64 (FP32 sweeps: float pairs) and the
+//              wall density from non-penetration (Eq. 38)
 //   k_bW       conservative update (Eq. 27) and the primitive record of W^{n+1}
 //   k_bstage2  second stage (Eq. 42), in velocity chunks, and partial sums of
 //              the heat flux of f^{n+1} (Eq. 13); k_bqsum adds the chunks.
@@ -377,6 +378,29 @@ __device__ __forceinline__ void flux_prefetch(const BlockedArgs<T>& a, int f, un
   }
 }
 
+// Running sum of a face moment over the velocity blocks.  FP32 sweeps keep it
+// as an unevaluated pair of floats hi + lo (Knuth's two-sum, then a fast
+// renormalisation), which carries the sum of the block sums to ~2^-44
+// relative without FP64 instructions: GB300's FP64 pipe runs at a small
+// fraction of its FP32 rate (with a convert and an add in FP64 per face and
+// block the flux kernel kept that pipe 21 % busy, and ran 4 % slower).
+// k_bwall turns the pairs into doubles after the last block.  FP64 sweeps
+// add in double.
+template <typename T>
+__device__ __forceinline__ void facc_add(double* dst, const double* prev, bool first, T v) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 p = first ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(prev);
+    const float s = p.x + v;
+    const float bp = s - p.x;
+    const float e = (p.x - (s - bp)) + (v - bp);
+    const float lo = p.y + e;
+    const float hi = s + lo;
+    *reinterpret_cast<float2*>(dst) = make_float2(hi, lo - (hi - s));
+  } else {
+    *dst = (first ? 0.0 : *prev) + double(v);
+  }
+}
+
 template <int D, int NR, int VB, typename T>
 __device__ __forceinline__ void flux_face(const BlockedArgs<T>& a, const int f, const unsigned char* st,
                                           const BlockVel<D, NR, VB, T>& v, const int first, const int lane) {
@@ -433,8 +457,8 @@ __device__ __forceinline__ void flux_face(const BlockedArgs<T>& a, const int f, 
     const T sin = warp_sum8<T>(m_in[0], m_in[1], m_in[2], m_in[3], m_in[4], T(0), T(0), T(0), lane);
     const T sout = warp_sum8<T>(m_out[0], m_out[1], m_out[2], m_out[3], m_out[4], T(0), T(0), T(0), lane);
     if (writer) {
-      Fa[idx8] = (first ? 0.0 : Fs[idx8]) + double(sin);
-      Fa[5 + idx8] = (first ? 0.0 : Fs[5 + idx8]) + double(sout);
+      facc_add<T>(Fa + idx8, Fs + idx8, first, sin);
+      facc_add<T>(Fa + 5 + idx8, Fs + 5 + idx8, first, sout);
     }
     return;
   }
@@ -489,7 +513,7 @@ __device__ __forceinline__ void flux_face(const BlockedArgs<T>& a, const int f, 
   }
   // value index t of the reduction is conservative variable t (energy at D + 1)
   const T sm = warp_sum8<T>(m_in[0], m_in[1], m_in[2], m_in[3], m_in[4], T(0), T(0), T(0), lane);
-  if (writer) Fa[idx8] = (first ? 0.0 : Fs[idx8]) + double(sm);
+  if (writer) facc_add<T>(Fa + idx8, Fs + idx8, first, sm);
 }
 
 template <int D, int NR, int VB, typename T>
@@ -1038,8 +1062,18 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage1_p(const BlockedArgs
 template <typename T>
 __global__ void k_bwall(const BlockedArgs<T> a) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= a.Nf || a.fg[f].bc_type != 1) return;
+  if (f >= a.Nf) return;
   double* F = a.Facc + size_t(f) * FACC_W;
+  if constexpr (sizeof(T) == 4) {
+    // float pairs of the FP32 sweep (facc_add) -> doubles
+    const bool wall = a.fg[f].bc_type == 1;
+    for (int t = 0; t < 10; ++t)
+      if (t < a.g.D + 2 || (wall && t >= 5 && t < 5 + a.g.D + 2)) {
+        const float2 p = *reinterpret_cast<const float2*>(F + t);
+        F[t] = double(p.x) + double(p.y);
+      }
+  }
+  if (a.fg[f].bc_type != 1) return;
   const int NW = a.g.D + 2;
   const double rw = F[5] != 0.0 ? -F[0] / F[5] : 0.0;
   for (int t = 0; t < NW; ++t) F[t] += rw * F[5 + t];
