@@ -456,11 +456,18 @@ def run_mixed_report(args):
     return 0
 
 
-def batch_cases(n=64, seed=4, cells_range=(5e3, 4e4), nv_range=(20, 48), mach_range=(2.0, 8.0)):
-    """The 64 cylinder cases of the batch workload: Ma ~ U[2, 8], Kn ~
+def batch_cases(n=64, seed=4, cells_range=(5e3, 4e4), nv_range=(20, 48), mach_range=(2.0, 4.0)):
+    """The 64 cylinder cases of the batch workload: Ma ~ U[2, 4], Kn ~
     log-uniform [1e-3, 1], triangle meshes of 5k-40k cells (log-uniform),
-    velocity grids sized to Ma (20^2 .. 48^2 points, spacing ~1 thermal unit
-    of the free stream, range covering the stagnation temperature)."""
+    velocity grids sized to Ma (20^2 .. 48^2 points on [-v, v]^2, v covering
+    the free stream and the stagnation temperature, spacing at most 0.7 =
+    about the thermal width sqrt(T_inf/2) of the free stream: grids of
+    spacing ~1 under-resolve the free-stream Maxwellian and those cases went
+    non-physical within 40-80 steps).  Above Ma ~4.4 the impulsive
+    freestream start against the hot wall drives f negative within a few
+    steps at these resolutions, in the FP64 oracle as on the GPU (Ma 7.5,
+    Kn 0.005: non-physical at step 4 in the oracle), so the Mach range is
+    [2, 4]."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
@@ -471,7 +478,7 @@ def batch_cases(n=64, seed=4, cells_range=(5e3, 4e4), nv_range=(20, 48), mach_ra
         u_inf = mesh.bc[1].u[0]
         T_stag = 1.0 + mach * mach / 3.0
         vmax = max(u_inf + 4.0, 3.5 * math.sqrt(T_stag))
-        nvx = int(min(nv_range[1], max(nv_range[0], round(2.0 * vmax))))
+        nvx = int(min(nv_range[1], max(nv_range[0], math.ceil(2.0 * vmax / 0.7))))
         grid = I.midpoint_grid(nvx, -vmax, vmax, 2)
         gas = I.Gas(model="shakhov", K=0, Pr=2.0 / 3.0, omega=0.81, mu_ref=I.mu_ref_from_kn(kn, 0.81), cfl=0.8)
         W0 = I.prim_to_conservative(I.uniform_primitives(mesh, 1.0, mesh.bc[1].u, 1.0), 2, 0)
@@ -488,7 +495,7 @@ def run_batch_report(args):
     import torch
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU (the CUDA library has no CPU path)")
-    big = time_batch(args, batch_cases(), "cylinder_batch64_ma2-8_kn1e-3-1_tri5k-40k_v20-48sq_shakhov_fp32")
+    big = time_batch(args, batch_cases(), "cylinder_batch64_ma2-4_kn1e-3-1_tri5k-40k_v20-48sq_shakhov_fp32")
     small = time_batch(args, batch_cases(seed=5, cells_range=(300, 1500), nv_range=(20, 24), mach_range=(1.5, 3.0)),
                        "cylinder_batch64_small_ma1.5-3_tri300-1500_v20-24sq_shakhov_fp32")
     print(json.dumps(dict(big, small_cases=small)), flush=True)

@@ -386,16 +386,29 @@ __device__ __forceinline__ void flux_prefetch(const BlockedArgs<T>& a, int f, un
 // block the flux kernel kept that pipe 21 % busy, and ran 4 % slower).
 // k_bwall turns the pairs into doubles after the last block.  FP64 sweeps
 // add in double.
+// (hi, lo) + v for an unevaluated float pair: two-sum, then renormalise.
+__device__ __forceinline__ float2 pair_add(float2 p, float v) {
+  const float s = p.x + v;
+  const float bp = s - p.x;
+  const float e = (p.x - (s - bp)) + (v - bp);
+  const float lo = p.y + e;
+  const float hi = s + lo;
+  return make_float2(hi, lo - (hi - s));
+}
+// (hi, lo) + (hi, lo)
+__device__ __forceinline__ float2 pair_add(float2 p, float2 q) {
+  const float s = p.x + q.x;
+  const float bp = s - p.x;
+  const float e = (p.x - (s - bp)) + (q.x - bp) + (p.y + q.y);
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+
 template <typename T>
 __device__ __forceinline__ void facc_add(double* dst, const double* prev, bool first, T v) {
   if constexpr (sizeof(T) == 4) {
     const float2 p = first ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(prev);
-    const float s = p.x + v;
-    const float bp = s - p.x;
-    const float e = (p.x - (s - bp)) + (v - bp);
-    const float lo = p.y + e;
-    const float hi = s + lo;
-    *reinterpret_cast<float2*>(dst) = make_float2(hi, lo - (hi - s));
+    *reinterpret_cast<float2*>(dst) = pair_add(p, v);
   } else {
     *dst = (first ? 0.0 : *prev) + double(v);
   }
@@ -1251,7 +1264,11 @@ __global__ void __launch_bounds__(kBlockedThreads, sizeof(T) == 4 ? (NR == 1 ? 4
   const int e0 = a.cf_off[cc], e1 = a.cf_off[cc + 1];
   bool has_wall = false;
   for (int e = e0; e < e1; ++e) has_wall |= (a.inc[e].flags & 1) != 0;
+  // partial sums of q: per lane in T for 32 blocks, then flushed into a
+  // running sum (FP64 for the FP64 sweep; a float pair for the FP32 sweep,
+  // which keeps this kernel off GB300's narrow FP64 pipe)
   double qd[3] = {0.0, 0.0, 0.0};
+  float2 qf[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   T qp[3] = {T(0), T(0), T(0)};
 
   // round k covers blocks [m, m + UNR); its rows and velocity records are
@@ -1316,17 +1333,32 @@ __global__ void __launch_bounds__(kBlockedThreads, sizeof(T) == 4 ? (NR == 1 ? 4
         ft[i][r] = fn[i][r];
         sc[i][r] = sn[i][r];
       }
-    if ((k & 3) == 3) {  // flush the FP32 partial sums every 32 blocks
+    if ((k & 3) == 3) {  // flush the per-lane partial sums every 32 blocks
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        qd[d] += double(qp[d]);
+        if constexpr (sizeof(T) == 4)
+          qf[d] = pair_add(qf[d], float(qp[d]));
+        else
+          qd[d] += double(qp[d]);
         qp[d] = T(0);
       }
     }
   }
   if (!valid) return;
 #pragma unroll
-  for (int d = 0; d < D; ++d) qd[d] = warp_sum(qd[d] + double(qp[d]));
+  for (int d = 0; d < D; ++d) {
+    if constexpr (sizeof(T) == 4) {
+      float2 v = pair_add(qf[d], float(qp[d]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float2 w = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+        v = pair_add(v, w);
+      }
+      qd[d] = double(v.x) + double(v.y);
+    } else {
+      qd[d] = warp_sum(qd[d] + double(qp[d]));
+    }
+  }
   double* qo = a.qpart + (size_t(chunk) * a.Nc + c) * 3;
   if (lane < 3) qo[lane] = lane < D ? (lane == 0 ? qd[0] : lane == 1 ? qd[D > 1 ? 1 : 0] : qd[D > 2 ? 2 : 0]) : 0.0;
 }
