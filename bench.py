@@ -586,7 +586,7 @@ def main():
     ap.add_argument("--cells", type=int, default=MESH_CELLS, help="mesh size (profiling runs only)")
     ap.add_argument("--nv-axis", type=int, default=NV_AXIS, help="velocities per axis (profiling runs only)")
     ap.add_argument("--sweep", default="auto", choices=["auto", "blocked", "tiled"])
-    ap.add_argument("--block-velocities", type=int, default=0, choices=[0, 32, 64, 128])
+    ap.add_argument("--block-velocities", type=int, default=0, choices=[0, 32, 64, 128, 256])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="storage of f (FP16 / BF16: deviations from a per-cell reference Maxwellian)")
     ap.add_argument("--report", default=None, choices=["mixed", "batch", "warmstart"],

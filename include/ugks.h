@@ -122,8 +122,9 @@ typedef struct {
  *     stage of each velocity block as three grid-wide kernels; TILED runs one
  *     persistent kernel over spatial tiles held in shared memory; AUTO picks
  *     BLOCKED.  Both give the same result up to rounding order.
- *   block_velocities: velocities per block of the blocked sweep (32, 64 or
- *     128; 0 = automatic) */
+ *   block_velocities: velocities per block of the blocked sweep (32, 64,
+ *     128, or 256 for dim 3 with one reduced distribution (K_xi = 0);
+ *     0 = automatic: 256 where allowed, else 128) */
 typedef struct {
   int32_t model;
   int32_t K;
@@ -272,7 +273,7 @@ ugks_status ugks_batch_create(int32_t n, const ugks_mesh *const *meshes, const u
                               ugks_batch **out);
 
 /* Block-size autotuner: every case not tuned yet runs two steps at each
- * block size of 32, 64 and 128 velocities that its buffers allow, timed on
+ * block size of 32, 64, 128 (and 256) velocities that its buffers allow, timed on
  * the device (the second step of each pair), and keeps the fastest.  These
  * steps advance the cases (different block sizes change only the summation
  * order of the moments).  The choice is cached for the process. */
@@ -284,7 +285,8 @@ ugks_status ugks_batch_step(ugks_batch *batch, int32_t n_steps);
 ugks_status ugks_batch_context(ugks_batch *batch, int32_t i, ugks_ctx **ctx);
 
 /* Block size in use for case i (velocities per block) and the autotuner's
- * timings (ms per step at 32, 64, 128 velocities per block; 0 = not run). */
+ * timings, ms_per_step[4]: ms per step at 32, 64, 128, 256 velocities per
+ * block (0 = not run). */
 ugks_status ugks_batch_tuning(ugks_batch *batch, int32_t i, int32_t *block_velocities, double *ms_per_step);
 
 ugks_status ugks_batch_destroy(ugks_batch *batch);

@@ -1473,6 +1473,7 @@ cudaError_t launch_bstage1_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t 
 
 #define UGKS_CELL_CASES(FN)                                                                               \
   FN(1, 2, 1) FN(1, 2, 2) FN(1, 2, 4) FN(2, 2, 1) FN(2, 2, 2) FN(2, 2, 4) FN(3, 1, 1) FN(3, 1, 2) FN(3, 1, 4) \
+  FN(3, 1, 8) \
   FN(3, 2, 1) FN(3, 2, 2) FN(3, 2, 4)
 
 template <typename T, typename S>
@@ -1510,7 +1511,7 @@ cudaError_t launch_bflux(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, in
   if (D == d && NR == nr && vb == b) return launch_bflux_tpl<d, nr, b, T>(s, a, m0, first);
   UGKS_FLUX_CASE(1, 2, 1) UGKS_FLUX_CASE(1, 2, 2) UGKS_FLUX_CASE(1, 2, 4)
   UGKS_FLUX_CASE(2, 2, 1) UGKS_FLUX_CASE(2, 2, 2) UGKS_FLUX_CASE(2, 2, 4)
-  UGKS_FLUX_CASE(3, 1, 1) UGKS_FLUX_CASE(3, 1, 2) UGKS_FLUX_CASE(3, 1, 4)
+  UGKS_FLUX_CASE(3, 1, 1) UGKS_FLUX_CASE(3, 1, 2) UGKS_FLUX_CASE(3, 1, 4) UGKS_FLUX_CASE(3, 1, 8)
   UGKS_FLUX_CASE(3, 2, 1) UGKS_FLUX_CASE(3, 2, 2) UGKS_FLUX_CASE(3, 2, 4)
 #undef UGKS_FLUX_CASE
   return cudaErrorInvalidValue;

@@ -278,8 +278,8 @@ ugks_status validate(const ugks_mesh* m, const ugks_vgrid* v, const ugks_params*
   if (p->sweep < UGKS_SWEEP_AUTO || p->sweep > UGKS_SWEEP_BLOCKED)
     return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "unknown sweep %d", p->sweep);
   if (p->block_velocities != 0 && p->block_velocities != 32 && p->block_velocities != 64 &&
-      p->block_velocities != 128)
-    return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "block_velocities must be 0, 32, 64 or 128");
+      p->block_velocities != 128 && p->block_velocities != 256)
+    return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "block_velocities must be 0, 32, 64, 128 or 256");
   return UGKS_OK;
 }
 
@@ -903,7 +903,13 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
       return fail(ctx, UGKS_ERR_UNSUPPORTED, "the blocked sweep needs fewer than 2^31 cells, faces and incidences");
     ctx->variant = 1;
   }
-  ctx->vb = p->block_velocities > 0 ? p->block_velocities / BV : 4;
+  // default: 256 velocities per block where compiled (3-D, one reduced
+  // distribution), else 128; fewer velocities than that: the largest power
+  // of two that fits
+  const bool vb8 = ctx->D == 3 && ctx->NR == 1;
+  ctx->vb = p->block_velocities > 0 ? p->block_velocities / BV : (vb8 ? 8 : 4);
+  if (ctx->vb == 8 && !vb8)
+    return fail(ctx, UGKS_ERR_UNSUPPORTED, "256 velocities per block: 3-D with one reduced distribution only");
   while (ctx->vb > ctx->M) ctx->vb /= 2;
   ctx->vb_max = ctx->vb;
   ctx->nchunk = int(std::min<int64_t>(ctx->M, 8));
@@ -1570,7 +1576,7 @@ struct ugks_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<int> tuned_bv;                 // velocities per block chosen by the autotuner (0: not tuned)
-  std::vector<std::vector<double>> tune_ms;  // ms per step of each candidate (32, 64, 128 velocities)
+  std::vector<std::vector<double>> tune_ms;  // ms per step of each candidate (32, 64, 128, 256 velocities)
   std::string err;
 };
 
@@ -1722,7 +1728,7 @@ ugks_status ugks_batch_create(int32_t n, const ugks_mesh* const* meshes, const u
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(TuneKey(c->Nc, c->nv, c->D, c->NR, c->storage));
     b->tuned_bv.push_back(0);
-    b->tune_ms.push_back(std::vector<double>(3, 0.0));
+    b->tune_ms.push_back(std::vector<double>(4, 0.0));
     if (it != g_tune_cache.end() && it->second <= c->vb_max) {
       c->vb = it->second;
       b->tuned_bv.back() = it->second * BV;
@@ -1816,7 +1822,7 @@ ugks_status ugks_batch_tuning(ugks_batch* b, int32_t i, int32_t* block_velocitie
     return bfail(b, UGKS_ERR_INVALID_ARGUMENT, "no case %d in this batch", i);
   if (block_velocities) *block_velocities = b->tuned_bv[i] ? b->tuned_bv[i] : b->cases[i]->vb * BV;
   if (ms_per_step)
-    for (int k = 0; k < 3; ++k) ms_per_step[k] = b->tune_ms[i][k];
+    for (int k = 0; k < 4; ++k) ms_per_step[k] = b->tune_ms[i][k];
   return UGKS_OK;
 }
 

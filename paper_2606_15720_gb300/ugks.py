@@ -361,7 +361,7 @@ class Batch:
 
     def tuning(self, i: int):
         bv = ctypes.c_int32()
-        ms = np.zeros(3)
+        ms = np.zeros(4)
         self._c(self._lib.ugks_batch_tuning(self._b, int(i), ctypes.byref(bv), _ptr(ms)))
         return bv.value, ms
 

@@ -62,8 +62,8 @@ def test_autotuner_picks_an_allowed_block_size_and_caches_it():
         b.autotune()
         picks = [b.tuning(i) for i in range(len(cases))]
         for bv, ms in picks:
-            assert bv in (32, 64, 128)
-            assert ms[0] > 0.0 and ms[{32: 0, 64: 1, 128: 2}[bv]] == pytest.approx(min(m for m in ms if m > 0))
+            assert bv in (32, 64, 128, 256)
+            assert ms[0] > 0.0 and ms[{32: 0, 64: 1, 128: 2, 256: 3}[bv]] == pytest.approx(min(m for m in ms if m > 0))
         for s in b.cases:
             assert np.all(np.isfinite(s.moments()))
     # the same case shapes again: the cached sizes are reused, no tuning steps run

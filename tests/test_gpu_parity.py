@@ -54,19 +54,28 @@ def w_err(a, b):
     return float(max(e_rho, e_mom, e_E))
 
 
-# device organisations of the sweep: the blocked sweep with 32, 64 and 128
-# velocities per block, and the tiled sweep (small tiles: several per CTA)
+# device organisations of the sweep: the blocked sweep with 32, 64, 128 and
+# (3-D, one reduced distribution) 256 velocities per block, and the tiled
+# sweep (small tiles: several per CTA)
 SWEEPS = {
     "blocked64": dict(sweep="blocked", block_velocities=64),
     "blocked32": dict(sweep="blocked", block_velocities=32),
     "blocked128": dict(sweep="blocked", block_velocities=128),
+    "blocked256": dict(sweep="blocked", block_velocities=256),
     "tiled": dict(sweep="tiled", tile_cells=48),
     "scaled": dict(sweep="blocked"),   # the storage argument selects FP16 / BF16
 }
 _oracle_cache = {}
 
 
+def supports(sweep, mesh, gas):
+    """256 velocities per block are compiled for 3-D with K_xi = 0 only."""
+    return sweep != "blocked256" or (mesh.dim == 3 and gas.K == 0)
+
+
 def run_pair(U, mesh, grid, gas, prim, nsteps, storage, sweep="blocked64", key=None):
+    if not supports(sweep, mesh, gas):
+        pytest.skip("256 velocities per block: 3-D with K_xi = 0 only")
     W0 = I.prim_to_conservative(prim, mesh.dim, gas.K)
     with U.Solver(mesh, grid, gas, W0, storage=storage, **SWEEPS[sweep]) as s:
         dt = s.dt
@@ -174,7 +183,7 @@ LONG_CASES = {
 }
 
 
-@pytest.mark.parametrize("sweep", ["blocked64", "tiled"])
+@pytest.mark.parametrize("sweep", ["blocked64", "blocked256", "tiled"])
 @pytest.mark.parametrize("name", sorted(LONG_CASES))
 def test_fp32_hundred_steps_matches_oracle(U, name, sweep):
     mesh, grid, gas, prim = LONG_CASES[name]()
@@ -211,8 +220,8 @@ def test_tiling_does_not_change_the_result(U):
 
 
 def test_sweep_organisations_agree(U):
-    """The blocked sweep at 32, 64 and 128 velocities per block and the tiled
-    sweep compute the same step: FP64 W agrees to round-off."""
+    """The blocked sweep at 32, 64, 128 and 256 velocities per block and the
+    tiled sweep compute the same step: FP64 W agrees to round-off."""
     mesh, grid, gas, prim = sphere_case(cells=2000, nvx=9)
     W0 = I.prim_to_conservative(prim, 3, 0)
     outs = {}
