@@ -1273,7 +1273,8 @@ __global__ void __launch_bounds__(kBlockedThreads, sizeof(T) == 4 ? (NR == 1 ? 4
 
   // round k covers blocks [m, m + UNR); its rows and velocity records are
   // requested during round k - 1
-  auto load_rows = [&](int64_t m, S (&ft)[UNR][NR], float (&sc)[UNR][NR]) {
+  constexpr int USC = SCALED ? UNR : 1;  // row scales are kept only for scaled storage
+  auto load_rows = [&](int64_t m, S (&ft)[UNR][NR], float (&sc)[USC][NR]) {
 #pragma unroll
     for (int i = 0; i < UNR; ++i)
       if (m + i < me)
@@ -1284,7 +1285,7 @@ __global__ void __launch_bounds__(kBlockedThreads, sizeof(T) == 4 ? (NR == 1 ? 4
         }
   };
   S ft[UNR][NR], fn[UNR][NR];
-  float sc[UNR][NR], sn[UNR][NR];
+  float sc[USC][NR], sn[USC][NR];
   if (mb * BV + threadIdx.x < me * BV) sv[0][threadIdx.x] = a.vel[mb * BV + threadIdx.x];
   if (valid) load_rows(mb, ft, sc);
   int k = 0;
@@ -1331,7 +1332,7 @@ __global__ void __launch_bounds__(kBlockedThreads, sizeof(T) == 4 ? (NR == 1 ? 4
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         ft[i][r] = fn[i][r];
-        sc[i][r] = sn[i][r];
+        if constexpr (SCALED) sc[i][r] = sn[i][r];
       }
     if ((k & 3) == 3) {  // flush the per-lane partial sums every 32 blocks
 #pragma unroll
