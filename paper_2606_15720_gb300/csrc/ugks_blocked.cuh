@@ -477,8 +477,38 @@ __device__ __forceinline__ void flux_face(const BlockedArgs<T>& a, const int f, 
   }
 
   const bool ghost = fg.nei < 0;
+  if (!ghost) {
+    // interior face: straight-line code (u.n = 0 gives a zero flux by itself)
+#pragma unroll
+    for (int j = 0; j < VB; ++j) {
+      T un = T(0);
+#pragma unroll
+      for (int d = 0; d < D; ++d) un += v.u[j][d] * n[d];
+      T c[3] = {T(0), T(0), T(0)}, c2 = T(0);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        c[d] = v.u[j][d] - R.U[d];
+        c2 += c[d] * c[d];
+      }
+      const T H0 = R.rho_pref * t_exp(-R.lam * c2);
+      const T phi_h = un * fma(H0, horner_cubic<D, T>(R.P[0], c[0], c[1], c[2]), Xs[(0 * VB + j) * BV]);
+      T phi_b = T(0);
+      if (NR == 2)
+        phi_b = un * fma(H0, horner_cubic<D, T>(R.P[NR - 1], c[0], c[1], c[2]), Xs[((NR - 1) * VB + j) * BV]);
+      Xf[(0 * VB + j) * BV] = phi_h;
+      if (NR == 2) Xf[((NR - 1) * VB + j) * BV] = phi_b;
+      const T wph = v.w[j] * phi_h;
+      m_in[0] += wph;
+#pragma unroll
+      for (int d = 0; d < D; ++d) m_in[1 + d] += wph * v.u[j][d];
+      m_in[D + 1] += T(0.5) * v.w[j] * (v.u2[j] * phi_h + phi_b);
+    }
+    const T sm = warp_sum8<T>(m_in[0], m_in[1], m_in[2], m_in[3], m_in[4], T(0), T(0), T(0), lane);
+    if (writer) facc_add<T>(Fa + idx8, Fs + idx8, first, sm);
+    return;
+  }
   T gr = T(0), gl = T(0), gU[3] = {T(0), T(0), T(0)}, gk = T(0);
-  if (ghost) {
+  {
     // ghost side of an artificial boundary: Maxwellian of the ghost state, no slope
     T rho, lam;
     ghost_state<D, NR, T>(a, int(-fg.nei - 1), int(fg.own), rho, lam, gU);
