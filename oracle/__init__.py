@@ -84,6 +84,8 @@ def load():
         lib.orc_reduced_equilibrium.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, P, P, P, P]
         lib.orc_initial_f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P, P, P]
         lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_set_threads.restype = ctypes.c_int
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -274,3 +276,8 @@ def chapman_enskog(dim: int, K: int, vgrid, fields: np.ndarray) -> np.ndarray:
 
 def num_threads() -> int:
     return int(load().orc_num_threads())
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of later oracle calls; returns the previous count."""
+    return int(load().orc_set_threads(int(n)))
