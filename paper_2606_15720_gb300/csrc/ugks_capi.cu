@@ -280,6 +280,8 @@ ugks_status validate(const ugks_mesh* m, const ugks_vgrid* v, const ugks_params*
   if (p->block_velocities != 0 && p->block_velocities != 32 && p->block_velocities != 64 &&
       p->block_velocities != 128 && p->block_velocities != 256)
     return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "block_velocities must be 0, 32, 64, 128 or 256");
+  if (p->block_velocities == 256 && !(m->dim == 3 && p->K == 0))
+    return fail(nullptr, UGKS_ERR_UNSUPPORTED, "256 velocities per block: dim 3 with K_xi = 0 only");
   return UGKS_OK;
 }
 
@@ -908,8 +910,6 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
   // of two that fits
   const bool vb8 = ctx->D == 3 && ctx->NR == 1;
   ctx->vb = p->block_velocities > 0 ? p->block_velocities / BV : (vb8 ? 8 : 4);
-  if (ctx->vb == 8 && !vb8)
-    return fail(ctx, UGKS_ERR_UNSUPPORTED, "256 velocities per block: 3-D with one reduced distribution only");
   while (ctx->vb > ctx->M) ctx->vb /= 2;
   ctx->vb_max = ctx->vb;
   ctx->nchunk = int(std::min<int64_t>(ctx->M, 8));

@@ -36,10 +36,10 @@ def test_library_exports_every_declared_entry_point(lib):
     assert not missing, missing
 
 
-def _status_of(mesh, grid, gas, storage="f32", sweep="auto", raw_storage=None):
+def _status_of(mesh, grid, gas, storage="f32", sweep="auto", raw_storage=None, block_velocities=0):
     lib = ugks.load()
     args = ugks._MeshArgs(mesh, grid)
-    prm = ugks.make_params(gas, storage, sweep=sweep)
+    prm = ugks.make_params(gas, storage, sweep=sweep, block_velocities=block_velocities)
     if raw_storage is not None:
         prm.storage = raw_storage
     ctx = ctypes.c_void_p()
@@ -74,6 +74,10 @@ def test_validation_errors_are_reported_before_any_device_work(lib):
     assert st == 8 and "storage" in msg
     st, msg = _status_of(mesh, grid, gas, raw_storage=7)
     assert st == 1 and "storage" in msg
+    st, msg = _status_of(mesh, grid, gas, block_velocities=256)          # compiled for 3-D, K_xi = 0 only
+    assert st == 8 and "256" in msg
+    st, msg = _status_of(mesh, grid, gas, block_velocities=96)
+    assert st == 1 and "block_velocities" in msg
     out = ctypes.c_void_p()
     assert lib.ugks_create(None, None, None, None, None, ctypes.byref(out)) == 1
     assert lib.ugks_create(None, None, None, None, None, None) == 1
@@ -86,3 +90,15 @@ def test_binding_raises_instead_of_falling_back(lib, monkeypatch):
     monkeypatch.setattr(ugks._build, "LIB", "/nonexistent/libugks.so")
     with pytest.raises(OSError):
         ugks.load(build_if_missing=False)
+
+
+def test_warm_start_network_validates_its_arguments_on_the_host(lib):
+    out = ctypes.c_void_p()
+    assert lib.ugks_mlp_create(6, 9, 0, 6, 0, None, ctypes.byref(out)) == 1     # width 0
+    assert "shape" in lib.ugks_mlp_last_error(None).decode()
+    assert lib.ugks_mlp_create(6, 9, 64, 0, 0, None, ctypes.byref(out)) == 1    # no hidden layer
+    assert lib.ugks_mlp_create(6, 9, 64, 2, 0, None, None) == 1                 # no output pointer
+    assert not out.value
+    assert lib.ugks_mlp_train(None, None, None, 1, 1, 1, ctypes.c_float(1e-3), 0, None) == 1
+    assert lib.ugks_mlp_predict(None, None, 1, None) == 1
+    assert lib.ugks_mlp_destroy(None) == 0
