@@ -482,9 +482,8 @@ ugks_status init_state_typed(ugks_ctx* ctx) {
     CUDA_TRY(ctx, cudaGetLastError());
     return UGKS_OK;
   }
-  launch_init_f<T>(ctx->stream, ctx->Nc, ctx->M, ctx->nv, ctx->gas, ctx->d_W[0], ctx->d_ux, ctx->d_uy, ctx->d_uz,
-                   static_cast<T*>(ctx->d_f[0]));
-  CUDA_TRY(ctx, cudaGetLastError());
+  CUDA_TRY(ctx, launch_init_f<T>(ctx->stream, ctx->Nc, ctx->M, ctx->nv, ctx->gas, ctx->d_W[0], ctx->d_ux,
+                                 ctx->d_uy, ctx->d_uz, static_cast<T*>(ctx->d_f[0])));
   launch_moments<T>(ctx->stream, ctx->Nc, ctx->M, ctx->gas, static_cast<const T*>(ctx->d_f[0]), ctx->d_W[0],
                     ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp, ctx->d_q[0], nullptr);
   CUDA_TRY(ctx, cudaGetLastError());

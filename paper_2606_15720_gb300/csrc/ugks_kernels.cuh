@@ -13,8 +13,8 @@ void launch_time_step(cudaStream_t s, int64_t Nc, int D, const int64_t* cf_off, 
                       unsigned long long* out_bits);
 
 template <typename T>
-void launch_init_f(cudaStream_t s, int64_t Nc, int64_t M, int64_t nv, const Gas& g, const double* W,
-                   const double* ux, const double* uy, const double* uz, T* f);
+cudaError_t launch_init_f(cudaStream_t s, int64_t Nc, int64_t M, int64_t nv, const Gas& g, const double* W,
+                          const double* ux, const double* uy, const double* uz, T* f);
 
 void launch_cell(cudaStream_t s, int64_t Nc, const Gas& g, const double* W, const double* q, const int64_t* cf_off,
                  const CellFace* cf, const double* vol, const BCDev* bcs, CellPrim* cp, double* gW, int* status);

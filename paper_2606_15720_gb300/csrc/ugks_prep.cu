@@ -4,6 +4,7 @@
 // is confined to O(N_cells + N_faces) work here: primitive variables, the
 // limited least-squares gradient of W, and the interface coefficients whose
 // exp(-dt/tau) terms cancel at small dt/tau (Eq. 34-35).
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -276,31 +277,60 @@ __global__ void k_time_step(int64_t Nc, int D, const int64_t* cf_off, const Cell
 
 // ---------------------------------------------------------------------------
 // Initial distribution: discrete reduced Maxwellians of W (h = H, b = K_xi/(2 lam) H);
-// padded velocities (k >= nv) hold zero.
+// padded velocities (k >= nv) hold zero.  The per-cell factors (rho
+// (lam/pi)^(D/2), lam, U, kappa) are formed once per cell in FP64; per value
+// only the exponential remains (FP64 for FP64 storage, FP32 for FP32), so the
+// 3e9-value initialisation of the sphere workload stays off GB300's narrow
+// FP64 pipe.
 // ---------------------------------------------------------------------------
+struct InitRec {
+  double pref, lam, U[3], kap;
+};
+
+template <int D>
+__global__ void k_init_rec(int64_t Nc, Gas g, const double* W, InitRec* rec) {
+  const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (c >= Nc) return;
+  bool ok;
+  const Prim p = prim_of<D>(load5<D>(W + c * NWP), g.K, ok);
+  InitRec r;
+  r.pref = p.rho * pow(p.lam / M_PI, 0.5 * D);
+  r.lam = p.lam;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) r.U[d] = p.U[d];
+  r.kap = g.Kxi / (2.0 * p.lam);
+  rec[c] = r;
+}
+
+// grid: x over cells (one warp each), y over velocity blocks
 template <int D, typename T>
-__global__ void k_init_f(int64_t Nc, int64_t M, int64_t nv, Gas g, const double* W, const double* ux,
+__global__ void k_init_f(int64_t Nc, int64_t M, int64_t nv, int NR, const InitRec* rec, const double* ux,
                          const double* uy, const double* uz, T* f) {
-  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= M * Nc * BV) return;
-  const int lane = int(idx & 31);
-  const int64_t row = idx >> 5;
-  const int64_t c = row % Nc, m = row / Nc;
+  const int64_t c = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= Nc) return;
+  const InitRec r = rec[c];
+  for (int64_t m = blockIdx.y; m < M; m += gridDim.y) {
   const int64_t k = m * BV + lane;
-  double H = 0.0, kap = 0.0;
+  T h = T(0), b = T(0);
   if (k < nv) {
-    bool ok;
-    const Prim p = prim_of<D>(load5<D>(W + c * NWP), g.K, ok);
     const double uu[3] = {ux[k], uy[k], uz[k]};
     double c2 = 0.0;
 #pragma unroll
-    for (int d = 0; d < D; ++d) c2 += (uu[d] - p.U[d]) * (uu[d] - p.U[d]);
-    H = p.rho * pow(p.lam / M_PI, 0.5 * D) * exp(-p.lam * c2);
-    kap = g.Kxi / (2.0 * p.lam);
+    for (int d = 0; d < D; ++d) c2 += (uu[d] - r.U[d]) * (uu[d] - r.U[d]);
+    if constexpr (sizeof(T) == 8) {
+      h = T(r.pref * exp(-r.lam * c2));
+      b = T(r.kap * double(h));
+    } else {
+      const float H = float(r.pref) * expf(float(-r.lam * c2));
+      h = T(H);
+      b = T(float(r.kap) * H);
+    }
   }
-  const size_t plane = size_t(M) * Nc * BV;
-  f[size_t(m) * Nc * BV + size_t(c) * BV + lane] = T(H);
-  if (g.NR == 2) f[plane + size_t(m) * Nc * BV + size_t(c) * BV + lane] = T(kap * H);
+  const size_t plane = size_t(M) * Nc * BV, at = size_t(m) * Nc * BV + size_t(c) * BV + lane;
+  f[at] = h;
+  if (NR == 2) f[plane + at] = b;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -924,12 +954,22 @@ void launch_time_step(cudaStream_t s, int64_t Nc, int D, const int64_t* cf_off, 
 }
 
 template <typename T>
-void launch_init_f(cudaStream_t s, int64_t Nc, int64_t M, int64_t nv, const Gas& g, const double* W,
-                   const double* ux, const double* uy, const double* uz, T* f) {
-  const unsigned nb = blocks_for(M * Nc * BV, 256);
-  if (g.D == 1) k_init_f<1, T><<<nb, 256, 0, s>>>(Nc, M, nv, g, W, ux, uy, uz, f);
-  if (g.D == 2) k_init_f<2, T><<<nb, 256, 0, s>>>(Nc, M, nv, g, W, ux, uy, uz, f);
-  if (g.D == 3) k_init_f<3, T><<<nb, 256, 0, s>>>(Nc, M, nv, g, W, ux, uy, uz, f);
+cudaError_t launch_init_f(cudaStream_t s, int64_t Nc, int64_t M, int64_t nv, const Gas& g, const double* W,
+                          const double* ux, const double* uy, const double* uz, T* f) {
+  InitRec* rec = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rec), size_t(Nc) * sizeof(InitRec), s);
+  if (e != cudaSuccess) return e;
+  const unsigned nc = blocks_for(Nc, 128);
+  if (g.D == 1) k_init_rec<1><<<nc, 128, 0, s>>>(Nc, g, W, rec);
+  if (g.D == 2) k_init_rec<2><<<nc, 128, 0, s>>>(Nc, g, W, rec);
+  if (g.D == 3) k_init_rec<3><<<nc, 128, 0, s>>>(Nc, g, W, rec);
+  const dim3 grid(blocks_for(Nc * 32, 256), unsigned(std::min<int64_t>(M, 65535)));
+  if (g.D == 1) k_init_f<1, T><<<grid, 256, 0, s>>>(Nc, M, nv, g.NR, rec, ux, uy, uz, f);
+  if (g.D == 2) k_init_f<2, T><<<grid, 256, 0, s>>>(Nc, M, nv, g.NR, rec, ux, uy, uz, f);
+  if (g.D == 3) k_init_f<3, T><<<grid, 256, 0, s>>>(Nc, M, nv, g.NR, rec, ux, uy, uz, f);
+  e = cudaGetLastError();
+  const cudaError_t e2 = cudaFreeAsync(rec, s);
+  return e != cudaSuccess ? e : e2;
 }
 
 void launch_cell(cudaStream_t s, int64_t Nc, const Gas& g, const double* W, const double* q, const int64_t* cf_off,
@@ -1000,8 +1040,8 @@ void launch_residual_finalize(cudaStream_t s, int nw, int64_t Nc, const double* 
                                     const double*, const double*, const double*, const double*, double*);         \
   template void launch_init_ce<T>(cudaStream_t, int64_t, int64_t, int64_t, const Gas&, const double*,             \
                                   const double*, const double*, const double*, T*);                               \
-  template void launch_init_f<T>(cudaStream_t, int64_t, int64_t, int64_t, const Gas&, const double*,             \
-                                 const double*, const double*, const double*, T*);                              \
+  template cudaError_t launch_init_f<T>(cudaStream_t, int64_t, int64_t, int64_t, const Gas&, const double*,      \
+                                        const double*, const double*, const double*, T*);                       \
   template void launch_face<T>(cudaStream_t, int64_t, const Gas&, const double*, const double*, const double*,   \
                                const int64_t*, const int64_t*, const double*, const double*, const double*,      \
                                const double*, const BCDev*, FaceRec<T>*, void*);                                 \
