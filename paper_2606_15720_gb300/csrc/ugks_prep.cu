@@ -248,23 +248,63 @@ __device__ __forceinline__ G5 time_integrals(double dt, double tau) {
 // dt_i is min-reduced through its bit pattern (positive doubles order like
 // their unsigned 64-bit images).
 // ---------------------------------------------------------------------------
-__global__ void k_time_step(int64_t Nc, int D, const int64_t* cf_off, const CellFace* cf, const double* fnormal,
-                            const double* vol, const double* u, const double* w, int64_t nv,
-                            unsigned long long* out_bits) {
-  int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (warp >= Nc) return;
-  int64_t i = warp;
+// The largest outflow sum_f S_f max(u_k . n_f, 0) of a cell over the
+// velocities, in two passes: FP32 sums find the maximum M32; the velocities
+// whose FP32 sum is within 1e-4 of M32 (a bound far above the FP32 error of
+// these sums of non-negative terms, so they include the FP64 maximiser) are
+// summed again in FP64 in the face order of the reference definition.  This
+// keeps the 3e9 (cell, velocity) pairs of the sphere workload off GB300's
+// narrow FP64 pipe and gives the FP64 result.  One warp per cell, its faces
+// (at most 32) staged in shared memory.
+template <int D>
+__global__ void __launch_bounds__(256) k_time_step(int64_t Nc, const int64_t* cf_off, const CellFace* cf,
+                                                    const double* fnormal, const double* vol, const double* u,
+                                                    const double* w, int64_t nv, unsigned long long* out_bits) {
+  __shared__ double sn[8][32][3], sa[8][32];
+  __shared__ float fn[8][32][3], fa[8][32];
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (i >= Nc) return;
+  const int64_t e0 = cf_off[i];
+  const int nf = int(cf_off[i + 1] - e0);
+  if (lane < nf) {
+    const CellFace& c = cf[e0 + lane];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      sn[wi][lane][d] = fnormal[c.face * 3 + d] * c.sign;
+      fn[wi][lane][d] = float(sn[wi][lane][d]);
+    }
+    sa[wi][lane] = c.area;
+    fa[wi][lane] = float(c.area);
+  }
+  __syncwarp();
+  auto sum32 = [&](int64_t k) {
+    float uk[3];
+#pragma unroll
+    for (int d = 0; d < D; ++d) uk[d] = float(u[k * D + d]);
+    float s = 0.f;
+    for (int e = 0; e < nf; ++e) {
+      float un = 0.f;
+#pragma unroll
+      for (int d = 0; d < D; ++d) un = fmaf(uk[d], fn[wi][e][d], un);
+      s = fmaf(fa[wi][e], fmaxf(un, 0.f), s);
+    }
+    return s;
+  };
+  float m32 = 0.f;
+  for (int64_t k = lane; k < nv; k += 32)
+    if (w[k] != 0.0) m32 = fmaxf(m32, sum32(k));
+  for (int o = 16; o > 0; o >>= 1) m32 = fmaxf(m32, __shfl_xor_sync(0xffffffffu, m32, o));
+  const float cut = m32 * (1.f - 1e-4f);
   double worst = 0.0;
   for (int64_t k = lane; k < nv; k += 32) {
-    if (w[k] == 0.0) continue;
+    if (w[k] == 0.0 || sum32(k) < cut) continue;
     double s = 0.0;
-    for (int64_t e = cf_off[i]; e < cf_off[i + 1]; ++e) {
-      const CellFace& c = cf[e];
+    for (int e = 0; e < nf; ++e) {
       double un = 0.0;
-      for (int d = 0; d < D; ++d) un += u[k * D + d] * fnormal[c.face * 3 + d];
-      un *= c.sign;
-      if (un > 0.0) s += c.area * un;
+#pragma unroll
+      for (int d = 0; d < D; ++d) un += u[k * D + d] * sn[wi][e][d];
+      if (un > 0.0) s += sa[wi][e] * un;
     }
     worst = fmax(worst, s);
   }
@@ -950,7 +990,10 @@ static inline unsigned blocks_for(int64_t n, int threads) { return unsigned((n +
 void launch_time_step(cudaStream_t s, int64_t Nc, int D, const int64_t* cf_off, const CellFace* cf,
                       const double* fnormal, const double* vol, const double* u, const double* w, int64_t nv,
                       unsigned long long* out_bits) {
-  k_time_step<<<blocks_for(Nc * 32, 256), 256, 0, s>>>(Nc, D, cf_off, cf, fnormal, vol, u, w, nv, out_bits);
+  const unsigned nb = blocks_for(Nc * 32, 256);
+  if (D == 1) k_time_step<1><<<nb, 256, 0, s>>>(Nc, cf_off, cf, fnormal, vol, u, w, nv, out_bits);
+  if (D == 2) k_time_step<2><<<nb, 256, 0, s>>>(Nc, cf_off, cf, fnormal, vol, u, w, nv, out_bits);
+  if (D == 3) k_time_step<3><<<nb, 256, 0, s>>>(Nc, cf_off, cf, fnormal, vol, u, w, nv, out_bits);
 }
 
 template <typename T>

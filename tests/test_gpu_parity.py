@@ -432,3 +432,22 @@ def test_moments13_and_chapman_enskog_start_match_oracle(U, name, storage, tol):
     np.testing.assert_allclose(W1, Wc, rtol=1e-13)
     Wo2, _, _, _ = O.run(mesh, grid, gas, Wc, fo_ce, 1, dt=dt)
     assert w_err(W2, Wo2) <= tol, w_err(W2, Wo2)
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-11), ("f32", 1e-5)])
+@pytest.mark.parametrize("name", ["cavity_shakhov", "sphere_tet", "cylinder_tri_K2"])
+def test_heat_flux_of_ugks_moments_matches_oracle(U, name, storage, tol):
+    """ugks_moments' q (Eq. 13) of the state after two steps against the
+    oracle's heat flux of the GPU's own f (h, b read back), per cell, relative
+    to the largest |q| of the case."""
+    mesh, grid, gas, prim = CASES[name]()
+    W0 = I.prim_to_conservative(prim, mesh.dim, gas.K)
+    with U.Solver(mesh, grid, gas, W0, storage=storage) as s:
+        s.step(2)
+        W, q = s.moments(with_q=True)
+        f = s.get_f(np.arange(mesh.n_cells))               # [cell, r, k]
+    qo = np.array([O.heat_flux(mesh.dim, gas.K, grid, f[i, 0], f[i, 1] if f.shape[1] == 2 else None, W[i])
+                   for i in range(mesh.n_cells)])
+    scale = np.abs(qo).max()
+    assert scale > 0
+    assert np.abs(q - qo).max() <= tol * scale
