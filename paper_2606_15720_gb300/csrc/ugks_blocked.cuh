@@ -386,24 +386,6 @@ __device__ __forceinline__ void flux_prefetch(const BlockedArgs<T>& a, int f, un
 // block the flux kernel kept that pipe 21 % busy, and ran 4 % slower).
 // k_bwall turns the pairs into doubles after the last block.  FP64 sweeps
 // add in double.
-// (hi, lo) + v for an unevaluated float pair: two-sum, then renormalise.
-__device__ __forceinline__ float2 pair_add(float2 p, float v) {
-  const float s = p.x + v;
-  const float bp = s - p.x;
-  const float e = (p.x - (s - bp)) + (v - bp);
-  const float lo = p.y + e;
-  const float hi = s + lo;
-  return make_float2(hi, lo - (hi - s));
-}
-// (hi, lo) + (hi, lo)
-__device__ __forceinline__ float2 pair_add(float2 p, float2 q) {
-  const float s = p.x + q.x;
-  const float bp = s - p.x;
-  const float e = (p.x - (s - bp)) + (q.x - bp) + (p.y + q.y);
-  const float hi = s + e;
-  return make_float2(hi, e - (hi - s));
-}
-
 template <typename T>
 __device__ __forceinline__ void facc_add(double* dst, const double* prev, bool first, T v) {
   if constexpr (sizeof(T) == 4) {

@@ -484,8 +484,10 @@ ugks_status init_state_typed(ugks_ctx* ctx) {
   }
   CUDA_TRY(ctx, launch_init_f<T>(ctx->stream, ctx->Nc, ctx->M, ctx->nv, ctx->gas, ctx->d_W[0], ctx->d_ux,
                                  ctx->d_uy, ctx->d_uz, static_cast<T*>(ctx->d_f[0])));
+  // q of f^0 (FP32 values: FP32 terms in float-pair sums over the context's velocity records)
   launch_moments<T>(ctx->stream, ctx->Nc, ctx->M, ctx->gas, static_cast<const T*>(ctx->d_f[0]), ctx->d_W[0],
-                    ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp, ctx->d_q[0], nullptr);
+                    ctx->d_ux, ctx->d_uy, ctx->d_uz, ctx->d_wp, ctx->d_q[0], nullptr,
+                    sizeof(T) == 4 ? ctx->d_velT : nullptr);
   CUDA_TRY(ctx, cudaGetLastError());
   return UGKS_OK;
 }

@@ -85,5 +85,26 @@ __device__ __forceinline__ double fast_div<double>(double a, double b) {
   return a / b;
 }
 
+// Unevaluated float pairs hi + lo (Knuth's two-sum, then a fast
+// renormalisation): sums of many FP32 terms to ~2^-44 relative without FP64
+// instructions, which GB300 executes at a small fraction of its FP32 rate.
+// (hi, lo) + v:
+__device__ __forceinline__ float2 pair_add(float2 p, float v) {
+  const float s = p.x + v;
+  const float bp = s - p.x;
+  const float e = (p.x - (s - bp)) + (v - bp);
+  const float lo = p.y + e;
+  const float hi = s + lo;
+  return make_float2(hi, lo - (hi - s));
+}
+// (hi, lo) + (hi, lo):
+__device__ __forceinline__ float2 pair_add(float2 p, float2 q) {
+  const float s = p.x + q.x;
+  const float bp = s - p.x;
+  const float e = (p.x - (s - bp)) + (q.x - bp) + (p.y + q.y);
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+
 }  // namespace
 }  // namespace ugks

@@ -25,9 +25,11 @@ void launch_face(cudaStream_t s, int64_t Nf, const Gas& g, const double* W, cons
                  const double* fshift, const double* xc, const BCDev* bcs, FaceRec<T>* rec, void* poly);
 
 template <typename T>
+// vel4: the context's FP32 velocity records (x, y, z, weight) for FP32
+// values (then the sums run in FP32 pairs), or NULL (FP64 sums)
 void launch_moments(cudaStream_t s, int64_t Nc, int64_t M, const Gas& g, const T* f, const double* W,
                     const double* ux, const double* uy, const double* uz, const double* w, double* q_out,
-                    double* Wf_out);
+                    double* Wf_out, const void* vel4 = nullptr);
 
 template <typename T>
 void launch_gather_f(cudaStream_t s, int64_t Nc, int64_t M, int NR, int64_t nv, const T* f, const int64_t* sel,

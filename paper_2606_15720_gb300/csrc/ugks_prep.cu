@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "ugks_device.cuh"
 #include "ugks_internal.cuh"
 #include "ugks_kernels.cuh"
 
@@ -783,12 +784,67 @@ void launch_surface(cudaStream_t s, int64_t nwall, int D, double dt, const int64
 // ---------------------------------------------------------------------------
 template <int D, typename T>
 __global__ void k_moments(int64_t Nc, int64_t M, Gas g, const T* f, const double* W, const double* ux,
-                          const double* uy, const double* uz, const double* w, double* q_out, double* Wf_out) {
+                          const double* uy, const double* uz, const double* w, const Vel4<float>* v4,
+                          double* q_out, double* Wf_out) {
   const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= Nc) return;
   bool ok;
   const Prim p = prim_of<D>(load5<D>(W + i * NWP), g.K, ok);
+  if constexpr (sizeof(T) == 4) {
+    if (v4) {
+      // FP32 values: FP32 terms summed as float pairs, one FP64 reduction per cell
+      float U[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) U[d] = float(p.U[d]);
+      const float2 z = make_float2(0.f, 0.f);
+      float2 qa[3] = {z, z, z}, ma[3] = {z, z, z}, m0 = z, mE = z;
+      const size_t plane = size_t(M) * Nc * BV;
+      for (int64_t m = 0; m < M; ++m) {
+        const Vel4<float> vq = v4[m * BV + lane];
+        const size_t at = size_t(m) * Nc * BV + size_t(i) * BV + lane;
+        const float h = float(f[at]);
+        const float b = g.NR == 2 ? float(f[plane + at]) : 0.f;
+        const float uu[3] = {vq.x, vq.y, vq.z};
+        float c[3], c2 = 0.f, u2 = 0.f;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          c[d] = uu[d] - U[d];
+          c2 = fmaf(c[d], c[d], c2);
+          u2 = fmaf(uu[d], uu[d], u2);
+        }
+        const float e = 0.5f * vq.w * fmaf(c2, h, b);
+#pragma unroll
+        for (int d = 0; d < D; ++d) qa[d] = pair_add(qa[d], c[d] * e);
+        if (Wf_out) {
+          const float wh = vq.w * h;
+          m0 = pair_add(m0, wh);
+#pragma unroll
+          for (int d = 0; d < D; ++d) ma[d] = pair_add(ma[d], wh * uu[d]);
+          mE = pair_add(mE, 0.5f * vq.w * fmaf(u2, h, b));
+        }
+      }
+      double qd[3], md[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        qd[d] = d < D ? warp_sum(double(qa[d].x) + double(qa[d].y)) : 0.0;
+        md[d] = (Wf_out && d < D) ? warp_sum(double(ma[d].x) + double(ma[d].y)) : 0.0;
+      }
+      const double m0d = Wf_out ? warp_sum(double(m0.x) + double(m0.y)) : 0.0;
+      const double mEd = Wf_out ? warp_sum(double(mE.x) + double(mE.y)) : 0.0;
+      if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) q_out[i * 3 + d] = qd[d];
+        if (Wf_out) {
+          Wf_out[i * NWP + 0] = m0d;
+#pragma unroll
+          for (int d = 0; d < D; ++d) Wf_out[i * NWP + 1 + d] = md[d];
+          Wf_out[i * NWP + D + 1] = mEd;
+        }
+      }
+      return;
+    }
+  }
   double qa[3] = {0.0, 0.0, 0.0}, ma[3] = {0.0, 0.0, 0.0}, m0 = 0.0, mE = 0.0;
   const size_t plane = size_t(M) * Nc * BV;
   for (int64_t m = 0; m < M; ++m) {
@@ -1036,11 +1092,12 @@ void launch_face(cudaStream_t s, int64_t Nf, const Gas& g, const double* W, cons
 template <typename T>
 void launch_moments(cudaStream_t s, int64_t Nc, int64_t M, const Gas& g, const T* f, const double* W,
                     const double* ux, const double* uy, const double* uz, const double* w, double* q_out,
-                    double* Wf_out) {
+                    double* Wf_out, const void* vel4) {
   const unsigned nb = blocks_for(Nc * 32, 256);
-  if (g.D == 1) k_moments<1, T><<<nb, 256, 0, s>>>(Nc, M, g, f, W, ux, uy, uz, w, q_out, Wf_out);
-  if (g.D == 2) k_moments<2, T><<<nb, 256, 0, s>>>(Nc, M, g, f, W, ux, uy, uz, w, q_out, Wf_out);
-  if (g.D == 3) k_moments<3, T><<<nb, 256, 0, s>>>(Nc, M, g, f, W, ux, uy, uz, w, q_out, Wf_out);
+  const Vel4<float>* v4 = sizeof(T) == 4 ? static_cast<const Vel4<float>*>(vel4) : nullptr;
+  if (g.D == 1) k_moments<1, T><<<nb, 256, 0, s>>>(Nc, M, g, f, W, ux, uy, uz, w, v4, q_out, Wf_out);
+  if (g.D == 2) k_moments<2, T><<<nb, 256, 0, s>>>(Nc, M, g, f, W, ux, uy, uz, w, v4, q_out, Wf_out);
+  if (g.D == 3) k_moments<3, T><<<nb, 256, 0, s>>>(Nc, M, g, f, W, ux, uy, uz, w, v4, q_out, Wf_out);
 }
 
 template <typename T>
@@ -1089,7 +1146,8 @@ void launch_residual_finalize(cudaStream_t s, int nw, int64_t Nc, const double* 
                                const int64_t*, const int64_t*, const double*, const double*, const double*,      \
                                const double*, const BCDev*, FaceRec<T>*, void*);                                 \
   template void launch_moments<T>(cudaStream_t, int64_t, int64_t, const Gas&, const T*, const double*,           \
-                                  const double*, const double*, const double*, const double*, double*, double*); \
+                                  const double*, const double*, const double*, const double*, double*, double*,  \
+                                  const void*);                                                                 \
   template void launch_gather_f<T>(cudaStream_t, int64_t, int64_t, int, int64_t, const T*, const int64_t*,       \
                                    int64_t, double*);                                                            \
   template void launch_scatter_f<T>(cudaStream_t, int64_t, int64_t, int, int64_t, const double*, const int64_t*, \
