@@ -58,6 +58,18 @@ def dist_env():
     return rank, world, local
 
 
+def replica_timing(local_ms, steps, dof_per_replica, world, dist=None, device="cuda"):
+    """Whole-job timing of N independent replicas: the slowest rank's time for
+    the timed steps (max over ranks), and the DOF updates of all ranks per
+    second of it.  Returns (ms per step, DOF/s)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / steps
+    return ms_per_step, dof_per_replica * world / (ms_per_step * 1e-3)
+
+
 N_SM = 152            # GB300 multiprocessors
 FP32_LANES = 128      # FP32 lanes per multiprocessor
 
@@ -361,12 +373,7 @@ def run_gpu(args):
                    "max_Cp": float(np.max(scoef[:, 0])), "max_Ch": float(np.max(scoef[:, 2])),
                    "max_Ct": float(np.max(scoef[:, 1]))}
         solver.close()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    ms_per_step = ms_max / args.steps
-    value = dof * world / (ms_per_step * 1e-3)
+    ms_per_step, value = replica_timing(ms, args.steps, dof, world, dist, "cuda")
 
     roofline, kernels, step_views = rooflines(stats, mesh, grid, dof, args.steps,
                                               BYTES_STAGE if args.storage == "f32" else BYTES_STAGE_SCALED)
