@@ -291,6 +291,13 @@ ugks_status ugks_batch_tuning(ugks_batch *batch, int32_t i, int32_t *block_veloc
 
 ugks_status ugks_batch_destroy(ugks_batch *batch);
 
+/* The same two calls under the names of the boundary's first proposal:
+ * ugks_create_batch = ugks_batch_create, ugks_step_batch = ugks_batch_step. */
+ugks_status ugks_create_batch(int32_t n, const ugks_mesh *const *meshes, const ugks_vgrid *const *vgrids,
+                              const ugks_params *params, const double *const *W_init, void *cuda_stream,
+                              ugks_batch **out);
+ugks_status ugks_step_batch(ugks_batch *batch, int32_t n_steps);
+
 /* ---- Learned warm start ----
  * The paper has no learned component; its conclusion lists steady-state
  * acceleration as future work.  This interface addition starts steady solves

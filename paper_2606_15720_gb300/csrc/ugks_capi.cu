@@ -1827,6 +1827,14 @@ ugks_status ugks_batch_tuning(ugks_batch* b, int32_t i, int32_t* block_velocitie
   return UGKS_OK;
 }
 
+ugks_status ugks_create_batch(int32_t n, const ugks_mesh* const* meshes, const ugks_vgrid* const* vgrids,
+                              const ugks_params* params, const double* const* W_init, void* cuda_stream,
+                              ugks_batch** out) {
+  return ugks_batch_create(n, meshes, vgrids, params, W_init, cuda_stream, out);
+}
+
+ugks_status ugks_step_batch(ugks_batch* b, int32_t n_steps) { return ugks_batch_step(b, n_steps); }
+
 ugks_status ugks_batch_destroy(ugks_batch* b) {
   if (!b) return UGKS_OK;
   if (b->stream) cudaStreamSynchronize(b->stream);
