@@ -209,11 +209,12 @@ __global__ void k_wall_distance(int64_t Nc, int dim, const double* xc, int64_t n
 
 // Batch input and targets from the data set by index, normalised:
 // x0 = (x - shift) / scale as BF16 (zero padding), t = (y - shift) / scale.
-__global__ void k_gather(int nb, int nvalid, const int64_t* idx, const float* X, int n_in, int in_pad, const float* Y,
-                         int n_out, const float* in_shift, const float* in_scale, const float* out_shift,
-                         const float* out_scale, bf16* x0, float* t) {
+__global__ void k_gather(int nb, int nvalid, const int64_t* idx, const int64_t* cursor, const float* X, int n_in,
+                         int in_pad, const float* Y, int n_out, const float* in_shift, const float* in_scale,
+                         const float* out_shift, const float* out_scale, bf16* x0, float* t) {
   const int s = blockIdx.x;
   if (s >= nb) return;
+  if (cursor) idx += *cursor;  // training: the batch's offset in the shuffled order
   for (int j = threadIdx.x; j < in_pad; j += blockDim.x) {
     float v = 0.f;
     if (s < nvalid && j < n_in) v = (X[idx[s] * n_in + j] - in_shift[j]) / in_scale[j];
@@ -251,11 +252,13 @@ __global__ void k_mse(int nb, int nvalid, int n_out, int out_pad, const float* y
   if (threadIdx.x == 0) atomicAdd(loss, part[0] / (double(nvalid) * n_out));
 }
 
-// Adam on FP32 master parameters (bias-corrected); refreshes the BF16 weights.
-__global__ void k_adam(int64_t n, float* p, const float* gr, float* m, float* v, bf16* pb, float lr, float c1,
-                       float c2) {
+// Adam on FP32 master parameters (bias-corrected, step t = *step + 1);
+// refreshes the BF16 weights.
+__global__ void k_adam(int64_t n, float* p, const float* gr, float* m, float* v, bf16* pb, float lr, const int* step) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const float t = float(*step + 1);
+  const float c1 = 1.f - powf(0.9f, t), c2 = 1.f - powf(0.999f, t);
   const float g = gr[i];
   const float mm = 0.9f * m[i] + 0.1f * g;
   const float vv = 0.999f * v[i] + 0.001f * g * g;
@@ -264,6 +267,14 @@ __global__ void k_adam(int64_t n, float* p, const float* gr, float* m, float* v,
   const float w = p[i] - lr * (mm / c1) / (sqrtf(vv / c2) + 1e-8f);
   p[i] = w;
   if (pb) pb[i] = __float2bfloat16_rn(w);
+}
+
+// after a training step: next batch, next Adam step
+__global__ void k_train_advance(int64_t* cursor, int64_t batch, int* step) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *cursor += batch;
+    *step += 1;
+  }
 }
 
 __global__ void k_to_bf16(int64_t n, const float* a, bf16* b) {
@@ -304,7 +315,12 @@ struct ugks_mlp {
   int64_t* didx = nullptr;
   float *dX = nullptr, *dY = nullptr;
   int64_t data_cap = 0;
-  int adam_step = 0;
+  int* d_step = nullptr;          // Adam steps taken (device)
+  int64_t* d_cursor = nullptr;    // offset of the next training batch in the shuffled order (device)
+  cudaGraph_t train_graph = nullptr;
+  cudaGraphExec_t train_exec = nullptr;  // one full training step (gather .. Adam), replayed per batch
+  int train_batch = 0;
+  float train_lr = 0.f;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<void*> allocs;
@@ -426,6 +442,14 @@ void backward(ugks_mlp* n, int nbatch) {
   }
 }
 
+void drop_train_graph(ugks_mlp* n) {
+  if (n->train_exec) cudaGraphExecDestroy(n->train_exec);
+  if (n->train_graph) cudaGraphDestroy(n->train_graph);
+  n->train_exec = nullptr;
+  n->train_graph = nullptr;
+  n->train_batch = 0;
+}
+
 void release(ugks_mlp* n, void* p) {
   if (!p) return;
   cudaStreamSynchronize(n->stream);
@@ -435,6 +459,7 @@ void release(ugks_mlp* n, void* p) {
 
 ugks_status upload_data(ugks_mlp* n, const float* X, const float* Y, int64_t count) {
   if (count > n->data_cap) {
+    drop_train_graph(n);  // it holds the old data pointers
     // grow the device copy of the data set
     release(n, n->dX);
     release(n, n->dY);
@@ -454,9 +479,9 @@ ugks_status upload_data(ugks_mlp* n, const float* X, const float* Y, int64_t cou
   return UGKS_OK;
 }
 
-void gather(ugks_mlp* n, int nb, int nvalid, const int64_t* idx, bool targets) {
+void gather(ugks_mlp* n, int nb, int nvalid, const int64_t* idx, bool targets, const int64_t* cursor = nullptr) {
   const float* nm = n->norm;
-  k_gather<<<unsigned(nb), 64, 0, n->stream>>>(nb, nvalid, idx, n->dX, n->n_in, n->din[0], n->dY, n->n_out, nm,
+  k_gather<<<unsigned(nb), 64, 0, n->stream>>>(nb, nvalid, idx, cursor, n->dX, n->n_in, n->din[0], n->dY, n->n_out, nm,
                                                 nm + n->n_in, nm + 2 * n->n_in, nm + 2 * n->n_in + n->n_out,
                                                 n->actb[0], targets ? n->tgt : nullptr);
 }
@@ -523,6 +548,8 @@ ugks_status ugks_mlp_create(int32_t n_in, int32_t n_out, int32_t width, int32_t 
   CREATE_TRY(malloc_n(n, &n->norm, size_t(2 * n_in + 2 * n_out)));
   CREATE_TRY(malloc_n(n, &n->tgt, size_t(n->max_batch) * n_out));
   CREATE_TRY(malloc_n(n, &n->dloss, 1));
+  CREATE_TRY(malloc_n(n, &n->d_step, 1));
+  CREATE_TRY(malloc_n(n, &n->d_cursor, 1));
   n->actf.assign(n->L + 1, nullptr);
   n->actb.assign(n->L + 1, nullptr);
   n->dzf.assign(n->L, nullptr);
@@ -622,7 +649,7 @@ ugks_status ugks_mlp_set_params(ugks_mlp* n, const float* params) {
   MLP_TRY(n, cudaMemsetAsync(n->vW, 0, n->nW * sizeof(float), n->stream));
   MLP_TRY(n, cudaMemsetAsync(n->mb, 0, n->nb * sizeof(float), n->stream));
   MLP_TRY(n, cudaMemsetAsync(n->vb, 0, n->nb * sizeof(float), n->stream));
-  n->adam_step = 0;
+  MLP_TRY(n, cudaMemsetAsync(n->d_step, 0, sizeof(int), n->stream));
   MLP_TRY(n, cudaStreamSynchronize(n->stream));
   return UGKS_OK;
 }
@@ -655,6 +682,33 @@ ugks_status ugks_mlp_train(ugks_mlp* n, const float* X, const float* Y, int64_t 
     return mfail(n, UGKS_ERR_INVALID_ARGUMENT, "need n >= 1, epochs >= 0, 1 <= batch <= %d, lr > 0", n->max_batch);
   ugks_status st = upload_data(n, X, Y, count);
   if (st != UGKS_OK) return st;
+  // one training step: batch at *d_cursor of the shuffled order, forward,
+  // loss, backward, Adam at step *d_step + 1, then both advance
+  auto train_step = [&](int nvalid) {
+    const int nb = (nvalid + 63) / 64 * 64;
+    gather(n, nb, nvalid, n->didx, true, n->d_cursor);
+    forward(n, nb);
+    loss_grad(n, nb, nvalid);
+    backward(n, nb);
+    k_adam<<<unsigned((n->nW + 255) / 256), 256, 0, n->stream>>>(n->nW, n->W, n->gW, n->mW, n->vW, n->Wb, lr,
+                                                                 n->d_step);
+    k_adam<<<unsigned((n->nb + 255) / 256), 256, 0, n->stream>>>(n->nb, n->b, n->gb, n->mb, n->vb, nullptr, lr,
+                                                                 n->d_step);
+    k_train_advance<<<1, 32, 0, n->stream>>>(n->d_cursor, nvalid, n->d_step);
+  };
+  // full batches replay one captured CUDA graph of the step (~30 launches)
+  if (n->train_exec && (n->train_batch != batch || n->train_lr != lr)) drop_train_graph(n);
+  if (!n->train_exec && count >= batch) {
+    MLP_TRY(n, cudaStreamBeginCapture(n->stream, cudaStreamCaptureModeThreadLocal));
+    train_step(batch);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(n->stream, &g);
+    if (ce != cudaSuccess) return mfail(n, UGKS_ERR_CUDA, "training graph capture: %s", cudaGetErrorString(ce));
+    n->train_graph = g;
+    MLP_TRY(n, cudaGraphInstantiate(&n->train_exec, g, 0));
+    n->train_batch = batch;
+    n->train_lr = lr;
+  }
   std::vector<int64_t> perm(count);
   uint64_t rs = seed;
   double last = 0.0;
@@ -663,23 +717,19 @@ ugks_status ugks_mlp_train(ugks_mlp* n, const float* X, const float* Y, int64_t 
     for (int64_t i = count - 1; i > 0; --i) std::swap(perm[i], perm[int64_t(splitmix(rs) % uint64_t(i + 1))]);
     MLP_TRY(n, cudaMemcpyAsync(n->didx, perm.data(), count * sizeof(int64_t), cudaMemcpyHostToDevice, n->stream));
     MLP_TRY(n, cudaMemsetAsync(n->dloss, 0, sizeof(double), n->stream));
+    MLP_TRY(n, cudaMemsetAsync(n->d_cursor, 0, sizeof(int64_t), n->stream));
     int64_t nbatches = 0;
     for (int64_t s0 = 0; s0 < count; s0 += batch, ++nbatches) {
       const int nvalid = int(std::min<int64_t>(batch, count - s0));
-      const int nb = (nvalid + 63) / 64 * 64;
-      gather(n, nb, nvalid, n->didx + s0, true);
-      forward(n, nb);
-      loss_grad(n, nb, nvalid);
-      backward(n, nb);
-      ++n->adam_step;
-      const float c1 = 1.f - std::pow(0.9f, float(n->adam_step)), c2 = 1.f - std::pow(0.999f, float(n->adam_step));
-      k_adam<<<unsigned((n->nW + 255) / 256), 256, 0, n->stream>>>(n->nW, n->W, n->gW, n->mW, n->vW, n->Wb, lr, c1, c2);
-      k_adam<<<unsigned((n->nb + 255) / 256), 256, 0, n->stream>>>(n->nb, n->b, n->gb, n->mb, n->vb, nullptr, lr, c1, c2);
+      if (nvalid == batch)
+        MLP_TRY(n, cudaGraphLaunch(n->train_exec, n->stream));
+      else
+        train_step(nvalid);
     }
     MLP_TRY(n, cudaGetLastError());
     double acc = 0.0;
     MLP_TRY(n, cudaMemcpyAsync(&acc, n->dloss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
-    MLP_TRY(n, cudaStreamSynchronize(n->stream));
+    MLP_TRY(n, cudaStreamSynchronize(n->stream));  // perm is rewritten next epoch
     last = acc / double(nbatches);  // mean over the epoch's batches
     if (!std::isfinite(last)) return mfail(n, UGKS_ERR_NONFINITE, "training diverged at epoch %d", ep);
   }
@@ -842,6 +892,7 @@ ugks_status ugks_mlp_warm_start(ugks_mlp* n, ugks_ctx* ctx, const ugks_mesh* mes
 ugks_status ugks_mlp_destroy(ugks_mlp* n) {
   if (!n) return UGKS_OK;
   if (n->stream) cudaStreamSynchronize(n->stream);
+  drop_train_graph(n);
   for (void* p : n->allocs) cudaFree(p);
   if (n->own_stream && n->stream) cudaStreamDestroy(n->stream);
   delete n;
