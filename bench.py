@@ -417,7 +417,8 @@ def run_gpu(args):
             "data": "synthetic",
             "config": {"workload": workload, "n_cells": mesh.n_cells, "n_faces": mesh.n_faces, "n_v": grid.n_v,
                        "n_reduced": n_reduced, "dof_per_step": dof, "parallelism": f"replicas x{world}",
-                       "sweep": args.sweep, "block_velocities": args.block_velocities, "storage": args.storage,
+                       "sweep": args.sweep, "storage": args.storage,
+                       "block_velocities": args.block_velocities or (256 if mesh.dim == 3 and gas.K == 0 else 128),
                        "l2": "inputs larger than L2 (two %.1f GB distribution buffers)" % (dof * 4 / 1e9),
                        "state_after": {"residual": [float(x) for x in res],
                                        "finite": bool(np.all(np.isfinite(W_end)))}},
