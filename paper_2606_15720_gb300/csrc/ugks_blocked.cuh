@@ -542,7 +542,7 @@ __device__ __forceinline__ void flux_face(const BlockedArgs<T>& a, const int f, 
 }
 
 template <int D, int NR, int VB, typename T>
-__global__ void __launch_bounds__(kBlockedThreads) k_bflux(const BlockedArgs<T> a, const int64_t m0,
+__global__ void __launch_bounds__(kBlockedThreads, VB == 8 ? 3 : 1) k_bflux(const BlockedArgs<T> a, const int64_t m0,
                                                            const int first) {
   using S = FluxStage<D, NR, VB, T>;
   extern __shared__ __align__(16) unsigned char flux_smem[];
