@@ -86,8 +86,11 @@ def load_peaks():
     return 6800.0, "fallback", N_SM * FP32_LANES * 2 * 2070e6 / 1e12
 
 
-# Algorithmic work of the blocked sweep per velocity (FP32 operations, FMA = 2;
-# derivation in the design doc).  inc = faces per cell (4 on tetrahedra).
+# Algorithmic work of the blocked sweep per velocity (FP32 operations, FMA = 2,
+# counted term by term from the formulas each kernel evaluates: gradient 9
+# and limiter 17 per face, upwind face value 15 per face, 17 per velocity in
+# the reconstruction; 69 per face-velocity in the flux; 27 + 2 per face in the
+# first stage; 34 in the second).  inc = faces per cell (4 on tetrahedra).
 def flops_recon(inc):       # per cell-velocity: LSQ gradient, limiter, upwind face values
     return 17 + 41 * inc
 
