@@ -87,12 +87,13 @@ def load_peaks():
 
 
 # Algorithmic work of the blocked sweep per velocity (FP32 operations, FMA = 2,
-# counted term by term from the formulas each kernel evaluates: gradient 9
-# and limiter 17 per face, upwind face value 15 per face, 17 per velocity in
-# the reconstruction; 69 per face-velocity in the flux; 27 + 2 per face in the
+# counted term by term from the formulas each kernel evaluates: gradient 9,
+# limiter increment 7 and upwind face value 15 per face, 41 per velocity (two
+# limiter evaluations, the limiter constants, clipping, scaling, u.g) in the
+# reconstruction; 69 per face-velocity in the flux; 27 + 2 per face in the
 # first stage; 34 in the second).  inc = faces per cell (4 on tetrahedra).
 def flops_recon(inc):       # per cell-velocity: LSQ gradient, limiter, upwind face values
-    return 17 + 41 * inc
+    return 41 + 31 * inc
 
 
 FLOPS_FLUX = 69             # per face-velocity: upwind pick, g0 P(c), flux, moments
