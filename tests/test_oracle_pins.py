@@ -714,3 +714,24 @@ def test_mlp_reference_adam_step_on_a_quadratic():
         np.testing.assert_allclose(W2 - W, -1e-3 * gW / (np.abs(gW) + 1e-8), rtol=1e-6, atol=1e-12)
         np.testing.assert_allclose(b2 - b, -1e-3 * gb / (np.abs(gb) + 1e-8), rtol=1e-6, atol=1e-12)
     assert state[0] == 1
+
+
+@pytest.mark.slow
+def test_steady_state_does_not_depend_on_the_start():
+    """Reading R3 (walls as zero-gradient ghosts in the least-squares matrix):
+    two different starts of a small cylinder flow (Ma 1.9, Kn 0.3; 12 of its
+    wall cells would extrapolate with negative self-weights, down to -2.8, if
+    walls were left out of the matrix) reach the same state.  With walls left
+    out the two starts settled on states 1e-3 apart near the wall."""
+    from paper_2606_15720_gb300 import warmstart as WS
+    mesh, grid, gas, W0 = WS.cylinder_case(1.9, 0.3, 120, 12, seed=7)
+    prim = I.smooth_random_primitives(mesh, seed=3, amp=0.15, U0=(mesh.bc[1].u[0], 0, 0), length=(12, 10))
+    W1 = I.prim_to_conservative(prim, 2, 0)
+    ends = []
+    for Wi in (W0, W1):
+        W, f = Wi, O.initial_f(mesh, grid, Wi, 0)
+        W, f, dt, diag = O.run(mesh, grid, gas, W, f, 10000)
+        assert diag[-1, 0] < 1e-7
+        ends.append(W)
+    diff = np.abs(ends[1] - ends[0]).max(axis=0) / np.abs(ends[0]).max(axis=0)
+    assert diff.max() < 2e-5, diff
