@@ -601,20 +601,10 @@ def run_warm_report(args):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU (the CUDA library has no CPU path)")
     from paper_2606_15720_gb300 import warmstart as WS
-    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
-    if args.warm_family == "wide":
-        # Ma 2-4 (the batch workload's range), Kn 0.02-0.5, 32^2 velocities
-        train = [(ma, kn) for ma in (2.0, 2.67, 3.33, 4.0) for kn in (0.02, 0.1, 0.5)]
-        rng = np.random.default_rng(6)
-        held = [(round(float(rng.uniform(2.2, 3.8)), 3), round(float(10 ** rng.uniform(math.log10(0.03), math.log10(0.4))), 4))
-                for _ in range(8)]
-        res = WS.experiment(train, held, cells=2000, nvx=32, ref_tol=1e-8, log=log)
-        workload = "cylinder_warmstart_ma2-4_kn0.02-0.5_tri2k_v32sq_shakhov_fp32"
-    else:
-        res = WS.experiment(WARM_TRAIN, warm_held_out(), cells=2000, nvx=28, ref_tol=1e-8, log=log)
-        workload = "cylinder_warmstart_ma1.5-3_kn0.05-0.5_tri2k_v28sq_shakhov_fp32"
+    res = WS.experiment(WARM_TRAIN, warm_held_out(), cells=2000, nvx=28, ref_tol=1e-8,
+                        log=lambda m: print(m, file=sys.stderr, flush=True))
     ratios = [c["time_ratio"] for c in res["cases"] if "time_ratio" in c]
-    res["workload"] = workload
+    res["workload"] = "cylinder_warmstart_ma1.5-3_kn0.05-0.5_tri2k_v28sq_shakhov_fp32"
     res["metric"] = "time_to_residual_1e-6_speedup"
     res["value"] = float(np.exp(np.mean(np.log(ratios)))) if ratios else None
     res["unit"] = "x (geometric mean over held-out cases, freestream seconds / warm-start seconds)"
@@ -640,9 +630,6 @@ def main():
                     help="mixed: per-field error of FP32/FP16/BF16 storage vs the oracle at 1e2 and 1e3 steps; "
                          "batch: 64 uneven cylinder cases in one CUDA graph with the block-size autotuner; "
                          "warmstart: time to steady residual 1e-6 from the learned warm start vs the freestream")
-    ap.add_argument("--warm-family", default="default", choices=["default", "wide"],
-                    help="warmstart report: default = Ma 1.5-3, Kn 0.05-0.5 (12 training, 16 held-out cases); "
-                         "wide = Ma 2-4, Kn 0.02-0.5 (12 training, 8 held-out cases)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
