@@ -913,7 +913,6 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
   ctx->vb = p->block_velocities > 0 ? p->block_velocities / BV : (vb8 ? 8 : 4);
   while (ctx->vb > ctx->M) ctx->vb /= 2;
   ctx->vb_max = ctx->vb;
-  ctx->nchunk = int(std::min<int64_t>(ctx->M, 8));
 
   // ---- tiles of the tiled sweep ----
   // One CTA of 1024 threads per SM sweeps tiles b, b + grid, ...; a tile's
@@ -924,6 +923,15 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
   CUDA_TRY(ctx, cudaGetDevice(&dev));
   CUDA_TRY(ctx, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   ctx->nsm = nsm;
+  // Velocity chunks of the second stage (grid: 8 cells per CTA x chunks):
+  // just enough chunks for ~32 CTAs per SM, so that each CTA walks as many
+  // blocks as it can (its set-up and the heat-flux reduction are per CTA).
+  {
+    const int64_t cell_ctas = (Nc + 7) / 8;
+    int64_t chunks = 1;
+    while (chunks < 8 && cell_ctas * chunks < int64_t(32) * nsm) chunks *= 2;
+    ctx->nchunk = int(std::min<int64_t>(ctx->M, chunks));
+  }
   int smem_optin = 0;
   CUDA_TRY(ctx, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const size_t elem = ctx->storage == UGKS_STORAGE_F64 ? sizeof(double) : sizeof(float);
