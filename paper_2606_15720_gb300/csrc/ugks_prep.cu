@@ -975,48 +975,53 @@ __global__ void k_moments13(int64_t Nc, int64_t M, Gas g, const T* f, const doub
 template <int D, typename T>
 __global__ void k_init_ce(int64_t Nc, int64_t M, int64_t nv, Gas g, const double* fields, const double* ux,
                           const double* uy, const double* uz, T* f) {
+  // grid: x over cells (one warp each), y over velocity blocks; the per-cell
+  // factors are formed once per thread
   constexpr int NS = D * (D + 1) / 2, N13 = 2 * D + 2 + NS;
-  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= M * Nc * BV) return;
-  const int lane = int(idx & 31);
-  const int64_t row = idx >> 5;
-  const int64_t c = row % Nc, m = row / Nc;
-  const int64_t k = m * BV + lane;
-  double h = 0.0, b = 0.0;
-  if (k < nv) {
-    const double* x = fields + c * N13;
-    const double rho = x[0], lam = 1.0 / x[D + 1];
-    const double uu[3] = {ux[k], uy[k], uz[k]};
-    double cc[3] = {0.0, 0.0, 0.0}, c2 = 0.0, qc = 0.0, scc = 0.0;
+  const int64_t c = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= Nc) return;
+  const double* x = fields + c * N13;
+  const double rho = x[0], lam = 1.0 / x[D + 1];
+  const double pref = rho * pow(lam / M_PI, 0.5 * D);
+  // the K_xi components of xi carry -tr(sigma) / K_xi each (trace-free
+  // stress over all degrees of freedom); reduced over xi that gives the
+  // constants th (in h) and tb (in b)
+  double tr = 0.0;
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      cc[d] = uu[d] - x[1 + d];
-      c2 += cc[d] * cc[d];
-      qc += x[D + 2 + NS + d] * cc[d];
-    }
-    int s = 0;
+  for (int a = 0, s2 = 0; a < D; ++a)
 #pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-      for (int e = a; e < D; ++e) scc += (a == e ? 1.0 : 2.0) * x[D + 2 + s++] * cc[a] * cc[e];
-    const double H = rho * pow(lam / M_PI, 0.5 * D) * exp(-lam * c2);
-    // the K_xi components of xi carry -tr(sigma) / K_xi each (trace-free
-    // stress over all degrees of freedom); reduced over xi that gives the
-    // constants th (in h) and tb (in b)
-    double tr = 0.0;
-#pragma unroll
-    for (int a = 0, s2 = 0; a < D; ++a)
-#pragma unroll
-      for (int e = a; e < D; ++e, ++s2)
-        if (a == e) tr += x[D + 2 + s2];
-    const double a2 = 2.0 * lam * lam / rho, a3 = 4.0 * lam * lam / ((g.K + 5.0) * rho);
-    const double th = -lam * tr / rho, tb = g.Kxi > 0 ? -lam * (g.Kxi + 2.0) * tr / (g.Kxi * rho) : 0.0;
-    h = H * (1.0 + a2 * scc + th + a3 * qc * (2.0 * lam * c2 - (D + 2)));
-    b = g.Kxi / (2.0 * lam) * H * (1.0 + a2 * scc + tb + a3 * qc * (2.0 * lam * c2 - D));
-  }
+    for (int e = a; e < D; ++e, ++s2)
+      if (a == e) tr += x[D + 2 + s2];
+  const double a2 = 2.0 * lam * lam / rho, a3 = 4.0 * lam * lam / ((g.K + 5.0) * rho);
+  const double th = -lam * tr / rho, tb = g.Kxi > 0 ? -lam * (g.Kxi + 2.0) * tr / (g.Kxi * rho) : 0.0;
+  const double kap = g.Kxi / (2.0 * lam);
   const size_t plane = size_t(M) * Nc * BV;
-  f[size_t(m) * Nc * BV + size_t(c) * BV + lane] = T(h);
-  if (g.NR == 2) f[plane + size_t(m) * Nc * BV + size_t(c) * BV + lane] = T(b);
+  for (int64_t m = blockIdx.y; m < M; m += gridDim.y) {
+    const int64_t k = m * BV + lane;
+    double h = 0.0, b = 0.0;
+    if (k < nv) {
+      const double uu[3] = {ux[k], uy[k], uz[k]};
+      double cc[3] = {0.0, 0.0, 0.0}, c2 = 0.0, qc = 0.0, scc = 0.0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        cc[d] = uu[d] - x[1 + d];
+        c2 += cc[d] * cc[d];
+        qc += x[D + 2 + NS + d] * cc[d];
+      }
+      int s = 0;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int e = a; e < D; ++e) scc += (a == e ? 1.0 : 2.0) * x[D + 2 + s++] * cc[a] * cc[e];
+      const double H = pref * exp(-lam * c2);
+      h = H * (1.0 + a2 * scc + th + a3 * qc * (2.0 * lam * c2 - (D + 2)));
+      b = kap * H * (1.0 + a2 * scc + tb + a3 * qc * (2.0 * lam * c2 - D));
+    }
+    const size_t at = size_t(m) * Nc * BV + size_t(c) * BV + lane;
+    f[at] = T(h);
+    if (g.NR == 2) f[plane + at] = T(b);
+  }
 }
 
 // Scatter of a full FP64 state in[NR][Nc_orig][nv] (original order) into f.
@@ -1125,10 +1130,10 @@ void launch_moments13(cudaStream_t s, int64_t Nc, int64_t M, const Gas& g, const
 template <typename T>
 void launch_init_ce(cudaStream_t s, int64_t Nc, int64_t M, int64_t nv, const Gas& g, const double* fields,
                     const double* ux, const double* uy, const double* uz, T* f) {
-  const unsigned nb = blocks_for(M * Nc * BV, 256);
-  if (g.D == 1) k_init_ce<1, T><<<nb, 256, 0, s>>>(Nc, M, nv, g, fields, ux, uy, uz, f);
-  if (g.D == 2) k_init_ce<2, T><<<nb, 256, 0, s>>>(Nc, M, nv, g, fields, ux, uy, uz, f);
-  if (g.D == 3) k_init_ce<3, T><<<nb, 256, 0, s>>>(Nc, M, nv, g, fields, ux, uy, uz, f);
+  const dim3 grid(blocks_for(Nc * 32, 256), unsigned(std::min<int64_t>(M, 65535)));
+  if (g.D == 1) k_init_ce<1, T><<<grid, 256, 0, s>>>(Nc, M, nv, g, fields, ux, uy, uz, f);
+  if (g.D == 2) k_init_ce<2, T><<<grid, 256, 0, s>>>(Nc, M, nv, g, fields, ux, uy, uz, f);
+  if (g.D == 3) k_init_ce<3, T><<<grid, 256, 0, s>>>(Nc, M, nv, g, fields, ux, uy, uz, f);
 }
 
 void launch_residual_finalize(cudaStream_t s, int nw, int64_t Nc, const double* acc, double* res) {
