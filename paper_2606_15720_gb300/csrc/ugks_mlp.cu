@@ -31,11 +31,13 @@ inline int pad16(int n) { return (n + 15) / 16 * 16; }
 
 // ---------------------------------------------------------------------------
 // C[M][N] = A[M][K] B[K][N]: BF16 operands with arbitrary strides, FP32
-// accumulation on the tensor cores.  CTA tile 64 x 64 x 32, four warps of
-// 32 x 32, each 2 x 4 mma tiles of 16 x 8 x 16.  Both operand tiles are kept
-// K-contiguous in shared memory, the layout the mma fragments read.
+// accumulation on the tensor cores.  Four warps (2 x 2) per CTA, each WM x WN
+// mma tiles of 16 x 8 x 16: CTA tiles of 64 x 64 (WM 2, WN 4) or, when that
+// leaves the GPU mostly idle, 32 x 32 (WM 1, WN 2); K in steps of 32.  Both
+// operand tiles are kept K-contiguous in shared memory, the layout the mma
+// fragments read.
 // ---------------------------------------------------------------------------
-constexpr int kTM = 64, kTN = 64, kTK = 32, kSK = kTK + 8;  // kSK: padded row (bank spread)
+constexpr int kTK = 32, kSK = kTK + 8;  // kSK: padded row (bank spread)
 
 struct GemmArgs {
   int M, N, K;
@@ -68,19 +70,20 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 // rows_total x K) with element (r, k) at P[r s_r + k s_k].  mode 1: 16-byte
 // vectors along k (s_k == 1); mode 2: 16-byte vectors along r (s_r == 1);
 // mode 0: single elements.
+template <int ROWS>
 __device__ __forceinline__ void load_tile(const bf16* __restrict__ P, int64_t s_r, int64_t s_k, int rows_total,
                                           int K, int r0, int k0, int mode, bf16 (*S)[kSK], int tid) {
   const bf16 zero = __float2bfloat16_rn(0.f);
   if (mode == 1) {
-    for (int v = tid; v < kTM * kTK / 8; v += 128) {
+    for (int v = tid; v < ROWS * kTK / 8; v += 128) {
       const int r = v / (kTK / 8), k = (v % (kTK / 8)) * 8;
       uint4 val = make_uint4(0u, 0u, 0u, 0u);
       if (r0 + r < rows_total && k0 + k < K) val = *reinterpret_cast<const uint4*>(P + (r0 + r) * s_r + (k0 + k));
       *reinterpret_cast<uint4*>(&S[r][k]) = val;
     }
   } else if (mode == 2) {
-    for (int v = tid; v < kTM * kTK / 8; v += 128) {
-      const int k = v / (kTM / 8), r = (v % (kTM / 8)) * 8;
+    for (int v = tid; v < ROWS * kTK / 8; v += 128) {
+      const int k = v / (ROWS / 8), r = (v % (ROWS / 8)) * 8;
       uint4 val = make_uint4(0u, 0u, 0u, 0u);
       if (r0 + r < rows_total && k0 + k < K) val = *reinterpret_cast<const uint4*>(P + (k0 + k) * s_k + (r0 + r));
       const bf16* e = reinterpret_cast<const bf16*>(&val);
@@ -88,7 +91,7 @@ __device__ __forceinline__ void load_tile(const bf16* __restrict__ P, int64_t s_
       for (int j = 0; j < 8; ++j) S[r + j][k] = e[j];
     }
   } else {
-    for (int idx = tid; idx < kTM * kTK; idx += 128) {
+    for (int idx = tid; idx < ROWS * kTK; idx += 128) {
       const int r = idx / kTK, k = idx % kTK;
       S[r][k] = (r0 + r < rows_total && k0 + k < K) ? P[(r0 + r) * s_r + (k0 + k) * s_k] : zero;
     }
@@ -104,57 +107,59 @@ __host__ int tile_mode(const bf16* P, int64_t s_r, int64_t s_k, int rows_total, 
   return 0;
 }
 
+template <int WM, int WN>
 __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
-  __shared__ __align__(16) bf16 As[kTM][kSK];
-  __shared__ __align__(16) bf16 Bs[kTN][kSK];
+  constexpr int TM = 32 * WM, TN = 16 * WN;  // CTA tile
+  __shared__ __align__(16) bf16 As[TM][kSK];
+  __shared__ __align__(16) bf16 Bs[TN][kSK];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 1, wn = warp & 1;
   const int gid = lane >> 2, tig = lane & 3;
-  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
-  float acc[2][4][4];
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  float acc[WM][WN][4];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < WM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < WN; ++j)
 #pragma unroll
       for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
   for (int k0 = 0; k0 < g.K; k0 += kTK) {
-    load_tile(g.A, g.a_m, g.a_k, g.M, g.K, m0, k0, g.a_mode, As, tid);
-    load_tile(g.B, g.b_n, g.b_k, g.N, g.K, n0, k0, g.b_mode, Bs, tid);
+    load_tile<TM>(g.A, g.a_m, g.a_k, g.M, g.K, m0, k0, g.a_mode, As, tid);
+    load_tile<TN>(g.B, g.b_n, g.b_k, g.N, g.K, n0, k0, g.b_mode, Bs, tid);
     __syncthreads();
 #pragma unroll
     for (int ks = 0; ks < kTK; ks += 16) {
-      uint32_t af[2][4], bfr[4][2];
+      uint32_t af[WM][4], bfr[WN][2];
 #pragma unroll
-      for (int mi = 0; mi < 2; ++mi) {
-        const int r = wm * 32 + mi * 16 + gid;
+      for (int mi = 0; mi < WM; ++mi) {
+        const int r = wm * 16 * WM + mi * 16 + gid;
         af[mi][0] = ld_pair(&As[r][ks + 2 * tig]);
         af[mi][1] = ld_pair(&As[r + 8][ks + 2 * tig]);
         af[mi][2] = ld_pair(&As[r][ks + 2 * tig + 8]);
         af[mi][3] = ld_pair(&As[r + 8][ks + 2 * tig + 8]);
       }
 #pragma unroll
-      for (int ni = 0; ni < 4; ++ni) {
-        const int c = wn * 32 + ni * 8 + gid;
+      for (int ni = 0; ni < WN; ++ni) {
+        const int c = wn * 8 * WN + ni * 8 + gid;
         bfr[ni][0] = ld_pair(&Bs[c][ks + 2 * tig]);
         bfr[ni][1] = ld_pair(&Bs[c][ks + 2 * tig + 8]);
       }
 #pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
+      for (int mi = 0; mi < WM; ++mi)
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni]);
+        for (int ni = 0; ni < WN; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni]);
     }
     __syncthreads();
   }
   // epilogue: accumulator r of tile (mi, ni) is row gid (+8 for r >= 2), column 2 tig + (r & 1)
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
+  for (int mi = 0; mi < WM; ++mi)
 #pragma unroll
-    for (int ni = 0; ni < 4; ++ni)
+    for (int ni = 0; ni < WN; ++ni)
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const int row = m0 + wm * 32 + mi * 16 + gid + (r >= 2 ? 8 : 0);
-        const int col = n0 + wn * 32 + ni * 8 + 2 * tig + (r & 1);
+        const int row = m0 + wm * 16 * WM + mi * 16 + gid + (r >= 2 ? 8 : 0);
+        const int col = n0 + wn * 8 * WN + ni * 8 + 2 * tig + (r & 1);
         if (row >= g.M || col >= g.N) continue;
         float v = acc[mi][ni][r];
         const int64_t o = row * g.ldc + col;
@@ -369,8 +374,14 @@ uint64_t splitmix(uint64_t& s) {
 void gemm(cudaStream_t s, GemmArgs g) {
   g.a_mode = tile_mode(g.A, g.a_m, g.a_k, g.M, g.K);
   g.b_mode = tile_mode(g.B, g.b_n, g.b_k, g.N, g.K);
-  dim3 grid(unsigned((g.N + kTN - 1) / kTN), unsigned((g.M + kTM - 1) / kTM));
-  k_gemm<<<grid, 128, 0, s>>>(g);
+  const int64_t big = int64_t((g.N + 63) / 64) * ((g.M + 63) / 64);
+  if (big >= 304) {  // two 64 x 64 tiles per SM or more
+    dim3 grid(unsigned((g.N + 63) / 64), unsigned((g.M + 63) / 64));
+    k_gemm<2, 4><<<grid, 128, 0, s>>>(g);
+  } else {
+    dim3 grid(unsigned((g.N + 31) / 32), unsigned((g.M + 31) / 32));
+    k_gemm<1, 2><<<grid, 128, 0, s>>>(g);
+  }
 }
 
 // Forward pass of nbatch rows of actb[0] (BF16 input, padded).
