@@ -1,0 +1,64 @@
+"""The arithmetic behind bench.py's roofline fields, on synthetic timings
+(no GPU): achieved rates follow from the stated work per DOF, the DOF one
+launch processes and the mean launch time; the dominant kernel is the one
+with the most time per step."""
+import importlib.util
+import os
+import types
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_math_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _mesh(n_cells, n_faces, n_boundary):
+    nb = np.zeros(n_faces, dtype=np.int64)
+    nb[:n_boundary] = -1
+    return types.SimpleNamespace(n_cells=n_cells, n_faces=n_faces, face_neighbor=nb)
+
+
+def test_per_kernel_rates_and_the_dominant_kernel(bench):
+    mesh = _mesh(1000, 2100, 100)                    # 2 x 2100 - 100 = 4100 incidences: 4.1 per cell
+    grid = types.SimpleNamespace(n_v=4096)
+    dof, steps = mesh.n_cells * grid.n_v, 10
+    # (ms in total, launches) over the 10 steps: 16 blocks per step
+    stats = {"block_reconstruction": (200.0, 160), "block_fluxes": (150.0, 160), "block_stage1": (80.0, 160),
+             "stage2": (100.0, 10), "velocity_block_sweep": (540.0, 10)}
+    roofline, kernels, step = bench.rooflines(stats, mesh, grid, dof, steps)
+    hbm_peak, _, fp32_peak = bench.load_peaks()
+    inc = 4100 / 1000
+    k = kernels["block_reconstruction"]
+    launch_s = 200.0 / 160 * 1e-3
+    dof_launch = dof * steps / 160
+    assert k["flops_per_dof"] == pytest.approx(41 + 31 * inc)
+    assert k["alu_tflops"] == pytest.approx((41 + 31 * inc) * dof_launch / launch_s / 1e12)
+    assert k["alu_frac"] == pytest.approx(k["alu_tflops"] / fp32_peak)
+    s2 = kernels["stage2"]
+    assert s2["bytes_per_dof"] == 8                  # read f~, write f^{n+1} in FP32
+    assert s2["hbm_gbs"] == pytest.approx(8 * dof / (100.0 / 10 * 1e-3) / 1e9)
+    assert s2["hbm_frac"] == pytest.approx(s2["hbm_gbs"] / hbm_peak)
+    # the reconstruction has the most time per step: it is the reported kernel
+    assert roofline["kernel"] == "block_reconstruction" and roofline["bound"] == "alu"
+    assert roofline["frac"] == pytest.approx(k["alu_frac"])
+    assert roofline["algorithmic_flops_per_launch"] == pytest.approx(k["flops_per_dof"] * dof_launch)
+    # whole step: 16 B per DOF against HBM, the sum of the kernels' flops against FP32
+    t = 540.0 / 10 * 1e-3
+    assert step["hbm"]["achieved_gbs"] == pytest.approx(16 * dof / t / 1e9)
+    assert step["alu"]["flops_per_dof"] == pytest.approx(sum(v["flops_per_dof"] for v in kernels.values()))
+
+
+def test_launch_count_of_the_blocked_sweep(bench):
+    stats = {"cell_stage": (1.0, 3), "face_stage": (1.0, 3), "velocity_block_sweep": (1.0, 3),
+             "block_reconstruction": (1.0, 384), "block_fluxes": (1.0, 384), "block_stage1": (1.0, 384),
+             "conserve": (1.0, 3), "stage2": (1.0, 3), "residual": (1.0, 3)}
+    # per step: 1 + 1 + 1 + 3 x 128 + 2 + 2 + 1 = 392 launches
+    assert bench.count_launches(stats) == 3 * 392
