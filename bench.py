@@ -175,10 +175,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(mesh, grid, gas, W0, target_cells=3000, steps=6):
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                v = line.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    return v
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline(mesh, grid, gas, W0, dt, target_cells=3000, steps=6):
     """The FP64 oracle as it stands, on a bounded sample of the workload: the
     face-connected patch of ~target_cells cells around a body-adjacent cell,
-    all 32^3 velocities, `steps` steps."""
+    all 32^3 velocities, `steps` steps at the GPU run's time step dt."""
     import oracle as O
     seed = int(mesh.face_owner[np.flatnonzero(mesh.face_neighbor == -1)[0]])
     rings, cells, pm = 1, None, None
@@ -189,15 +210,15 @@ def cpu_baseline(mesh, grid, gas, W0, target_cells=3000, steps=6):
         rings += 1
     W = W0[cells]
     f = O.initial_f(pm, grid, W, gas.K)
-    dt = 1e-4
     O.run(pm, grid, gas, W, f, 1, dt=dt)             # warm-up (page-in, thread pool)
     t0 = time.perf_counter()
     O.run(pm, grid, gas, W, f, steps, dt=dt)
     el = time.perf_counter() - t0
     dof = pm.n_cells * grid.n_v * O.n_reduced(3, gas.K)
-    out = {"value": dof * steps / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+    out = {"value": dof * steps / el, "unit": UNIT, "cores": O.num_threads(), "cpu_model": cpu_model(),
+           "nproc": os.cpu_count(), "kind": "oracle", "dt": dt,
            "sample": f"{steps} steps of a {pm.n_cells}-cell patch of the workload mesh x {grid.n_v} velocities "
-                     f"({dof * steps:.3g} DOF updates, {el:.1f} s)"}
+                     f"at the GPU run's dt ({dof * steps:.3g} DOF updates, {el:.1f} s)"}
     # one thread, on a patch of about a tenth of the cells
     rings, cells1, pm1 = 1, None, None
     while True:
@@ -235,7 +256,7 @@ def run_reference(args):
         rings += 1
     W = W0[cells]
     f = O.initial_f(pm, grid, W, gas.K)
-    dt = 1e-4
+    dt = O.time_step(mesh, grid, gas.cfl)          # the time step of the full workload
     dof = pm.n_cells * grid.n_v * O.n_reduced(3, gas.K)
     for _ in range(args.warmup):
         W, f, _, _ = O.run(pm, grid, gas, W, f, 1, dt=dt)
@@ -249,24 +270,36 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_cells": pm.n_cells, "n_v": grid.n_v, "sampled_from_cells": mesh.n_cells},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "cpu_model": cpu_model(),
+                             "nproc": os.cpu_count(), "kind": "oracle", "dt": dt, "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def rooflines(stats, mesh, grid, dof, steps, bytes_stage=BYTES_STAGE):
-    """Per-kernel rooflines of the blocked sweep from the library's event
-    timings (CUDA events on the stream the kernels run on), the roofline of
-    the dominant kernel, and the whole-step HBM and ALU views."""
+def rooflines(stats, mesh, grid, dof, steps, ms_per_step, bytes_stage=BYTES_STAGE):
+    """Rooflines of the blocked sweep from the library's event timings (CUDA
+    events on the stream the kernels run on).
+
+    roofline (the headline): the whole step against HBM on its algorithmic
+    bytes: 4 s bytes per phase-space DOF (s = bytes per stored
+    value: the first stage reads f^n and writes f~, the second reads f~ and
+    writes f^{n+1}), achieved = 4 s x DOF / (ms_per_step), so the fraction
+    reproduces from ms_per_step.  traffic = the step's DRAM bytes from the
+    committed ncu capture (null when the kernels changed since).
+    kernels: per kernel the ALU view (algorithmic FP32 operations), the
+    algorithmic-bytes view where the kernel has algorithmic bytes, and the
+    measured DRAM rate (ncu bytes per launch / event-timed launch); the bound
+    is the larger of the two times at the peaks, using the measured bytes
+    where they exist."""
     hbm_peak, peak_kind, fp32_peak = load_peaks()
     n_inc = 2 * mesh.n_faces - int(np.sum(mesh.face_neighbor < 0))
     inc = n_inc / mesh.n_cells
-    nv = grid.n_v
     traffic = recorded_traffic()
     per_dof = {"block_reconstruction": (flops_recon(inc), 0), "block_fluxes": (FLOPS_FLUX * mesh.n_faces / mesh.n_cells, 0),
                "block_stage1": (flops_stage1(inc), bytes_stage), "stage2": (FLOPS_STAGE2, bytes_stage)}
     kernels = {}
+    step_traffic, traffic_complete = 0.0, bool(traffic)
     for name, (fl, by) in per_dof.items():
         ms, n = stats.get(name, (0.0, 0))
         if not n:
@@ -275,39 +308,44 @@ def rooflines(stats, mesh, grid, dof, steps, bytes_stage=BYTES_STAGE):
         dof_launch = dof * steps / n              # phase-space points one launch processes
         tflops = fl * dof_launch / launch_s / 1e12
         gbs = by * dof_launch / launch_s / 1e9
-        bound = "alu" if by == 0 or fl / by > fp32_peak * 1e12 / (hbm_peak * 1e9) else "hbm"
-        kernels[name] = {"launch_ms": ms / n, "ms_per_step": ms / steps, "bound": bound,
+        dram = traffic.get(name)
+        if dram is None:
+            traffic_complete = False
+        else:
+            step_traffic += dram * n / steps
+        dram_gbs = dram / launch_s / 1e9 if dram is not None else None
+        t_alu = fl * dof_launch / (fp32_peak * 1e12)
+        t_mem = (dram if dram is not None else by * dof_launch) / (hbm_peak * 1e9)
+        kernels[name] = {"launch_ms": ms / n, "ms_per_step": ms / steps, "launches_per_step": n / steps,
+                         "bound": "hbm" if t_mem > t_alu else "alu",
                          "flops_per_dof": fl, "bytes_per_dof": by,
                          "alu_tflops": tflops, "alu_frac": tflops / fp32_peak,
                          "hbm_gbs": gbs if by else None, "hbm_frac": gbs / hbm_peak if by else None,
-                         "dram_bytes_per_launch": traffic.get(name)}
-    roofline = None
-    if kernels:
-        top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
-        k = kernels[top]
-        if k["bound"] == "alu":
-            roofline = {"bound": "alu", "kernel": top, "achieved": k["alu_tflops"], "peak": fp32_peak,
-                        "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock", "unit": "TFLOP/s",
-                        "frac": k["alu_frac"], "traffic": k["dram_bytes_per_launch"],
-                        "algorithmic_flops_per_launch": k["flops_per_dof"] * dof * steps / stats[top][1],
-                        "launch_ms": k["launch_ms"]}
-        else:
-            roofline = {"bound": "hbm", "kernel": top, "achieved": k["hbm_gbs"], "peak": hbm_peak,
-                        "peak_kind": peak_kind, "unit": "GB/s", "frac": k["hbm_frac"],
-                        "traffic": k["dram_bytes_per_launch"],
-                        "algorithmic_bytes_per_launch": k["bytes_per_dof"] * dof * steps / stats[top][1],
-                        "launch_ms": k["launch_ms"]}
+                         "dram_bytes_per_launch": dram, "dram_gbs": dram_gbs,
+                         "dram_frac": dram_gbs / hbm_peak if dram_gbs is not None else None}
+    b_step = 2 * bytes_stage
+    achieved = b_step * dof / (ms_per_step * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "whole step (every kernel of one UGKS step)",
+                "achieved": achieved, "peak": hbm_peak, "peak_kind": peak_kind + " (copy bandwidth)",
+                "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": step_traffic if traffic_complete else None,
+                "traffic_unit": "DRAM bytes per step (ncu, sum over the sweep kernels)",
+                "algorithmic_bytes_per_step": b_step * dof, "bytes_per_dof": b_step,
+                "launch_ms": ms_per_step}
     sweep_ms, sweep_n = stats.get("velocity_block_sweep", (0.0, 0))
     step_views = None
     if sweep_n:
         t = sweep_ms / sweep_n * 1e-3
         fl = sum(v["flops_per_dof"] for v in kernels.values())
-        bstep = 2 * bytes_stage
         step_views = {"sweep_ms": sweep_ms / sweep_n,
-                      "hbm": {"bytes_per_dof": bstep, "achieved_gbs": bstep * dof / t / 1e9,
-                              "frac": bstep * dof / t / 1e9 / hbm_peak, "peak": hbm_peak, "peak_kind": peak_kind},
+                      "hbm": {"bytes_per_dof": b_step, "achieved_gbs": b_step * dof / t / 1e9,
+                              "frac": b_step * dof / t / 1e9 / hbm_peak, "peak": hbm_peak, "peak_kind": peak_kind},
                       "alu": {"flops_per_dof": fl, "achieved_tflops": fl * dof / t / 1e12,
-                              "frac": fl * dof / t / 1e12 / fp32_peak, "peak": fp32_peak}}
+                              "frac": fl * dof / t / 1e12 / fp32_peak, "peak": fp32_peak,
+                              "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}}
+        if kernels:
+            top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+            step_views["dominant_kernel"] = top
     return roofline, kernels, step_views
 
 
@@ -350,6 +388,7 @@ def run_gpu(args):
         solver = U.Solver(mesh, grid, gas, W0, storage=args.storage, stream=int(stream.cuda_stream),
                           sweep=args.sweep, block_velocities=args.block_velocities)
         assert solver.n_reduced == n_reduced
+        dt_run = solver.dt
         solver.step(args.warmup)
         solver.residual()
         solver.stats_enable(True)
@@ -379,7 +418,7 @@ def run_gpu(args):
         solver.close()
     ms_per_step, value = replica_timing(ms, args.steps, dof, world, dist, "cuda")
 
-    roofline, kernels, step_views = rooflines(stats, mesh, grid, dof, args.steps,
+    roofline, kernels, step_views = rooflines(stats, mesh, grid, dof, args.steps, ms_per_step,
                                               BYTES_STAGE if args.storage == "f32" else BYTES_STAGE_SCALED)
 
     # end to end through the one-shot C call with host buffers: mesh, grid and
@@ -410,7 +449,7 @@ def run_gpu(args):
         return 0
     cpu = None
     if world == 1 and not args.no_cpu_baseline and (args.cells, args.nv_axis) == (MESH_CELLS, NV_AXIS):
-        cpu = cpu_baseline(mesh, grid, gas, W0)
+        cpu = cpu_baseline(mesh, grid, gas, W0, dt_run)
     workload = WORKLOAD if (args.cells, args.nv_axis) == (MESH_CELLS, NV_AXIS) else \
         f"sphere_tet{args.cells // 1000}k_v{args.nv_axis}cube_shakhov_fp32 (reduced size for profiling)"
     if args.storage != "f32":

@@ -20,7 +20,9 @@
  *     data (moments, residual, get_f, state) synchronise that stream.
  *     Non-finite or non-physical states detected on the device latch into a
  *     status word that the next ugks_moments or ugks_residual reports as
- *     UGKS_ERR_NONFINITE; ugks_get_f and ugks_get_state return the raw state
+ *     UGKS_ERR_NONFINITE; a bounded device wait that gave up (shared-memory
+ *     staging whose copies did not complete) latches UGKS_ERR_TIMEOUT the
+ *     same way.  ugks_get_f and ugks_get_state return the raw state
  *     regardless, so that it can be inspected.
  *   * A context is not thread-safe; distinct contexts are independent.
  *   * Units: R = 1/2 (so lambda = 1/T, p = rho T / 2), velocities in
@@ -46,7 +48,7 @@ typedef enum {
   UGKS_ERR_OUT_OF_MEMORY = 4,    /* device or host allocation failed */
   UGKS_ERR_CUDA = 5,             /* a CUDA runtime call failed */
   UGKS_ERR_NONFINITE = 6,        /* NaN/Inf or non-positive density / temperature */
-  UGKS_ERR_TIMEOUT = 7,          /* reserved for bounded device waits */
+  UGKS_ERR_TIMEOUT = 7,          /* a bounded device wait (shared-memory staging) gave up */
   UGKS_ERR_UNSUPPORTED = 8       /* valid request this build does not implement */
 } ugks_status;
 
@@ -167,7 +169,11 @@ ugks_status ugks_step(ugks_ctx *ctx, int32_t n_steps);
  * once per device); make that first call before any stream capture.  All
  * calls share the array and each call overwrites it (the accumulators are
  * cleared by the kernel), so calls whose work overlaps on the GPU (other
- * streams, other contexts) race on it.  Contexts whose scratch needs more
+ * streams, other contexts) race on it.  At the end of each step the face
+ * accumulators are copied (device to device, on the context's stream) into
+ * the context's own buffer, so ugks_surface after a static step reports that
+ * context's wall fluxes even when another context has used the array since.
+ * Contexts whose scratch needs more
  * than 16 MiB are rejected with UGKS_ERR_INVALID_ARGUMENT and a message
  * naming the size; use ugks_step for them. */
 ugks_status ugks_step_static_scratch(ugks_ctx *ctx, int32_t n_steps);

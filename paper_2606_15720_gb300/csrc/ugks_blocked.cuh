@@ -35,7 +35,9 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
+#include <type_traits>
 
+#include "ugks_bulk.cuh"
 #include "ugks_device.cuh"
 #include "ugks_internal.cuh"
 #include "ugks_kernels.cuh"
@@ -1169,90 +1171,158 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bW(const BlockedArgs<T> a) 
 }
 
 // ---------------------------------------------------------------------------
-// Second stage (Eq. 42) of one cell over one chunk of velocity blocks, with
-// the outgoing wall flux rho_w g_w (known only after the sweep), and the
-// chunk's partial sums of the heat flux of f^{n+1} (Eq. 13).  The 8 warps of
-// a CTA (8 cells) step through the chunk together, 8 blocks per round: the
-// CTA stages the round's velocity records in shared memory (one per thread)
-// and each warp keeps its cell's 8 rows in flight.  Per-lane FP32 partial
-// sums of q are flushed to FP64 every 32 blocks and reduced over the warp once.
+// Second stage (Eq. 42) over one chunk of velocity rows, with the outgoing
+// wall flux rho_w g_w (known only after the sweep), and the chunk's partial
+// sums of the heat flux of f^{n+1} (Eq. 13).  A streaming pass over f~: a CTA
+// owns 32 consecutive cells, whose rows of one velocity block are one
+// contiguous segment (4 KB in FP32).  A producer warp stages the chunk's rows
+// into a ring of shared-memory stages with 1-D bulk asynchronous copies
+// (completion counted in bytes on an mbarrier per stage); 8 consumer warps
+// (8 threads per cell, 4 consecutive velocities each) read their values,
+// release the stage, update and write f^{n+1} in place.  On tensor grids
+// whose fastest axis has 32 points (a row is one line along that axis) the
+// Maxwellians factor into a per-row part (one exponential per row and thread)
+// and the thread's four lane parts (computed once), and the heat-flux sums
+// factor the same way.
 // ---------------------------------------------------------------------------
-// Second stage of one block of one cell: ft holds f~ on entry and f^{n+1}
-// on exit; H receives the cell's Maxwellian of W^{n+1} at the lane's velocity.
-template <int D, int NR, bool WALL, typename T>
-__device__ __forceinline__ void stage2_block(const BlockedArgs<T>& a, int c, int e0, int e1, int64_t m,
-                                             int lane, const Vel4<T>& vq, T (&ft)[NR], const T (&Uc)[3],
-                                             const T (&qc)[3], T pref, T lam, T s0, T kap, T beta1, T inv1, T iv,
-                                             T (&qp)[3], T& H_out) {
-  const T dt = T(a.g.dt);
-  const int64_t k = m * BV + lane;
-  T u[3];
-  u[0] = vq.x;
-  u[1] = D > 1 ? vq.y : T(0);
-  u[2] = D > 2 ? vq.z : T(0);
-  const bool real_v = k < a.nv;
-  if (WALL) {
-    for (int e = e0; e < e1; ++e) {
-      if (!(a.inc[e].flags & 1)) continue;
-      const int fidx = a.inc[e].face;
-      const FaceGeom<T>& fg = a.fg[fidx];
-      const FacePoly<D, NR, T>& R = static_cast<const FacePoly<D, NR, T>*>(a.fpoly)[fidx];
-      T un = T(0), c2 = T(0);
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        un += u[d] * fg.n[d];
-        c2 += (u[d] - R.U[d]) * (u[d] - R.U[d]);
-      }
-      if (un < T(0)) {
-        const T rw = T(a.Facc[size_t(fidx) * FACC_W + 10]);
-        const T out = un * dt * rw * R.rho_pref * t_exp(-R.lam * c2);
-        const T area = a.inc[e].sarea;  // walls have owner cells only: +area
-        ft[0] -= area * iv * out;
-        if (NR == 2) ft[NR - 1] -= area * iv * R.kappa * out;
-      }
-    }
+constexpr int kS2Consumers = 256;                    // 8 warps: 32 cells x 8 threads
+constexpr int kS2Threads = kS2Consumers + 32;        // and one producer warp
+constexpr int kS2Cells = kS2Consumers / 8;           // cells per CTA
+constexpr int kS2Flush = 8;                          // rows between flushes of the FP32 heat-flux partials
+
+template <int NR, typename S>
+struct S2Ring {
+  static constexpr int ROW = kS2Cells * BV * int(sizeof(S));   // one row (r, m) of the CTA's cells
+  static constexpr int STAGE = NR * ROW;
+  static constexpr int NST = (32 * 1024 / STAGE) < 2 ? 2 : (32 * 1024 / STAGE) > 8 ? 8 : (32 * 1024 / STAGE);
+  static constexpr int BYTES = NST * STAGE + 2 * NST * 8;        // stages, then full and empty barriers
+};
+
+// Four consecutive stored values of one row (the thread's velocities).
+template <typename S>
+struct Quad {
+  S v[4];
+};
+template <typename S>
+__device__ __forceinline__ Quad<S> quad_lds(const unsigned char* p) {
+  Quad<S> q;
+  if constexpr (sizeof(S) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    q.v[0] = t.x, q.v[1] = t.y, q.v[2] = t.z, q.v[3] = t.w;
+  } else if constexpr (sizeof(S) == 8) {
+    const double2 t0 = reinterpret_cast<const double2*>(p)[0];
+    const double2 t1 = reinterpret_cast<const double2*>(p)[1];
+    q.v[0] = t0.x, q.v[1] = t0.y, q.v[2] = t1.x, q.v[3] = t1.y;
+  } else {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    const S* h = reinterpret_cast<const S*>(&t);
+    q.v[0] = h[0], q.v[1] = h[1], q.v[2] = h[2], q.v[3] = h[3];
   }
-  T cc[3], c2 = T(0), cq = T(0);
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    cc[d] = u[d] - Uc[d];
-    c2 += cc[d] * cc[d];
-    cq += cc[d] * qc[d];
+  return q;
+}
+template <typename S>
+__device__ __forceinline__ void quad_store(S* p, const Quad<S>& q) {
+  if constexpr (sizeof(S) == 4) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(q.v[0], q.v[1], q.v[2], q.v[3]));
+  } else if constexpr (sizeof(S) == 8) {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(q.v[0], q.v[1]));
+    __stcs(reinterpret_cast<double2*>(p) + 1, make_double2(q.v[2], q.v[3]));
+  } else {
+    uint2 t;
+    S* h = reinterpret_cast<S*>(&t);
+    h[0] = q.v[0], h[1] = q.v[1], h[2] = q.v[2], h[3] = q.v[3];
+    __stcs(reinterpret_cast<uint2*>(p), t);
   }
-  const T H = pref * t_exp(-lam * c2);
-  const T s = s0 * cq;
-  T f1[NR];
-  f1[0] = (ft[0] + beta1 * H * (T(1) + s * (T(2) * lam * c2 - T(2 + D)))) * inv1;
-  if (NR == 2) f1[NR - 1] = (ft[NR - 1] + beta1 * kap * H * (T(1) + s * (T(2) * lam * c2 - T(D)))) * inv1;
-#pragma unroll
-  for (int r = 0; r < NR; ++r) ft[r] = real_v ? f1[r] : T(0);
-  H_out = real_v ? H : T(0);
-  const T wq = T(0.5) * vq.w;  // zero on padding
-  const T e_ = wq * (c2 * ft[0] + (NR == 2 ? ft[NR - 1] : T(0)));
-#pragma unroll
-  for (int d = 0; d < D; ++d) qp[d] += cc[d] * e_;
 }
 
-template <int D, int NR, typename T, typename S>
-__global__ void __launch_bounds__(kBlockedThreads, sizeof(T) == 4 ? (NR == 1 ? 4 : 2) : 1) k_bstage2(const BlockedArgs<T> a) {
+// Maximum over the 8 threads of one cell (lanes 8k .. 8k+7 of the warp).
+__device__ __forceinline__ float max8(float v) {
+  v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
+  v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
+  return fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
+}
+
+// The first diffuse-wall face of a cell, held in registers by the second
+// stage: its re-emitted flux at velocity u is coef (u.n) exp(-lam |u - U|^2)
+// for u.n < 0 (and kappa times that for b), coef = area/|Omega| dt rho_w
+// rho_pref (Eq. 36-38).
+template <typename T>
+struct WallEmit {
+  T coef, lam, kap;
+  T n[3], U[3];
+};
+
+// Launched twice per step: WALL = false handles the CTAs without a wall cell,
+// WALL = true the CTAs holding one (threads of their other cells carry
+// coef = 0); each launch returns at once for the other kind, so the common
+// kind keeps the registers of the wall terms free.
+template <int D, int NR, bool TENSOR, bool WALL, typename T, typename S>
+__global__ void __launch_bounds__(kS2Threads, sizeof(T) == 4 && NR == 1 && !WALL ? 3 : 2) k_bstage2(const BlockedArgs<T> a) {
   constexpr bool SCALED = StoreTraits<S>::scaled;
-  constexpr int UNR = kBlockedThreads / BV;  // blocks per round: one velocity record per thread of the CTA
-  __shared__ Vel4<T> sv[2][UNR * BV];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c = blockIdx.x * (kBlockedThreads / 32) + warp;
-  const bool valid = c < a.Nc;  // every warp takes part in the CTA barriers
-  const int cc = valid ? c : a.Nc - 1;
+  using RG = S2Ring<NR, S>;
+  extern __shared__ __align__(128) unsigned char s2_smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(s2_smem + RG::NST * RG::STAGE);
+  uint64_t* empty = full + RG::NST;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool producer = warp == kS2Consumers / 32;
+  const int qd_ = threadIdx.x & 7;                     // velocities 4 qd_ .. 4 qd_ + 3 of every row
+  const int cl0 = (threadIdx.x >> 3) & (kS2Cells - 1); // the thread's cell within the CTA
+  const int c0 = blockIdx.x * kS2Cells;
+  const int ncta = a.Nc - c0 < kS2Cells ? a.Nc - c0 : kS2Cells;
+  const int c = c0 + cl0;
+  const bool valid = !producer && cl0 < ncta;
+  const int cc = valid ? c : c0;
   const int chunk = blockIdx.y;
   const int64_t per = (a.M + a.nchunk - 1) / a.nchunk;
   const int64_t mb = int64_t(chunk) * per;
   const int64_t me = mb + per < a.M ? mb + per : a.M;
+  const int nrow = me > mb ? int(me - mb) : 0;
   const size_t sj = size_t(a.Nc) * BV, sr = size_t(a.M) * sj;
-  S* fc = reinterpret_cast<S*>(a.f_next) + size_t(cc) * BV + lane;
+
+  // diffuse-wall faces of the cell: the first in registers, further ones
+  // (rare) re-read per row
+  const int e0 = a.cf_off[cc], e1 = a.cf_off[cc + 1];
+  int nwall = 0, ewall = -1;
+  if (valid)
+    for (int e = e0; e < e1; ++e)
+      if (a.inc[e].flags & 1) {
+        if (nwall == 0) ewall = e;
+        ++nwall;
+      }
+  if ((__syncthreads_or(nwall > 0) != 0) != WALL) return;   // CTA-uniform
+  if (threadIdx.x == 0)
+    for (int st = 0; st < RG::NST; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], kS2Consumers / 32);
+    }
+  __syncthreads();
+
+  if (producer) {
+    if (lane != 0) return;
+    const S* src = reinterpret_cast<const S*>(a.f_next) + size_t(c0) * BV;
+    const unsigned bytes = unsigned(ncta) * BV * unsigned(sizeof(S));   // a multiple of 16
+    int issued = 0;
+    for (int i = 0; i < nrow; ++i) {
+      const int st = i % RG::NST;
+      if (i >= RG::NST && !mbar_wait(&empty[st], unsigned((i / RG::NST) - 1) & 1u, a.status)) break;
+      mbar_arrive_expect_tx(&full[st], NR * bytes);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        bulk_load(s2_smem + st * RG::STAGE + r * RG::ROW, src + r * sr + (mb + i) * sj, bytes, &full[st]);
+      issued = i + 1;
+    }
+    // the CTA's shared memory must outlive every copy issued into it
+    for (int i = issued > RG::NST ? issued - RG::NST : 0; i < issued; ++i)
+      if (!mbar_wait(&full[i % RG::NST], unsigned(i / RG::NST) & 1u, a.status)) break;
+    return;
+  }
+
+  S* fc = reinterpret_cast<S*>(a.f_next) + size_t(cc) * BV + 4 * qd_;
   const CellEq<T> E = a.ceq1[cc];
   RefMaxwell Rc{};  // reference of f~ (scaled storage)
   if constexpr (SCALED) {
     Rc = a.ref_cur[cc];
-    if (valid && chunk == 0 && lane == 0) {
+    if (valid && chunk == 0 && qd_ == 0) {
       // f^{n+1} is stored against the Maxwellian of W^{n+1}
       RefMaxwell Rn;
       Rn.pref = E.pref;
@@ -1267,113 +1337,273 @@ __global__ void __launch_bounds__(kBlockedThreads, sizeof(T) == 4 ? (NR == 1 ? 4
   }
   const T lam = E.lam, beta1 = E.beta, pref = E.pref, s0 = E.s0, kap = E.kap, iv = E.inv_vol;
   const T inv1 = T(1) / (T(1) + beta1);
-  T Uc[3], qc[3];
+  const T tl = T(2) * lam;
+  WallEmit<T> wf{};
+  if (WALL && nwall > 0) {
+    const int fidx = a.inc[ewall].face;
+    const FaceGeom<T>& fg = a.fg[fidx];
+    const FacePoly<D, NR, T>& R = static_cast<const FacePoly<D, NR, T>*>(a.fpoly)[fidx];
+    wf.coef = a.inc[ewall].sarea * iv * T(a.g.dt) * T(a.Facc[size_t(fidx) * FACC_W + 10]) * R.rho_pref;
+    wf.lam = R.lam;
+    wf.kap = R.kappa;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    Uc[d] = E.U[d];
-    qc[d] = E.q[d];
+    for (int d = 0; d < 3; ++d) {
+      wf.n[d] = d < D ? fg.n[d] : T(0);
+      wf.U[d] = d < D ? R.U[d] : T(0);
+    }
   }
-  const int e0 = a.cf_off[cc], e1 = a.cf_off[cc + 1];
-  bool has_wall = false;
-  for (int e = e0; e < e1; ++e) has_wall |= (a.inc[e].flags & 1) != 0;
-  // partial sums of q: per lane in T for 32 blocks, then flushed into a
-  // running sum (FP64 for the FP64 sweep; a float pair for the FP32 sweep,
-  // which keeps this kernel off GB300's narrow FP64 pipe)
-  double qd[3] = {0.0, 0.0, 0.0};
-  float2 qf[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-  T qp[3] = {T(0), T(0), T(0)};
 
-  // round k covers blocks [m, m + UNR); its rows and velocity records are
-  // requested during round k - 1
-  constexpr int USC = SCALED ? UNR : 1;  // row scales are kept only for scaled storage
-  auto load_rows = [&](int64_t m, S (&ft)[UNR][NR], float (&sc)[USC][NR]) {
+  // lane parts (tensor grids): c along the lane axis, its Maxwellian factors
+  // (the cell's, that of the reference of f~, the wall's), the lane weight
+  T cl[4], El[4], wl[4], Er[4], Ew[4];
 #pragma unroll
-    for (int i = 0; i < UNR; ++i)
-      if (m + i < me)
+  for (int i = 0; i < 4; ++i) {
+    cl[i] = El[i] = wl[i] = Er[i] = Ew[i] = T(0);
+    if constexpr (TENSOR) {
+      const T ul = a.lanev[4 * qd_ + i];
+      wl[i] = a.lanev[BV + 4 * qd_ + i];
+      cl[i] = ul - E.U[0];
+      El[i] = t_exp(-lam * cl[i] * cl[i]);
+      if constexpr (SCALED) Er[i] = t_exp(-T(Rc.lam) * (ul - T(Rc.U[0])) * (ul - T(Rc.U[0])));
+      if constexpr (WALL) Ew[i] = t_exp(-wf.lam * (ul - wf.U[0]) * (ul - wf.U[0]));
+    }
+  }
+  // heat-flux partial sums: FP32 for kS2Flush rows, then into float pairs
+  // (FP32 sweeps) or doubles (FP64 sweep)
+  T qp[3] = {T(0), T(0), T(0)};
+  float2 qf[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  double qdd[3] = {0.0, 0.0, 0.0};
+  int since_flush = 0;
+  const unsigned char* mine = s2_smem + (cl0 * BV + 4 * qd_) * int(sizeof(S));
+
+  for (int i = 0; i < nrow; ++i) {
+    const int64_t m = mb + i;
+    const int st = i % RG::NST;
+    if (!mbar_wait(&full[st], unsigned(i / RG::NST) & 1u, a.status)) break;
+    Quad<S> x[NR];
+    float sc[NR];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          ft[i][r] = fc[r * sr + (m + i) * sj];
-          if constexpr (SCALED) sc[i][r] = a.sc_next[(size_t(r) * a.M + m + i) * a.Nc + cc];
-        }
-  };
-  S ft[UNR][NR], fn[UNR][NR];
-  float sc[USC][NR], sn[USC][NR];
-  if (mb * BV + threadIdx.x < me * BV) sv[0][threadIdx.x] = a.vel[mb * BV + threadIdx.x];
-  if (valid) load_rows(mb, ft, sc);
-  int k = 0;
-  for (int64_t m = mb; m < me; m += UNR, ++k) {
-    __syncthreads();  // round k's records are visible; round k - 1's slot is free
-    const int64_t mn = m + UNR;
-    if (mn * BV + threadIdx.x < me * BV) sv[(k + 1) & 1][threadIdx.x] = a.vel[mn * BV + threadIdx.x];
-    if (!valid) continue;
-    if (mn < me) load_rows(mn, fn, sn);
+    for (int r = 0; r < NR; ++r) {
+      x[r] = quad_lds<S>(mine + st * RG::STAGE + r * RG::ROW);
+      if constexpr (SCALED) sc[r] = a.sc_next[(size_t(r) * a.M + m) * a.Nc + cc];
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);   // the warp's values are in registers: the stage may be refilled
+
+    // row part of the velocities (tensor grids)
+    T crow[3] = {T(0), T(0), T(0)}, c2row = T(0), cqrow = T(0), Hrow = pref, Grow = T(0), wrow = T(0);
+    T unrow = T(0), Wrow = T(0);
+    Vel4<T> rv{};
+    if constexpr (TENSOR) {
+      rv = a.rowv[m];
+      const T ur[3] = {T(0), rv.y, rv.z};
 #pragma unroll
-    for (int i = 0; i < UNR; ++i) {
-      if (m + i >= me) break;
-      const Vel4<T> vq = sv[k & 1][i * BV + lane];
-      const bool real_v = (m + i) * BV + lane < a.nv;
-      T f[NR], H;
-      if constexpr (SCALED) {
-        const float u[3] = {vq.x, vq.y, vq.z};
-        const float g = ref_value<D>(Rc, 0, u, real_v);
-#pragma unroll
-        for (int r = 0; r < NR; ++r) f[r] = decode_value(ft[i][r], sc[i][r], r == 0 ? g : Rc.kap * g);
-      } else {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) f[r] = ft[i][r];
+      for (int d = 1; d < D; ++d) {
+        crow[d] = ur[d] - E.U[d];
+        c2row += crow[d] * crow[d];
+        cqrow += crow[d] * E.q[d];
       }
-      if (has_wall)
-        stage2_block<D, NR, true, T>(a, cc, e0, e1, m + i, lane, vq, f, Uc, qc, pref, lam, s0, kap, beta1, inv1, iv,
-                                     qp, H);
-      else
-        stage2_block<D, NR, false, T>(a, cc, e0, e1, m + i, lane, vq, f, Uc, qc, pref, lam, s0, kap, beta1, inv1, iv,
-                                      qp, H);
+      Hrow = pref * t_exp(-lam * c2row);
+      wrow = T(0.5) * rv.w;
+      if constexpr (SCALED) {
+        T g2 = T(0);
+#pragma unroll
+        for (int d = 1; d < D; ++d) g2 += (ur[d] - T(Rc.U[d])) * (ur[d] - T(Rc.U[d]));
+        Grow = T(Rc.pref) * t_exp(-T(Rc.lam) * g2);
+      }
+      if constexpr (WALL) {
+        // u.n = n0 (c_lane + U0) + n1 u1 + n2 u2, and the wall Maxwellian's row factor
+        T w2 = T(0);
+        unrow = wf.n[0] * E.U[0];
+#pragma unroll
+        for (int d = 1; d < D; ++d) {
+          unrow = fma(wf.n[d], ur[d], unrow);
+          w2 += (ur[d] - wf.U[d]) * (ur[d] - wf.U[d]);
+        }
+        Wrow = wf.coef * t_exp(-wf.lam * w2);
+      }
+    }
+    T Se = T(0), Sl = T(0);   // tensor: sum of e and of c_lane e over the thread's 4 velocities
+    // per velocity: the cell's Maxwellian H of W^{n+1}, |c|^2, c.q, the
+    // weight; f~ decoded; then the wall's re-emitted flux subtracted
+    T ft[4][NR], c2v[4], cqv[4], Hv[4], wv[4], uv[4][3];
+    bool real_v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t k = m * BV + 4 * qd_ + j;
+      T g = T(0);
+      real_v[j] = true;
+      uv[j][0] = uv[j][1] = uv[j][2] = T(0);
+      if constexpr (TENSOR) {
+        c2v[j] = fma(cl[j], cl[j], c2row);
+        cqv[j] = fma(cl[j], E.q[0], cqrow);
+        Hv[j] = Hrow * El[j];
+        wv[j] = wl[j];
+        if constexpr (SCALED) g = Grow * Er[j];
+      } else {
+        const Vel4<T> vq = a.vel[k];
+        uv[j][0] = vq.x;
+        uv[j][1] = D > 1 ? vq.y : T(0);
+        uv[j][2] = D > 2 ? vq.z : T(0);
+        real_v[j] = k < a.nv;
+        T c2 = T(0), cq = T(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const T cd = uv[j][d] - E.U[d];
+          c2 += cd * cd;
+          cq += cd * E.q[d];
+        }
+        c2v[j] = c2;
+        cqv[j] = cq;
+        Hv[j] = real_v[j] ? pref * t_exp(-lam * c2) : T(0);
+        wv[j] = T(0.5) * vq.w;   // zero on padding
+        if constexpr (SCALED) {
+          const float uf[3] = {float(uv[j][0]), float(uv[j][1]), float(uv[j][2])};
+          g = ref_value<D>(Rc, 0, uf, real_v[j]);
+        }
+      }
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
-        if constexpr (SCALED) {
-          float scale;
-          fc[r * sr + (m + i) * sj] = encode_value<S>(f[r], r == 0 ? H : kap * H, scale);
-          if (lane == 0) a.sc_next[(size_t(r) * a.M + m + i) * a.Nc + cc] = scale;
+        if constexpr (SCALED)
+          ft[j][r] = decode_value(x[r].v[j], sc[r], r == 0 ? g : T(Rc.kap) * g);
+        else
+          ft[j][r] = T(x[r].v[j]);
+      }
+      if constexpr (WALL) {
+        T un, ew;
+        if constexpr (TENSOR) {
+          un = fma(wf.n[0], cl[j], unrow);
+          ew = Wrow * Ew[j];
         } else {
-          fc[r * sr + (m + i) * sj] = f[r];
+          T w2 = T(0);
+          un = T(0);
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            un = fma(wf.n[d], uv[j][d], un);
+            w2 += (uv[j][d] - wf.U[d]) * (uv[j][d] - wf.U[d]);
+          }
+          ew = wf.coef * t_exp(-wf.lam * w2);
+        }
+        const T out = un < T(0) ? un * ew : T(0);
+        ft[j][0] -= out;
+        if (NR == 2) ft[j][NR - 1] -= wf.kap * out;
+      }
+    }
+    if constexpr (WALL) {
+      // further wall faces of the cell (rare): records re-read per row
+      if (nwall > 1) {
+        if constexpr (TENSOR) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            uv[j][0] = a.lanev[4 * qd_ + j];
+            uv[j][1] = rv.y;
+            uv[j][2] = rv.z;
+          }
+        }
+        const T dt = T(a.g.dt);
+        for (int e = e0; e < e1; ++e) {
+          if (e == ewall || !(a.inc[e].flags & 1)) continue;
+          const int fidx = a.inc[e].face;
+          const FaceGeom<T>& fg = a.fg[fidx];
+          const FacePoly<D, NR, T>& R = static_cast<const FacePoly<D, NR, T>*>(a.fpoly)[fidx];
+          const T coef = a.inc[e].sarea * iv * dt * T(a.Facc[size_t(fidx) * FACC_W + 10]) * R.rho_pref;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            T un = T(0), w2 = T(0);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              un = fma(fg.n[d], uv[j][d], un);
+              w2 += (uv[j][d] - R.U[d]) * (uv[j][d] - R.U[d]);
+            }
+            const T out = un < T(0) ? coef * un * t_exp(-R.lam * w2) : T(0);
+            ft[j][0] -= out;
+            if (NR == 2) ft[j][NR - 1] -= R.kappa * out;
+          }
         }
       }
     }
+    T f1[4][NR];
 #pragma unroll
-    for (int i = 0; i < UNR; ++i)
+    for (int j = 0; j < 4; ++j) {
+      const T s = s0 * cqv[j];
+      const T bh = beta1 * Hv[j];
+      f1[j][0] = (ft[j][0] + bh * fma(s, fma(tl, c2v[j], -T(2 + D)), T(1))) * inv1;
+      if (NR == 2) f1[j][NR - 1] = (ft[j][NR - 1] + kap * bh * fma(s, fma(tl, c2v[j], -T(D)), T(1))) * inv1;
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        ft[i][r] = fn[i][r];
-        if constexpr (SCALED) sc[i][r] = sn[i][r];
+      for (int r = 0; r < NR; ++r) f1[j][r] = real_v[j] ? f1[j][r] : T(0);
+      const T e_ = wv[j] * fma(c2v[j], f1[j][0], NR == 2 ? f1[j][NR - 1] : T(0));
+      if constexpr (TENSOR) {
+        Se += e_;
+        Sl = fma(cl[j], e_, Sl);
+      } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) qp[d] = fma(uv[j][d] - E.U[d], e_, qp[d]);
       }
-    if ((k & 3) == 3) {  // flush the per-lane partial sums every 32 blocks
+    }
+    if constexpr (TENSOR) {
+      qp[0] = fma(Sl, wrow, qp[0]);
+      const T sw = Se * wrow;
+#pragma unroll
+      for (int d = 1; d < D; ++d) qp[d] = fma(crow[d], sw, qp[d]);
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      Quad<S> y;
+      if constexpr (SCALED) {
+        float dev[4], mx = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          dev[j] = f1[j][r] - (r == 0 ? Hv[j] : kap * Hv[j]);
+          mx = fmaxf(mx, fabsf(dev[j]));
+        }
+        float scale = max8(mx);
+        if (scale < kScaleFloor) scale = 0.f;
+        const float inv = scale > 0.f ? 1.f / scale : 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y.v[j] = StoreTraits<S>::from_f(dev[j] * inv);
+        if (qd_ == 0 && valid) a.sc_next[(size_t(r) * a.M + m) * a.Nc + cc] = scale;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y.v[j] = S(f1[j][r]);
+      }
+      if (valid) quad_store(fc + r * sr + m * sj, y);
+    }
+    if (++since_flush == kS2Flush) {
+      since_flush = 0;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         if constexpr (sizeof(T) == 4)
           qf[d] = pair_add(qf[d], float(qp[d]));
         else
-          qd[d] += double(qp[d]);
+          qdd[d] += double(qp[d]);
         qp[d] = T(0);
       }
     }
   }
-  if (!valid) return;
+
+  // sum over the cell's 8 threads
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     if constexpr (sizeof(T) == 4) {
       float2 v = pair_add(qf[d], float(qp[d]));
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int o = 1; o < 8; o <<= 1) {
         const float2 w = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
         v = pair_add(v, w);
       }
-      qd[d] = double(v.x) + double(v.y);
+      qdd[d] = double(v.x) + double(v.y);
     } else {
-      qd[d] = warp_sum(qd[d] + double(qp[d]));
+      double v = qdd[d] + double(qp[d]);
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      qdd[d] = v;
     }
   }
+  if (!valid || qd_ != 0) return;
   double* qo = a.qpart + (size_t(chunk) * a.Nc + c) * 3;
-  if (lane < 3) qo[lane] = lane < D ? (lane == 0 ? qd[0] : lane == 1 ? qd[D > 1 ? 1 : 0] : qd[D > 2 ? 2 : 0]) : 0.0;
+  qo[0] = qdd[0];
+  qo[1] = D > 1 ? qdd[D > 1 ? 1 : 0] : 0.0;
+  qo[2] = D > 2 ? qdd[D > 2 ? 2 : 0] : 0.0;
 }
 
 // Heat flux of f^{n+1}: the chunks' partial sums added in chunk order.
@@ -1563,15 +1793,36 @@ cudaError_t launch_bconserve(cudaStream_t s, const BlockedArgs<T>& a) {
   return cudaGetLastError();
 }
 
+template <int D, int NR, bool TENSOR, typename T, typename S>
+cudaError_t launch_bstage2_tpl(cudaStream_t s, const BlockedArgs<T>& a) {
+  constexpr int smem = S2Ring<NR, S>::BYTES;
+  static bool attr = false;   // per instantiation
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_bstage2<D, NR, TENSOR, false, T, S>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_bstage2<D, NR, TENSOR, true, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const dim3 grid(unsigned((a.Nc + kS2Cells - 1) / kS2Cells), unsigned(a.nchunk));
+  k_bstage2<D, NR, TENSOR, false, T, S><<<grid, kS2Threads, smem, s>>>(a);
+  k_bstage2<D, NR, TENSOR, true, T, S><<<grid, kS2Threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T, typename S>
 cudaError_t launch_bstage2(cudaStream_t s, const BlockedArgs<T>& a) {
-  const dim3 grid(blocked_warp_grid(a.Nc), unsigned(a.nchunk));
   const int D = a.g.D, NR = a.g.NR;
-  if (D == 1 && NR == 2) k_bstage2<1, 2, T, S><<<grid, kBlockedThreads, 0, s>>>(a);
-  else if (D == 2 && NR == 2) k_bstage2<2, 2, T, S><<<grid, kBlockedThreads, 0, s>>>(a);
-  else if (D == 3 && NR == 1) k_bstage2<3, 1, T, S><<<grid, kBlockedThreads, 0, s>>>(a);
-  else if (D == 3 && NR == 2) k_bstage2<3, 2, T, S><<<grid, kBlockedThreads, 0, s>>>(a);
-  else return cudaErrorInvalidValue;
+  const bool ten = a.tensor != 0;
+  cudaError_t e = cudaErrorInvalidValue;
+#define UGKS_S2(d, nr)                                                                     \
+  if (D == d && NR == nr)                                                                  \
+    e = ten ? launch_bstage2_tpl<d, nr, true, T, S>(s, a) : launch_bstage2_tpl<d, nr, false, T, S>(s, a);
+  UGKS_S2(1, 2) UGKS_S2(2, 2) UGKS_S2(3, 1) UGKS_S2(3, 2)
+#undef UGKS_S2
+  if (e != cudaSuccess) return e;
   k_bqsum<T><<<unsigned((int64_t(a.Nc) * 3 + 255) / 256), 256, 0, s>>>(a);
   return cudaGetLastError();
 }

@@ -72,6 +72,9 @@ struct ugks_ctx {
   // velocities
   double *d_u = nullptr, *d_wgt = nullptr, *d_ux = nullptr, *d_uy = nullptr, *d_uz = nullptr, *d_wp = nullptr;
   void *d_uxT = nullptr, *d_uyT = nullptr, *d_uzT = nullptr, *d_wT = nullptr, *d_velT = nullptr;
+  // tensor grid whose fastest axis has BV points: per-row and per-lane tables
+  int tensor = 0;
+  void *d_rowv = nullptr, *d_lanev = nullptr;
   // distributions
   void* d_f[2] = {nullptr, nullptr};
   // scaled (FP16 / BF16) storage: per-row scales and per-cell reference Maxwellians
@@ -329,6 +332,35 @@ size_t blocked_X_bytes(const ugks_ctx* ctx) {
 size_t blocked_Facc_bytes(const ugks_ctx* ctx) { return size_t(ctx->Nf) * FACC_W * sizeof(double); }
 size_t blocked_qpart_bytes(const ugks_ctx* ctx) { return size_t(ctx->nchunk) * ctx->Nc * 3 * sizeof(double); }
 
+// Tensor grids whose fastest axis has BV points and no padding: every row of
+// BV velocities is one line along that axis.  Splits the velocities into the
+// lane component (the same in every row) and the row components (the same
+// along a row), and the weights into lane and row factors (w = lane_w[l] *
+// row_w[m], checked to 1e-13 relative).  Returns false for other grids.
+bool split_tensor_rows(int64_t nv, int64_t M, const double* ux, const double* uy, const double* uz,
+                       const double* wp, std::vector<double>& lane, std::vector<double>& rows) {
+  if (nv != M * BV || !(wp[0] > 0.0)) return false;
+  lane.assign(2 * BV, 0.0);
+  rows.assign(size_t(M) * 4, 0.0);
+  for (int l = 0; l < BV; ++l) {
+    lane[l] = ux[l];
+    lane[BV + l] = wp[l];
+  }
+  for (int64_t m = 0; m < M; ++m) {
+    const int64_t k0 = m * BV;
+    rows[m * 4 + 1] = uy[k0];
+    rows[m * 4 + 2] = uz[k0];
+    rows[m * 4 + 3] = wp[k0] / wp[0];
+    for (int l = 0; l < BV; ++l) {
+      const int64_t k = k0 + l;
+      if (ux[k] != ux[l] || uy[k] != uy[k0] || uz[k] != uz[k0]) return false;
+      const double w = lane[BV + l] * rows[m * 4 + 3];
+      if (!(std::fabs(w - wp[k]) <= 1e-13 * std::fabs(wp[k]))) return false;
+    }
+  }
+  return true;
+}
+
 template <typename T, typename S>
 ugks_status build_typed(ugks_ctx* ctx, const std::vector<int64_t>& cf_off, const std::vector<CellFace>& cf,
                         const std::vector<double>& eps2,
@@ -388,6 +420,20 @@ ugks_status build_typed(ugks_ctx* ctx, const std::vector<int64_t>& cf_off, const
     Vel4<T>* dv;
     CUDA_TRY(ctx, upload(ctx, &dv, vel.data(), Mp * sizeof(Vel4<T>)));
     ctx->d_velT = dv;
+    std::vector<double> lane, rows;
+    ctx->tensor = split_tensor_rows(ctx->nv, ctx->M, ux, uy, uz, wp, lane, rows) ? 1 : 0;
+    if (ctx->tensor) {
+      std::vector<T> laneT(lane.begin(), lane.end());
+      std::vector<Vel4<T>> rowT(ctx->M);
+      for (int64_t m = 0; m < ctx->M; ++m)
+        rowT[m] = Vel4<T>{T(0), T(rows[m * 4 + 1]), T(rows[m * 4 + 2]), T(rows[m * 4 + 3])};
+      Vel4<T>* dr;
+      T* dl;
+      CUDA_TRY(ctx, upload(ctx, &dr, rowT.data(), rowT.size() * sizeof(Vel4<T>)));
+      CUDA_TRY(ctx, upload(ctx, &dl, laneT.data(), laneT.size() * sizeof(T)));
+      ctx->d_rowv = dr;
+      ctx->d_lanev = dl;
+    }
   }
   if (ctx->variant == 1) {
     FaceRec<T>* fr;
@@ -519,6 +565,9 @@ ugks_status sweep_blocked(ugks_ctx* ctx, int cur, void* X, double* Facc, double*
   a.cp_next = ctx->d_cp[1];
   a.q_next = ctx->d_q[nxt];
   a.vel = static_cast<const Vel4<T>*>(ctx->d_velT);
+  a.tensor = ctx->tensor;
+  a.rowv = static_cast<const Vel4<T>*>(ctx->d_rowv);
+  a.lanev = static_cast<const T*>(ctx->d_lanev);
   a.vol = ctx->d_vol;
   a.eps2 = static_cast<const T*>(ctx->d_eps2);
   a.cf_off = ctx->d_cf_off32;
@@ -681,7 +730,11 @@ ugks_status step_typed_static(ugks_ctx* ctx, unsigned char* base) {
     ugks_status st = sweep_blocked<T, S>(ctx, cur, X, reinterpret_cast<double*>(Facc), reinterpret_cast<double*>(qpart));
     ctx->stats_on = was_on;
     if (st != UGKS_OK) return st;
-    ctx->last_facc = reinterpret_cast<double*>(Facc);
+    // The shared array is overwritten by the next static step of any context:
+    // keep this step's face accumulators (wall fluxes for ugks_surface) in the
+    // context's own buffer, allocated at create.
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_Facc_b, Facc, blocked_Facc_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->last_facc = ctx->d_Facc_b;
     launch_residual_finalize(ctx->stream, ctx->D + 2, ctx->Nc, ctx->d_res_acc, ctx->d_res);
     CUDA_TRY(ctx, cudaGetLastError());
     ctx->cur = nxt;
@@ -736,6 +789,8 @@ ugks_status check_status(ugks_ctx* ctx) {
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   int st = 0;
   CUDA_TRY(ctx, cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & 2)
+    return fail(ctx, UGKS_ERR_TIMEOUT, "a bounded device wait (shared-memory staging) gave up; results are invalid");
   if (st) return fail(ctx, UGKS_ERR_NONFINITE, "non-physical state (rho <= 0, T <= 0 or NaN) was produced");
   return UGKS_OK;
 }
@@ -923,13 +978,14 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
   CUDA_TRY(ctx, cudaGetDevice(&dev));
   CUDA_TRY(ctx, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   ctx->nsm = nsm;
-  // Velocity chunks of the second stage (grid: 8 cells per CTA x chunks):
-  // just enough chunks for ~32 CTAs per SM, so that each CTA walks as many
-  // blocks as it can (its set-up and the heat-flux reduction are per CTA).
+  // Velocity chunks of the second stage (grid: 32 cells per CTA x chunks):
+  // enough chunks for about 8 waves of 4 CTAs per SM, so that the last wave
+  // is a small part of the pass, and no more (each CTA's set-up and
+  // heat-flux reduction are per chunk).
   {
-    const int64_t cell_ctas = (Nc + 7) / 8;
+    const int64_t cell_ctas = (Nc + 31) / 32;
     int64_t chunks = 1;
-    while (chunks < 8 && cell_ctas * chunks < int64_t(32) * nsm) chunks *= 2;
+    while (chunks < 16 && cell_ctas * chunks < int64_t(32) * nsm) chunks *= 2;
     ctx->nchunk = int(std::min<int64_t>(ctx->M, chunks));
   }
   int smem_optin = 0;

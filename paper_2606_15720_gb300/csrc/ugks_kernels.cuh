@@ -111,6 +111,12 @@ struct BlockedArgs {
   CellPrim* cp_next;             // primitive record of W^{n+1}
   double* q_next;                // [Nc][3] heat flux of f^{n+1}
   const Vel4<T>* vel;            // [M*BV] velocities and weights (padded: zero)
+  // tensor grids whose fastest axis has BV points (no padding): every row of
+  // BV velocities is one line along that axis, u = (lanev[l], rowv[m].y,
+  // rowv[m].z) and weight = lanev[BV + l] * rowv[m].w
+  int tensor;
+  const Vel4<T>* rowv;           // [M] row components (y, z) and row weight factor (w)
+  const T* lanev;                // [2][BV] lane-axis values, lane weight factors
   const double* vol;
   const T* eps2;                 // limiter constant (K_v |Omega|^(1/D))^3 per cell
   const int32_t* cf_off;         // per cell incidence CSR

@@ -1,7 +1,8 @@
 """The arithmetic behind bench.py's roofline fields, on synthetic timings
 (no GPU): achieved rates follow from the stated work per DOF, the DOF one
-launch processes and the mean launch time; the dominant kernel is the one
-with the most time per step."""
+launch processes and the mean launch time; the headline roofline is the whole
+step's algorithmic bytes (16 per DOF in FP32) over ms_per_step against the
+HBM peak; the dominant kernel is the one with the most time per step."""
 import importlib.util
 import os
 import types
@@ -26,14 +27,16 @@ def _mesh(n_cells, n_faces, n_boundary):
     return types.SimpleNamespace(n_cells=n_cells, n_faces=n_faces, face_neighbor=nb)
 
 
-def test_per_kernel_rates_and_the_dominant_kernel(bench):
+def test_per_kernel_rates_and_the_dominant_kernel(bench, monkeypatch):
+    monkeypatch.setattr(bench, "recorded_traffic", lambda: {})   # no ncu record
     mesh = _mesh(1000, 2100, 100)                    # 2 x 2100 - 100 = 4100 incidences: 4.1 per cell
     grid = types.SimpleNamespace(n_v=4096)
     dof, steps = mesh.n_cells * grid.n_v, 10
     # (ms in total, launches) over the 10 steps: 16 blocks per step
     stats = {"block_reconstruction": (200.0, 160), "block_fluxes": (150.0, 160), "block_stage1": (80.0, 160),
              "stage2": (100.0, 10), "velocity_block_sweep": (540.0, 10)}
-    roofline, kernels, step = bench.rooflines(stats, mesh, grid, dof, steps)
+    ms_per_step = 55.0
+    roofline, kernels, step = bench.rooflines(stats, mesh, grid, dof, steps, ms_per_step)
     hbm_peak, _, fp32_peak = bench.load_peaks()
     inc = 4100 / 1000
     k = kernels["block_reconstruction"]
@@ -46,14 +49,37 @@ def test_per_kernel_rates_and_the_dominant_kernel(bench):
     assert s2["bytes_per_dof"] == 8                  # read f~, write f^{n+1} in FP32
     assert s2["hbm_gbs"] == pytest.approx(8 * dof / (100.0 / 10 * 1e-3) / 1e9)
     assert s2["hbm_frac"] == pytest.approx(s2["hbm_gbs"] / hbm_peak)
-    # the reconstruction has the most time per step: it is the reported kernel
-    assert roofline["kernel"] == "block_reconstruction" and roofline["bound"] == "alu"
-    assert roofline["frac"] == pytest.approx(k["alu_frac"])
-    assert roofline["algorithmic_flops_per_launch"] == pytest.approx(k["flops_per_dof"] * dof_launch)
+    # headline: 16 B per DOF over ms_per_step against the HBM peak
+    assert roofline["bound"] == "hbm" and roofline["unit"] == "GB/s"
+    assert roofline["achieved"] == pytest.approx(16 * dof / (ms_per_step * 1e-3) / 1e9)
+    assert roofline["frac"] == pytest.approx(roofline["achieved"] / hbm_peak)
+    assert roofline["algorithmic_bytes_per_step"] == 16 * dof
+    # the reconstruction has the most time per step: it is the dominant kernel;
+    # without measured DRAM bytes it carries no algorithmic bytes and is ALU-bound
+    assert step["dominant_kernel"] == "block_reconstruction" and k["bound"] == "alu"
     # whole step: 16 B per DOF against HBM, the sum of the kernels' flops against FP32
     t = 540.0 / 10 * 1e-3
     assert step["hbm"]["achieved_gbs"] == pytest.approx(16 * dof / t / 1e9)
     assert step["alu"]["flops_per_dof"] == pytest.approx(sum(v["flops_per_dof"] for v in kernels.values()))
+
+
+def test_measured_dram_bytes_set_the_kernel_bound_and_step_traffic(bench, monkeypatch):
+    mesh = _mesh(1000, 2100, 100)
+    grid = types.SimpleNamespace(n_v=4096)
+    dof, steps = mesh.n_cells * grid.n_v, 10
+    stats = {"block_reconstruction": (200.0, 160), "block_fluxes": (150.0, 160), "block_stage1": (80.0, 160),
+             "stage2": (100.0, 10), "velocity_block_sweep": (540.0, 10)}
+    # DRAM bytes per launch far above what the ALU time covers at the peaks
+    dram = {"block_reconstruction": 4e9, "block_fluxes": 1e6, "block_stage1": 2e6, "stage2": 3e7}
+    monkeypatch.setattr(bench, "recorded_traffic", lambda: dram)
+    roofline, kernels, _ = bench.rooflines(stats, mesh, grid, dof, steps, 55.0)
+    hbm_peak, _, _ = bench.load_peaks()
+    k = kernels["block_reconstruction"]
+    assert k["dram_gbs"] == pytest.approx(4e9 / (200.0 / 160 * 1e-3) / 1e9)
+    assert k["dram_frac"] == pytest.approx(k["dram_gbs"] / hbm_peak)
+    assert k["bound"] == "hbm" and kernels["block_fluxes"]["bound"] == "alu"
+    # per step: 16 launches of each block kernel, one second stage
+    assert roofline["traffic"] == pytest.approx(16 * (4e9 + 1e6 + 2e6) + 3e7)
 
 
 def test_launch_count_of_the_blocked_sweep(bench):
