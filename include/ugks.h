@@ -56,7 +56,7 @@ enum { UGKS_BC_WALL = 1, UGKS_BC_FARFIELD = 2, UGKS_BC_OUTFLOW = 3 };
 enum { UGKS_MODEL_BGK = 0, UGKS_MODEL_SHAKHOV = 1 };
 enum { UGKS_LIMITER_NONE = 0, UGKS_LIMITER_VENKATAKRISHNAN = 1, UGKS_LIMITER_BARTH_JESPERSEN = 2 };
 enum { UGKS_STORAGE_F64 = 0, UGKS_STORAGE_F32 = 1, UGKS_STORAGE_F16 = 2, UGKS_STORAGE_BF16 = 3 };
-enum { UGKS_SWEEP_AUTO = 0, UGKS_SWEEP_TILED = 1, UGKS_SWEEP_BLOCKED = 2 };
+enum { UGKS_SWEEP_AUTO = 0, UGKS_SWEEP_TILED = 1, UGKS_SWEEP_BLOCKED = 2, UGKS_SWEEP_BLOCKED_FUSED = 3 };
 
 /* Boundary condition of the faces whose neighbour is -(index+1).
  * WALL: diffuse isothermal wall (Sec. 2.1, Eq. 36-38) with wall velocity u
@@ -120,10 +120,15 @@ typedef struct {
  *     8 faces per cell.  Moments, W and the interface coefficients stay FP64.
  *   tile_cells: cells per tile of the tiled sweep, 0 = automatic
  *   sweep: device organisation of the velocity-block sweep (Sec. 2.2.2,
- *     Table B.1), UGKS_SWEEP_*: BLOCKED runs gradients, fluxes and the first
- *     stage of each velocity block as three grid-wide kernels; TILED runs one
+ *     Table B.1), UGKS_SWEEP_*: BLOCKED runs, per velocity block, the
+ *     reconstruction (K2), the micro fluxes of every face (K1, written to a
+ *     per-face buffer) and the first stage (K3) as three grid-wide kernels;
+ *     BLOCKED_FUSED runs K1 and K3 as one kernel in which each cell evaluates
+ *     the fluxes of its own faces (an interior face is evaluated by both of
+ *     its cells, its moments added by the owner; the same arithmetic, one
+ *     DRAM pass over the per-face buffer instead of three); TILED runs one
  *     persistent kernel over spatial tiles held in shared memory; AUTO picks
- *     BLOCKED.  Both give the same result up to rounding order.
+ *     BLOCKED.  All give the same result up to rounding order.
  *   block_velocities: velocities per block of the blocked sweep (32, 64,
  *     128, or 256 for dim 3 with one reduced distribution (K_xi = 0);
  *     0 = automatic: 256 where allowed, else 128) */

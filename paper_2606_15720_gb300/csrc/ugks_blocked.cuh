@@ -352,6 +352,52 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Tensor grids (a row of 32 velocities is one line along the fastest axis,
+// the lane axis): with c = u - U0 split into its lane component c0 and its
+// row components, the equilibrium part of a face factors as
+//   g0(u) P_r(c) = [rho_pref exp(-lam |c_row|^2)] exp(-lam c0^2) sum_a c0^a Q_{r,a}(c_row),
+// Q_{r,a} the polynomial of the coefficients of c0^a (degree <= 3 - a in the
+// row components).  Per face, one lane per row evaluates that row's factors
+// and publishes them in shared memory; every lane then needs one exponential
+// per face and three FMA per velocity for the cubic.  The flux moments
+// factor the same way: sums over the lane's rows with the row weight, times
+// the lane's weight and velocity once per face.
+template <int NR, typename T>
+struct __align__(16) RowFac {
+  T Q[NR][4];     // row polynomials times rho_pref exp(-lam |c_row|^2)
+  T un;           // row part of u . n
+  T w;            // row weight factor
+  T wu1, wu2;     // w u_1, w u_2 (row components of u)
+  T wusq;         // w |u_row|^2
+  T pad[(4 - (4 * NR + 5) % 4) % 4];
+};
+
+// Q_a(c1, c2) of one face polynomial (coefficients in mono_index order).
+template <int D, typename T>
+__device__ __forceinline__ void row_polys(const T (&p)[NPoly<D>::value], T c1, T c2, T (&Q)[4]) {
+#pragma unroll
+  for (int a = 0; a <= 3; ++a) {
+    if constexpr (D == 1) {
+      Q[a] = p[a];
+    } else if constexpr (D == 2) {
+      T q = p[mono_index<2>(a, 3 - a, 0)];
+#pragma unroll
+      for (int e1 = 2 - a; e1 >= 0; --e1) q = fma(q, c1, p[mono_index<2>(a, e1, 0)]);
+      Q[a] = q;
+    } else {
+      T q = T(0);
+#pragma unroll
+      for (int e1 = 3 - a; e1 >= 0; --e1) {
+        T in = p[mono_index<3>(a, e1, 3 - a - e1)];
+#pragma unroll
+        for (int e2 = 2 - a - e1; e2 >= 0; --e2) in = fma(in, c2, p[mono_index<3>(a, e1, e2)]);
+        q = e1 == 3 - a ? in : fma(q, c1, in);
+      }
+      Q[a] = q;
+    }
+  }
+}
+
 // Shared-memory stage of one face: [FacePoly][FaceGeom][X rows][accumulators].
 template <int D, int NR, int VB, typename T>
 struct FluxStage {
@@ -398,23 +444,22 @@ __device__ __forceinline__ void facc_add(double* dst, const double* prev, bool f
   }
 }
 
+// Micro fluxes of one face for this lane's velocities of the block (Eq. 28-29,
+// 32-38), time-integrated and without the face area, in the face's
+// orientation (u.n with the normal from owner to neighbour): Phi[r][j] for
+// velocity (m0 + j) 32 + lane.  Xs: this lane's column of the face's rows of
+// upwind free-transport parts (written by the reconstruction).  Every caller
+// runs the same code on the same inputs, so both cells of a face obtain
+// bitwise the same fluxes.  With `moments` the block's weighted moments of
+// the flux are added to m_in (conservative-variable order, energy at D + 1)
+// and, at a diffuse wall, those of the unit-density re-emitted half to m_out.
 template <int D, int NR, int VB, typename T>
-__device__ __forceinline__ void flux_face(const BlockedArgs<T>& a, const int f, const unsigned char* st,
-                                          const BlockVel<D, NR, VB, T>& v, const int first, const int lane) {
-  using S = FluxStage<D, NR, VB, T>;
-  constexpr int NW = D + 2;
-  const FacePoly<D, NR, T>& R = *reinterpret_cast<const FacePoly<D, NR, T>*>(st);
-  const FaceGeom<T>& fg = *reinterpret_cast<const FaceGeom<T>*>(st + S::SP);
-  const T* Xs = reinterpret_cast<const T*>(st + S::SP + S::SG) + lane;
-  const double* Fs = reinterpret_cast<const double*>(st + S::SP + S::SG + S::SX);
-  const int idx8 = sum8_index(lane);
-  const bool writer = (lane & 3) == 0 && idx8 < NW;
-  double* Fa = a.Facc + size_t(f) * FACC_W;
+__device__ __forceinline__ void face_fluxes(const BlockedArgs<T>& a, const FacePoly<D, NR, T>& R,
+                                            const FaceGeom<T>& fg, const T* Xs, const BlockVel<D, NR, VB, T>& v,
+                                            const int lane, const int64_t m0, RowFac<NR, T>* rowbuf, const T ul,
+                                            const T wl, const bool moments, T (&Phi)[NR][VB], T (&m_in)[NWP],
+                                            T (&m_out)[NWP]) {
   const T dt = T(a.g.dt);
-  T* Xf = a.X + size_t(f) * (NR * VB * BV) + lane;
-  T m_in[NWP], m_out[NWP];  // moments of the block, conservative variable order (energy at D + 1)
-#pragma unroll
-  for (int t = 0; t < NWP; ++t) m_in[t] = m_out[t] = T(0);
   T n[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) n[d] = fg.n[d];
@@ -422,7 +467,7 @@ __device__ __forceinline__ void flux_face(const BlockedArgs<T>& a, const int f, 
   if (fg.bc_type == 1) {
     // diffuse wall (Eq. 36-38): free transport on the incoming side; the
     // re-emitted half is the unit-density wall Maxwellian, scaled by rho_w
-    // once all blocks are summed.
+    // once all blocks are summed (added in the second stage).
 #pragma unroll
     for (int j = 0; j < VB; ++j) {
       T un = T(0);
@@ -432,35 +477,86 @@ __device__ __forceinline__ void flux_face(const BlockedArgs<T>& a, const int f, 
       if (un > T(0)) {
         phi_h = un * Xs[(0 * VB + j) * BV];
         if (NR == 2) phi_b = un * Xs[((NR - 1) * VB + j) * BV];
-      } else if (un < T(0)) {
+      } else if (un < T(0) && moments) {
         T c2 = T(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) c2 += (v.u[j][d] - R.U[d]) * (v.u[j][d] - R.U[d]);
         out_h = un * dt * R.rho_pref * t_exp(-R.lam * c2);
       }
-      Xf[(0 * VB + j) * BV] = phi_h;
-      if (NR == 2) Xf[((NR - 1) * VB + j) * BV] = phi_b;
-      const T wph = v.w[j] * phi_h, wpo = v.w[j] * out_h;
-      m_in[0] += wph;
-      m_out[0] += wpo;
+      Phi[0][j] = phi_h;
+      if (NR == 2) Phi[NR - 1][j] = phi_b;
+      if (moments) {
+        const T wph = v.w[j] * phi_h, wpo = v.w[j] * out_h;
+        m_in[0] += wph;
+        m_out[0] += wpo;
 #pragma unroll
-      for (int d = 0; d < D; ++d) {
-        m_in[1 + d] += wph * v.u[j][d];
-        m_out[1 + d] += wpo * v.u[j][d];
+        for (int d = 0; d < D; ++d) {
+          m_in[1 + d] += wph * v.u[j][d];
+          m_out[1 + d] += wpo * v.u[j][d];
+        }
+        m_in[D + 1] += T(0.5) * v.w[j] * (v.u2[j] * phi_h + phi_b);
+        m_out[D + 1] += T(0.5) * v.w[j] * (v.u2[j] * out_h + R.kappa * out_h);
       }
-      m_in[D + 1] += T(0.5) * v.w[j] * (v.u2[j] * phi_h + phi_b);
-      m_out[D + 1] += T(0.5) * v.w[j] * (v.u2[j] * out_h + R.kappa * out_h);
-    }
-    const T sin = warp_sum8<T>(m_in[0], m_in[1], m_in[2], m_in[3], m_in[4], T(0), T(0), T(0), lane);
-    const T sout = warp_sum8<T>(m_out[0], m_out[1], m_out[2], m_out[3], m_out[4], T(0), T(0), T(0), lane);
-    if (writer) {
-      facc_add<T>(Fa + idx8, Fs + idx8, first, sin);
-      facc_add<T>(Fa + 5 + idx8, Fs + 5 + idx8, first, sout);
     }
     return;
   }
 
   const bool ghost = fg.nei < 0;
+  if (!ghost && a.tensor) {
+    // interior face on a tensor grid: lanes 0 .. VB-1 publish the row factors
+    // (row polynomials times the row's Maxwellian factor, u.n and weight parts)
+    __syncwarp();   // earlier readers of rowbuf are done
+    if (lane < VB) {
+      const Vel4<T> rv = a.rowv[m0 + lane];
+      const T c1 = D > 1 ? rv.y - R.U[D > 1 ? 1 : 0] : T(0), c2 = D > 2 ? rv.z - R.U[D > 2 ? 2 : 0] : T(0);
+      RowFac<NR, T> rf;
+      const T E = R.rho_pref * t_exp(-R.lam * (c1 * c1 + c2 * c2));
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        row_polys<D, T>(R.P[r], c1, c2, rf.Q[r]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rf.Q[r][q] *= E;
+      }
+      rf.un = (D > 1 ? n[D > 1 ? 1 : 0] * rv.y : T(0)) + (D > 2 ? n[D > 2 ? 2 : 0] * rv.z : T(0));
+      rf.w = rv.w;
+      rf.wu1 = rv.w * rv.y;
+      rf.wu2 = rv.w * rv.z;
+      rf.wusq = rv.w * (rv.y * rv.y + rv.z * rv.z);
+#pragma unroll
+      for (int q = 0; q < int(sizeof(rf.pad) / sizeof(T)); ++q) rf.pad[q] = T(0);
+      rowbuf[lane] = rf;
+    }
+    __syncwarp();
+    const T c0 = ul - R.U[0];
+    const T El = t_exp(-R.lam * c0 * c0);
+    const T un0 = n[0] * ul;
+    T A0 = T(0), A1 = T(0), A2 = T(0), A4 = T(0);   // sums over the lane's rows, lane weight factored out
+#pragma unroll
+    for (int j = 0; j < VB; ++j) {
+      const RowFac<NR, T> rf = rowbuf[j];
+      const T un = un0 + rf.un;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const T P = fma(c0, fma(c0, fma(c0, rf.Q[r][3], rf.Q[r][2]), rf.Q[r][1]), rf.Q[r][0]);
+        Phi[r][j] = un * fma(El, P, Xs[(r * VB + j) * BV]);
+      }
+      if (moments) {
+        A0 = fma(rf.w, Phi[0][j], A0);
+        if (D > 1) A1 = fma(rf.wu1, Phi[0][j], A1);
+        if (D > 2) A2 = fma(rf.wu2, Phi[0][j], A2);
+        A4 = fma(rf.wusq, Phi[0][j], A4);
+        if (NR == 2) A4 = fma(rf.w, Phi[NR - 1][j], A4);
+      }
+    }
+    if (moments) {
+      m_in[0] += wl * A0;
+      m_in[1] += wl * ul * A0;
+      if (D > 1) m_in[2] += wl * A1;
+      if (D > 2) m_in[3] += wl * A2;
+      m_in[D + 1] += T(0.5) * wl * fma(ul * ul, A0, A4);
+    }
+    return;
+  }
   if (!ghost) {
     // interior face: straight-line code (u.n = 0 gives a zero flux by itself)
 #pragma unroll
@@ -475,20 +571,17 @@ __device__ __forceinline__ void flux_face(const BlockedArgs<T>& a, const int f, 
         c2 += c[d] * c[d];
       }
       const T H0 = R.rho_pref * t_exp(-R.lam * c2);
-      const T phi_h = un * fma(H0, horner_cubic<D, T>(R.P[0], c[0], c[1], c[2]), Xs[(0 * VB + j) * BV]);
-      T phi_b = T(0);
-      if (NR == 2)
-        phi_b = un * fma(H0, horner_cubic<D, T>(R.P[NR - 1], c[0], c[1], c[2]), Xs[((NR - 1) * VB + j) * BV]);
-      Xf[(0 * VB + j) * BV] = phi_h;
-      if (NR == 2) Xf[((NR - 1) * VB + j) * BV] = phi_b;
-      const T wph = v.w[j] * phi_h;
-      m_in[0] += wph;
 #pragma unroll
-      for (int d = 0; d < D; ++d) m_in[1 + d] += wph * v.u[j][d];
-      m_in[D + 1] += T(0.5) * v.w[j] * (v.u2[j] * phi_h + phi_b);
+      for (int r = 0; r < NR; ++r)
+        Phi[r][j] = un * fma(H0, horner_cubic<D, T>(R.P[r], c[0], c[1], c[2]), Xs[(r * VB + j) * BV]);
+      if (moments) {
+        const T wph = v.w[j] * Phi[0][j];
+        m_in[0] += wph;
+#pragma unroll
+        for (int d = 0; d < D; ++d) m_in[1 + d] += wph * v.u[j][d];
+        m_in[D + 1] += T(0.5) * v.w[j] * (v.u2[j] * Phi[0][j] + (NR == 2 ? Phi[NR - 1][j] : T(0)));
+      }
     }
-    const T sm = warp_sum8<T>(m_in[0], m_in[1], m_in[2], m_in[3], m_in[4], T(0), T(0), T(0), lane);
-    if (writer) facc_add<T>(Fa + idx8, Fs + idx8, first, sm);
     return;
   }
   T gr = T(0), gl = T(0), gU[3] = {T(0), T(0), T(0)}, gk = T(0);
@@ -508,7 +601,7 @@ __device__ __forceinline__ void flux_face(const BlockedArgs<T>& a, const int f, 
     T phi_h = T(0), phi_b = T(0);
     if (un != T(0)) {
       T tr[NR];
-      if (un > T(0) || !ghost) {
+      if (un > T(0)) {
 #pragma unroll
         for (int r = 0; r < NR; ++r) tr[r] = Xs[(r * VB + j) * BV];
       } else {
@@ -530,17 +623,57 @@ __device__ __forceinline__ void flux_face(const BlockedArgs<T>& a, const int f, 
       phi_h = un * fma(H0, horner_cubic<D, T>(R.P[0], c[0], c[1], c[2]), tr[0]);
       if (NR == 2) phi_b = un * fma(H0, horner_cubic<D, T>(R.P[NR - 1], c[0], c[1], c[2]), tr[NR - 1]);
     }
-    Xf[(0 * VB + j) * BV] = phi_h;
-    if (NR == 2) Xf[((NR - 1) * VB + j) * BV] = phi_b;
-    const T wph = v.w[j] * phi_h;
-    m_in[0] += wph;
+    Phi[0][j] = phi_h;
+    if (NR == 2) Phi[NR - 1][j] = phi_b;
+    if (moments) {
+      const T wph = v.w[j] * phi_h;
+      m_in[0] += wph;
 #pragma unroll
-    for (int d = 0; d < D; ++d) m_in[1 + d] += wph * v.u[j][d];
-    m_in[D + 1] += T(0.5) * v.w[j] * (v.u2[j] * phi_h + phi_b);
+      for (int d = 0; d < D; ++d) m_in[1 + d] += wph * v.u[j][d];
+      m_in[D + 1] += T(0.5) * v.w[j] * (v.u2[j] * phi_h + phi_b);
+    }
   }
-  // value index t of the reduction is conservative variable t (energy at D + 1)
-  const T sm = warp_sum8<T>(m_in[0], m_in[1], m_in[2], m_in[3], m_in[4], T(0), T(0), T(0), lane);
-  if (writer) facc_add<T>(Fa + idx8, Fs + idx8, first, sm);
+}
+
+// Adds the block's moments of one face (per-lane partials, reduced over the
+// warp) to its accumulator: slots [0, D+2) the flux, [5, 5+D+2) at a wall the
+// unit re-emitted half.  Fs: the accumulator as it was before this block
+// (ignored on the first block).
+template <int D, typename T>
+__device__ __forceinline__ void face_moments_add(double* Fa, const double* Fs, bool wall, int first,
+                                                 const T (&m_in)[NWP], const T (&m_out)[NWP], int lane) {
+  constexpr int NW = D + 2;
+  const int idx8 = sum8_index(lane);
+  const bool writer = (lane & 3) == 0 && idx8 < NW;
+  const T sin = warp_sum8<T>(m_in[0], m_in[1], m_in[2], m_in[3], m_in[4], T(0), T(0), T(0), lane);
+  if (writer) facc_add<T>(Fa + idx8, Fs + idx8, first, sin);
+  if (wall) {
+    const T sout = warp_sum8<T>(m_out[0], m_out[1], m_out[2], m_out[3], m_out[4], T(0), T(0), T(0), lane);
+    if (writer) facc_add<T>(Fa + 5 + idx8, Fs + 5 + idx8, first, sout);
+  }
+}
+
+// Flux kernel step for one face: its fluxes overwrite the face's rows of X,
+// its moments go to the face accumulator.
+template <int D, int NR, int VB, typename T>
+__device__ __forceinline__ void flux_face(const BlockedArgs<T>& a, const int f, const unsigned char* st,
+                                          const BlockVel<D, NR, VB, T>& v, const int first, const int lane,
+                                          const int64_t m0, RowFac<NR, T>* rowbuf, const T ul, const T wl) {
+  using S = FluxStage<D, NR, VB, T>;
+  const FacePoly<D, NR, T>& R = *reinterpret_cast<const FacePoly<D, NR, T>*>(st);
+  const FaceGeom<T>& fg = *reinterpret_cast<const FaceGeom<T>*>(st + S::SP);
+  const T* Xs = reinterpret_cast<const T*>(st + S::SP + S::SG) + lane;
+  const double* Fs = reinterpret_cast<const double*>(st + S::SP + S::SG + S::SX);
+  T Phi[NR][VB], m_in[NWP], m_out[NWP];
+#pragma unroll
+  for (int t = 0; t < NWP; ++t) m_in[t] = m_out[t] = T(0);
+  face_fluxes<D, NR, VB, T>(a, R, fg, Xs, v, lane, m0, rowbuf, ul, wl, true, Phi, m_in, m_out);
+  T* Xf = a.X + size_t(f) * (NR * VB * BV) + lane;
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+#pragma unroll
+    for (int j = 0; j < VB; ++j) Xf[(r * VB + j) * BV] = Phi[r][j];
+  face_moments_add<D, T>(a.Facc + size_t(f) * FACC_W, Fs, fg.bc_type == 1, first, m_in, m_out, lane);
 }
 
 template <int D, int NR, int VB, typename T>
@@ -550,8 +683,11 @@ __global__ void __launch_bounds__(kBlockedThreads, VB == 8 ? 3 : 1) k_bflux(cons
   extern __shared__ __align__(16) unsigned char flux_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* const st = flux_smem + warp * (2 * S::BYTES);
+  RowFac<NR, T>* const rowbuf =
+      reinterpret_cast<RowFac<NR, T>*>(flux_smem + (kBlockedThreads / 32) * 2 * S::BYTES) + warp * VB;
   BlockVel<D, NR, VB, T> v;
   v.load(a, m0, lane);
+  const T ul = a.tensor ? a.lanev[lane] : T(0), wl = a.tensor ? a.lanev[BV + lane] : T(0);
   const int stride = gridDim.x * (kBlockedThreads / 32);
   int f = blockIdx.x * (kBlockedThreads / 32) + warp;
   if (f < a.Nf) flux_prefetch<D, NR, VB, T>(a, f, st, lane);
@@ -562,7 +698,7 @@ __global__ void __launch_bounds__(kBlockedThreads, VB == 8 ? 3 : 1) k_bflux(cons
     cp_async_commit();
     cp_async_wait<1>();  // this face's stage has landed
     __syncwarp();
-    flux_face<D, NR, VB, T>(a, f, st + (it & 1) * S::BYTES, v, first, lane);
+    flux_face<D, NR, VB, T>(a, f, st + (it & 1) * S::BYTES, v, first, lane, m0, rowbuf, ul, wl);
     __syncwarp();        // all lanes done with the stage before it is refilled
   }
   cp_async_wait<0>();
@@ -1071,6 +1207,158 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage1_p(const BlockedArgs
           const RefMaxwell& R = *reinterpret_cast<const RefMaxwell*>(own + SL::ROWS + SL::SCL);
           float scale;
           const S d = encode_value<S>(ft, r == 0 ? g0[j] : R.kap * g0[j], scale);
+          reinterpret_cast<S*>(a.f_next)[base + r * sr + j * sj] = d;
+          if (lane == 0) a.sc_next[(size_t(r) * a.M + m0 + j) * a.Nc + c] = scale;
+        } else {
+          a.f_next[base + r * sr + j * sj] = ft;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// K1 + K3 fused: the micro fluxes of every face of the cell and the first
+// stage (Eq. 28-29, 32-38, 41; Algorithms 1 and 4).  Each cell evaluates the
+// fluxes of its faces itself (an interior face is evaluated by both of its
+// cells, with the same code on the same inputs, so both use bitwise the same
+// fluxes); the owner cell alone adds the face's moments to the face
+// accumulator.  This replaces the per-face flux kernel, whose write and
+// re-read of the face buffer X cost two DRAM passes over X per block.  The
+// pipeline is that of k_bstage1_p: per incidence the face's X rows, interface
+// polynomial, geometry and accumulator are staged one cell ahead.
+// ---------------------------------------------------------------------------
+template <int D, int NR, int VB, typename T>
+struct FaceSlot {
+  static constexpr int ROW = NR * VB * BV * int(sizeof(T));   // the face's rows of X
+  static constexpr int SP = int(sizeof(FacePoly<D, NR, T>));
+  static constexpr int SG = int(sizeof(FaceGeom<T>));
+  static constexpr int SF = FACC_W * int(sizeof(double));
+  static constexpr int BYTES = ROW + SP + SG + SF;
+  static_assert(ROW % 16 == 0 && SP % 16 == 0 && SG % 16 == 0 && SF % 16 == 0, "16-byte slot pieces");
+};
+
+template <int D, int NR, int VB, typename T, typename S>
+__host__ __device__ constexpr int stage1f_warp_bytes(int W) {
+  return 3 * (W * CellStage<NR, VB, T>::INC + int(sizeof(CellEq<T>))) +
+         2 * (W * FaceSlot<D, NR, VB, T>::BYTES + CellSlot<NR, VB, S>::BYTES) + VB * int(sizeof(RowFac<NR, T>));
+}
+
+template <int D, int NR, int VB, int WT, typename T, typename S>
+__global__ void __launch_bounds__(kBlockedThreads) k_bstage1f(const BlockedArgs<T> a, const int64_t m0,
+                                                              const int first) {
+  using CS = CellStage<NR, VB, T>;
+  using SL = CellSlot<NR, VB, S>;
+  using FS = FaceSlot<D, NR, VB, T>;
+  extern __shared__ __align__(16) unsigned char cell_smem[];
+  constexpr int W = WT;  // ELL slots per cell (the table is padded to WT)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int AB = W * CS::INC + int(sizeof(CellEq<T>)), BB = W * FS::BYTES + SL::BYTES;
+  unsigned char* const As = cell_smem + warp * stage1f_warp_bytes<D, NR, VB, T, S>(W);
+  unsigned char* const Bs = As + 3 * AB;
+  RowFac<NR, T>* const rowbuf = reinterpret_cast<RowFac<NR, T>*>(Bs + 2 * BB);
+  BlockVel<D, NR, VB, T> v;
+  v.load(a, m0, lane);
+  const T ul = a.tensor ? a.lanev[lane] : T(0), wl = a.tensor ? a.lanev[BV + lane] : T(0);
+  const size_t sj = size_t(a.Nc) * BV, sr = size_t(a.M) * sj;
+  const int stride = gridDim.x * nwarps;
+  const int cbeg = blockIdx.x * nwarps + warp;
+
+  auto issueA = [&](int c, unsigned char* dst) {
+    stage_bytes(dst, a.ell + size_t(c) * W, W * CS::INC, lane);
+    stage_bytes(dst + W * CS::INC, a.ceq0 + c, int(sizeof(CellEq<T>)), lane);
+  };
+  auto issueB = [&](int c, const unsigned char* A, unsigned char* dst) {
+    const IncT<T>* inc = reinterpret_cast<const IncT<T>*>(A);
+    for (int i = 0; i < W; ++i) {
+      if (inc[i].flags & 2) continue;
+      const size_t f = size_t(inc[i].face);
+      unsigned char* d = dst + i * FS::BYTES;
+      stage_bytes(d, a.X + f * (NR * VB * BV), FS::ROW, lane);
+      stage_bytes(d + FS::ROW, static_cast<const unsigned char*>(a.fpoly) + f * FS::SP, FS::SP, lane);
+      stage_bytes(d + FS::ROW + FS::SP, a.fg + f, FS::SG, lane);
+      if (!first && inc[i].sarea > T(0)) stage_bytes(d + FS::ROW + FS::SP + FS::SG, a.Facc + f * FACC_W, FS::SF, lane);
+    }
+    stage_cell<NR, VB, T, S>(dst + W * FS::BYTES, a, m0, c, lane);
+  };
+
+  if (cbeg < a.Nc) issueA(cbeg, As);
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncwarp();
+  if (cbeg < a.Nc) issueB(cbeg, As, Bs);
+  if (cbeg + stride < a.Nc) issueA(cbeg + stride, As + AB);
+  cp_async_commit();
+  int it = 0;
+  for (int c = cbeg; c < a.Nc; c += stride, ++it) {
+    cp_async_wait<0>();
+    __syncwarp();
+    const int cn = c + stride, cnn = c + 2 * stride;
+    if (cn < a.Nc) issueB(cn, As + ((it + 1) % 3) * AB, Bs + ((it + 1) & 1) * BB);
+    if (cnn < a.Nc) issueA(cnn, As + ((it + 2) % 3) * AB);
+    cp_async_commit();
+
+    const unsigned char* A = As + (it % 3) * AB;
+    const unsigned char* B = Bs + (it & 1) * BB;
+    const IncT<T>* inc = reinterpret_cast<const IncT<T>*>(A);
+    const CellEq<T>& E = *reinterpret_cast<const CellEq<T>*>(A + W * CS::INC);
+    T flux[NR][VB];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int j = 0; j < VB; ++j) flux[r][j] = T(0);
+#pragma unroll 1
+    for (int i = 0; i < W; ++i) {
+      if (inc[i].flags & 2) continue;
+      const unsigned char* fsl = B + i * FS::BYTES;
+      const FacePoly<D, NR, T>& R = *reinterpret_cast<const FacePoly<D, NR, T>*>(fsl + FS::ROW);
+      const FaceGeom<T>& fg = *reinterpret_cast<const FaceGeom<T>*>(fsl + FS::ROW + FS::SP);
+      const T* Xs = reinterpret_cast<const T*>(fsl) + lane;
+      const T sa = inc[i].sarea;
+      const bool owner = sa > T(0);   // walls and artificial boundaries have owner cells only
+      T Phi[NR][VB], m_in[NWP], m_out[NWP];
+#pragma unroll
+      for (int t = 0; t < NWP; ++t) m_in[t] = m_out[t] = T(0);
+      face_fluxes<D, NR, VB, T>(a, R, fg, Xs, v, lane, m0, rowbuf, ul, wl, owner, Phi, m_in, m_out);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int j = 0; j < VB; ++j) flux[r][j] = fma(sa, Phi[r][j], flux[r][j]);
+      if (owner)
+        face_moments_add<D, T>(a.Facc + size_t(inc[i].face) * FACC_W,
+                               reinterpret_cast<const double*>(fsl + FS::ROW + FS::SP + FS::SG), fg.bc_type == 1,
+                               first, m_in, m_out, lane);
+    }
+    const unsigned char* own = B + W * FS::BYTES;
+    T g0[VB];
+    slot_refs<D, NR, VB, T, S>(own, v, g0);
+    const T lam = E.lam, beta0 = E.beta, pref = E.pref, s0 = E.s0, kap = E.kap, inv_vol = E.inv_vol;
+    const size_t base = size_t(m0) * sj + size_t(c) * BV + lane;
+#pragma unroll
+    for (int j = 0; j < VB; ++j) {
+      T c2 = T(0), cq = T(0);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const T cd = v.u[j][d] - E.U[d];
+        c2 += cd * cd;
+        cq += cd * E.q[d];
+      }
+      const T H = pref * t_exp(-lam * c2);
+      const T s = s0 * cq;
+      T fp[NR];
+      fp[0] = H * (T(1) + s * (T(2) * lam * c2 - T(2 + D)));
+      if (NR == 2) fp[NR - 1] = kap * H * (T(1) + s * (T(2) * lam * c2 - T(D)));
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const T f = slot_value<NR, VB, T, S>(own, r, j, lane, g0);
+        const T ft = v.real[j] ? f - flux[r][j] * inv_vol + beta0 * (fp[r] - f) : T(0);
+        if constexpr (SL::SCALED) {
+          // f~ is stored against the same reference as f^n
+          const RefMaxwell& Rf = *reinterpret_cast<const RefMaxwell*>(own + SL::ROWS + SL::SCL);
+          float scale;
+          const S d = encode_value<S>(ft, r == 0 ? g0[j] : Rf.kap * g0[j], scale);
           reinterpret_cast<S*>(a.f_next)[base + r * sr + j * sj] = d;
           if (lane == 0) a.sc_next[(size_t(r) * a.M + m0 + j) * a.Nc + c] = scale;
         } else {
@@ -1714,6 +2002,37 @@ cudaError_t launch_bstage1_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t 
   return launch_cell_cached<T>(k_bstage1_p<D, NR, VB, 8, T, S>, s, a, m0, bytes, cb8, cw8, cg8);
 }
 
+// The fused flux and first-stage kernel; cudaErrorNotSupported where it does
+// not apply (ELL widths other than 4 and 8, or stages beyond the per-warp
+// shared-memory bound): the caller then runs the flux and first-stage kernels.
+// Per-warp shared memory above which the fused kernel is not used.
+constexpr int kFusedWarpBytes = 48 * 1024;
+
+template <int D, int NR, int VB, typename T, typename S>
+bool bstage1f_fits(const BlockedArgs<T>& a) {
+  return (a.W == 4 || a.W == 8) && stage1f_warp_bytes<D, NR, VB, T, S>(a.W) <= kFusedWarpBytes;
+}
+
+template <int D, int NR, int VB, typename T, typename S>
+cudaError_t launch_bstage1f_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int first) {
+  const int bytes = stage1f_warp_bytes<D, NR, VB, T, S>(a.W);
+  if (!bstage1f_fits<D, NR, VB, T, S>(a)) return cudaErrorNotSupported;
+  static int cb4 = -1, cw4 = 0, cb8 = -1, cw8 = 0;
+  static unsigned cg4 = 0, cg8 = 0;
+  auto run = [&](auto kernel, int& cb, int& cw, unsigned& cg) -> cudaError_t {
+    if (cb != bytes) {
+      cudaError_t e = launch_cell_pipelined(kernel, a.nsm, bytes, cw, cg);
+      if (e != cudaSuccess) return e;
+      cb = bytes;
+    }
+    const unsigned grid = std::min<unsigned>(cg, unsigned((a.Nc + cw - 1) / cw));
+    kernel<<<grid, cw * 32, cw * bytes, s>>>(a, m0, first);
+    return cudaGetLastError();
+  };
+  if (a.W == 4) return run(k_bstage1f<D, NR, VB, 4, T, S>, cb4, cw4, cg4);
+  return run(k_bstage1f<D, NR, VB, 8, T, S>, cb8, cw8, cg8);
+}
+
 #define UGKS_CELL_CASES(FN)                                                                               \
   FN(1, 2, 1) FN(1, 2, 2) FN(1, 2, 4) FN(2, 2, 1) FN(2, 2, 2) FN(2, 2, 4) FN(3, 1, 1) FN(3, 1, 2) FN(3, 1, 4) \
   FN(3, 1, 8) \
@@ -1733,7 +2052,7 @@ cudaError_t launch_brecon(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, i
 // (occupancy with the kernel's shared-memory stages), at most one warp per face.
 template <int D, int NR, int VB, typename T>
 cudaError_t launch_bflux_tpl(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int first) {
-  constexpr int smem = 2 * (kBlockedThreads / 32) * FluxStage<D, NR, VB, T>::BYTES;
+  constexpr int smem = (kBlockedThreads / 32) * (2 * FluxStage<D, NR, VB, T>::BYTES + VB * int(sizeof(RowFac<NR, T>)));
   static int per_sm = 0;  // per instantiation, computed on first use
   if (per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(k_bflux<D, NR, VB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1767,6 +2086,26 @@ cudaError_t launch_bstage1(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, 
   if (D == d && NR == nr && vb == b) return launch_bstage1_tpl<d, nr, b, T, S>(s, a, m0);
   UGKS_CELL_CASES(UGKS_STAGE1_CASE)
 #undef UGKS_STAGE1_CASE
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, typename S>
+bool bstage1f_supported(const BlockedArgs<T>& a, int vb) {
+  const int D = a.g.D, NR = a.g.NR;
+#define UGKS_STAGE1F_Q(d, nr, b) \
+  if (D == d && NR == nr && vb == b) return bstage1f_fits<d, nr, b, T, S>(a);
+  UGKS_CELL_CASES(UGKS_STAGE1F_Q)
+#undef UGKS_STAGE1F_Q
+  return false;
+}
+
+template <typename T, typename S>
+cudaError_t launch_bstage1f(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb, int first) {
+  const int D = a.g.D, NR = a.g.NR;
+#define UGKS_STAGE1F_CASE(d, nr, b) \
+  if (D == d && NR == nr && vb == b) return launch_bstage1f_tpl<d, nr, b, T, S>(s, a, m0, first);
+  UGKS_CELL_CASES(UGKS_STAGE1F_CASE)
+#undef UGKS_STAGE1F_CASE
   return cudaErrorInvalidValue;
 }
 
@@ -1831,6 +2170,8 @@ cudaError_t launch_bstage2(cudaStream_t s, const BlockedArgs<T>& a) {
   template cudaError_t launch_brecon<T, T>(cudaStream_t, const BlockedArgs<T>&, int64_t, int);       \
   template cudaError_t launch_bflux<T>(cudaStream_t, const BlockedArgs<T>&, int64_t, int, int);     \
   template cudaError_t launch_bstage1<T, T>(cudaStream_t, const BlockedArgs<T>&, int64_t, int);     \
+  template cudaError_t launch_bstage1f<T, T>(cudaStream_t, const BlockedArgs<T>&, int64_t, int, int); \
+  template bool bstage1f_supported<T, T>(const BlockedArgs<T>&, int);                                \
   template cudaError_t launch_bcelleq<T>(cudaStream_t, const BlockedArgs<T>&);                       \
   template cudaError_t launch_bconserve<T>(cudaStream_t, const BlockedArgs<T>&);                     \
   template cudaError_t launch_bstage2<T, T>(cudaStream_t, const BlockedArgs<T>&);
@@ -1840,6 +2181,8 @@ cudaError_t launch_bstage2(cudaStream_t s, const BlockedArgs<T>& a) {
 #define UGKS_INSTANTIATE_SCALED(S)                                                                   \
   template cudaError_t launch_brecon<float, S>(cudaStream_t, const BlockedArgs<float>&, int64_t, int);   \
   template cudaError_t launch_bstage1<float, S>(cudaStream_t, const BlockedArgs<float>&, int64_t, int);  \
+  template cudaError_t launch_bstage1f<float, S>(cudaStream_t, const BlockedArgs<float>&, int64_t, int, int); \
+  template bool bstage1f_supported<float, S>(const BlockedArgs<float>&, int);                           \
   template cudaError_t launch_bstage2<float, S>(cudaStream_t, const BlockedArgs<float>&);
 
 }  // namespace ugks

@@ -39,9 +39,9 @@ struct KernelTiming {
 // block_* entries and the two after them split the blocked sweep by kernel.
 const char* const kKernelNames[] = {"cell_stage",   "face_stage",   "velocity_block_sweep",
                                     "residual",     "block_reconstruction", "block_fluxes",
-                                    "block_stage1", "conserve",     "stage2"};
-constexpr int kNumKernels = 9;
-enum { kTCell = 0, kTFace, kTSweep, kTRes, kTGrad, kTFlux, kTStage1, kTConserve, kTStage2 };
+                                    "block_stage1", "conserve",     "stage2", "block_flux_stage1"};
+constexpr int kNumKernels = 10;
+enum { kTCell = 0, kTFace, kTSweep, kTRes, kTGrad, kTFlux, kTStage1, kTConserve, kTStage2, kTFused };
 
 }  // namespace
 
@@ -82,6 +82,7 @@ struct ugks_ctx {
   RefMaxwell* d_ref[2] = {nullptr, nullptr};
   // sweep organisation: 1 tiled, 2 blocked; velocities per lane of the blocked sweep
   int variant = 2, vb = 1, vb_max = 1;  // vb_max: the block size the per-face buffer was sized for
+  bool fused = false;                    // blocked sweep: fluxes and first stage in one kernel per block
   // blocked sweep: 32-bit incidence records, per-block scratch
   int32_t* d_cf_off32 = nullptr;
   void* d_inc = nullptr;
@@ -278,7 +279,7 @@ ugks_status validate(const ugks_mesh* m, const ugks_vgrid* v, const ugks_params*
   if ((p->storage == UGKS_STORAGE_F16 || p->storage == UGKS_STORAGE_BF16) && p->sweep == UGKS_SWEEP_TILED)
     return fail(nullptr, UGKS_ERR_UNSUPPORTED, "FP16 / BF16 storage runs in the blocked sweep only");
   if (p->tile_cells < 0) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "tile_cells must be >= 0");
-  if (p->sweep < UGKS_SWEEP_AUTO || p->sweep > UGKS_SWEEP_BLOCKED)
+  if (p->sweep < UGKS_SWEEP_AUTO || p->sweep > UGKS_SWEEP_BLOCKED_FUSED)
     return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "unknown sweep %d", p->sweep);
   if (p->block_velocities != 0 && p->block_velocities != 32 && p->block_velocities != 64 &&
       p->block_velocities != 128 && p->block_velocities != 256)
@@ -598,10 +599,19 @@ ugks_status sweep_blocked(ugks_ctx* ctx, int cur, void* X, double* Facc, double*
   int64_t m0 = 0;
   for (int pass = 0; pass < 2; ++pass) {
     const int vb = pass == 0 ? ctx->vb : 1;
+    // the fused flux + first-stage kernel where requested and its stages
+    // fit, else the flux kernel (fluxes into X) and the first stage
+    const bool fused = ctx->fused && bstage1f_supported<T, S>(a, vb);
     for (; m0 + vb <= M; m0 += vb) {
       record_start(ctx, kTGrad, &ev);
       LAUNCH_TRY(ctx, (launch_brecon<T, S>(s, a, m0, vb)));
       record_stop(ctx, kTGrad, ev);
+      if (fused) {
+        record_start(ctx, kTFused, &ev);
+        LAUNCH_TRY(ctx, (launch_bstage1f<T, S>(s, a, m0, vb, m0 == 0 ? 1 : 0)));
+        record_stop(ctx, kTFused, ev);
+        continue;
+      }
       record_start(ctx, kTFlux, &ev);
       LAUNCH_TRY(ctx, launch_bflux<T>(s, a, m0, vb, m0 == 0 ? 1 : 0));
       record_stop(ctx, kTFlux, ev);
@@ -956,8 +966,9 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
   // The blocked sweep indexes cells, faces and incidences with 32 bits.
   const bool fits32 = Nc < INT32_MAX && Nf < INT32_MAX && int64_t(cf.size()) < INT32_MAX;
   ctx->variant = p->sweep == UGKS_SWEEP_TILED ? 1 : 2;
+  ctx->fused = p->sweep == UGKS_SWEEP_BLOCKED_FUSED;
   if (ctx->variant == 2 && !fits32) {
-    if (p->sweep == UGKS_SWEEP_BLOCKED)
+    if (p->sweep == UGKS_SWEEP_BLOCKED || p->sweep == UGKS_SWEEP_BLOCKED_FUSED)
       return fail(ctx, UGKS_ERR_UNSUPPORTED, "the blocked sweep needs fewer than 2^31 cells, faces and incidences");
     ctx->variant = 1;
   }

@@ -150,6 +150,10 @@ template <typename T>
 cudaError_t launch_bflux(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb, int first);
 template <typename T, typename S>
 cudaError_t launch_bstage1(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb);
+template <typename T, typename S>
+cudaError_t launch_bstage1f(cudaStream_t s, const BlockedArgs<T>& a, int64_t m0, int vb, int first);
+template <typename T, typename S>
+bool bstage1f_supported(const BlockedArgs<T>& a, int vb);
 template <typename T>
 cudaError_t launch_bcelleq(cudaStream_t s, const BlockedArgs<T>& a);
 template <typename T>

@@ -18,7 +18,7 @@ from . import build as _build
 from .inputs import LIMITERS, MODELS, Gas, Mesh, VelocityGrid
 
 STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
-SWEEP = {"auto": 0, "tiled": 1, "blocked": 2}
+SWEEP = {"auto": 0, "tiled": 1, "blocked": 2, "blocked_fused": 3}
 STATUS = {0: "UGKS_OK", 1: "UGKS_ERR_INVALID_ARGUMENT", 2: "UGKS_ERR_MESH", 3: "UGKS_ERR_VGRID",
           4: "UGKS_ERR_OUT_OF_MEMORY", 5: "UGKS_ERR_CUDA", 6: "UGKS_ERR_NONFINITE", 7: "UGKS_ERR_TIMEOUT",
           8: "UGKS_ERR_UNSUPPORTED"}

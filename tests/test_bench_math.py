@@ -86,5 +86,10 @@ def test_launch_count_of_the_blocked_sweep(bench):
     stats = {"cell_stage": (1.0, 3), "face_stage": (1.0, 3), "velocity_block_sweep": (1.0, 3),
              "block_reconstruction": (1.0, 384), "block_fluxes": (1.0, 384), "block_stage1": (1.0, 384),
              "conserve": (1.0, 3), "stage2": (1.0, 3), "residual": (1.0, 3)}
-    # per step: 1 + 1 + 1 + 3 x 128 + 2 + 2 + 1 = 392 launches
-    assert bench.count_launches(stats) == 3 * 392
+    # per step: 1 + 1 + 1 + 3 x 128 + 2 + 3 + 1 = 393 launches
+    assert bench.count_launches(stats) == 3 * 393
+    fused = {"cell_stage": (1.0, 3), "face_stage": (1.0, 3), "velocity_block_sweep": (1.0, 3),
+             "block_reconstruction": (1.0, 384), "block_flux_stage1": (1.0, 384),
+             "conserve": (1.0, 3), "stage2": (1.0, 3), "residual": (1.0, 3)}
+    # per step: 1 + 1 + 1 + 2 x 128 + 2 + 3 + 1 = 265 launches
+    assert bench.count_launches(fused) == 3 * 265

@@ -55,13 +55,15 @@ def w_err(a, b):
 
 
 # device organisations of the sweep: the blocked sweep with 32, 64, 128 and
-# (3-D, one reduced distribution) 256 velocities per block, and the tiled
-# sweep (small tiles: several per CTA)
+# (3-D, one reduced distribution) 256 velocities per block, its fused form
+# (each cell evaluates its faces' fluxes in the first-stage kernel), and the
+# tiled sweep (small tiles: several per CTA)
 SWEEPS = {
     "blocked64": dict(sweep="blocked", block_velocities=64),
     "blocked32": dict(sweep="blocked", block_velocities=32),
     "blocked128": dict(sweep="blocked", block_velocities=128),
     "blocked256": dict(sweep="blocked", block_velocities=256),
+    "blocked_fused64": dict(sweep="blocked_fused", block_velocities=64),   # fluxes evaluated per cell with stage 1
     "tiled": dict(sweep="tiled", tile_cells=48),
     "scaled": dict(sweep="blocked"),   # the storage argument selects FP16 / BF16
 }
@@ -146,6 +148,31 @@ def cylinder_case(cells=1500, nvx=13):
     return mesh, grid, gas, prim
 
 
+def tensor_cases():
+    """Velocity grids whose fastest axis has 32 points (every row of 32
+    velocities is one line along that axis): the separable path of the
+    kernels.  2-D cavity (32 x 20), 3-D sphere (32 x 10 x 10, Shakhov),
+    3-D periodic box with two reduced distributions (32 x 6 x 6, BGK K = 2),
+    1-D strip (32 points, one row)."""
+    def cavity():
+        mesh, _, gas, prim = cavity_case(model="shakhov")
+        return mesh, I.midpoint_grid([32, 20], -4.5, 4.5, 2), gas, prim
+
+    def sphere():
+        mesh, _, gas, prim = sphere_case()
+        return mesh, I.midpoint_grid([32, 10, 10], -6.0, 6.0, 3), gas, prim
+
+    def periodic():
+        mesh, _, gas, prim = periodic3d_case("bgk", K=2)
+        return mesh, I.midpoint_grid([32, 6, 6], -5, 5, 3), gas, prim
+
+    def strip():
+        mesh, _, gas, prim = strip1d_case()
+        return mesh, I.midpoint_grid(32, -8, 8, 1), gas, prim
+    return {"cavity_tensor32": cavity, "sphere_tensor32": sphere, "periodic3d_tensor32_K2": periodic,
+            "strip1d_tensor32": strip}
+
+
 CASES = {
     "cavity_bgk": cavity_case,
     "cavity_shakhov": lambda: cavity_case(model="shakhov"),
@@ -154,6 +181,7 @@ CASES = {
     "strip1d_farfield_outflow": strip1d_case,
     "sphere_tet": sphere_case,
     "cylinder_tri_K2": cylinder_case,
+    **tensor_cases(),
 }
 
 
@@ -180,6 +208,8 @@ LONG_CASES = {
     "cavity_bgk": cavity_case,
     "periodic3d_shakhov": periodic3d_case,
     "sphere_tet_small": lambda: sphere_case(cells=1200, nvx=12),
+    "sphere_tensor32_small": lambda: (lambda c: (c[0], I.midpoint_grid([32, 8, 8], -6.0, 6.0, 3), c[2], c[3]))(
+        sphere_case(cells=1200, nvx=12)),
 }
 
 
@@ -189,6 +219,40 @@ def test_fp32_hundred_steps_matches_oracle(U, name, sweep):
     mesh, grid, gas, prim = LONG_CASES[name]()
     Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 100, "f32", sweep, key="long_" + name)
     assert w_err(Wg, Wo) <= 1e-4, w_err(Wg, Wo)
+
+
+def sphere_benchmark_physics_case():
+    """The benchmark's physics on a reduced mesh: Ma 5 impulsive freestream
+    start (Kn 0.05, Shakhov, Pr 2/3, diffuse wall at the stagnation
+    temperature, far field, outflow) on 1200 tetrahedra of the same
+    generator, velocities on [-12, 12]^3 with 32 points along the flow axis
+    (the tensor-row path) and 20 across."""
+    mesh = I.sphere_tet_mesh(1200, seed=2)
+    grid = I.midpoint_grid([32, 20, 20], -12.0, 12.0, 3)
+    gas = I.Gas(model="shakhov", K=0, Pr=2.0 / 3.0, omega=0.81, mu_ref=I.mu_ref_from_kn(0.05, 0.81), cfl=0.8)
+    prim = I.uniform_primitives(mesh, 1.0, mesh.bc[1].u, 1.0)
+    return mesh, grid, gas, prim
+
+
+@pytest.mark.parametrize("sweep", ["blocked64", "blocked256"])
+def test_fp32_hundred_steps_at_benchmark_physics(U, sweep):
+    """100 FP32 steps of the Ma 5 sphere on [-12, 12]^3 against the FP64
+    oracle: W within the benchmark spec's bound 1e-4."""
+    mesh, grid, gas, prim = sphere_benchmark_physics_case()
+    Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 100, "f32", sweep, key="ma5_sphere")
+    assert np.all(np.isfinite(Wg))
+    assert w_err(Wg, Wo) <= 1e-4, w_err(Wg, Wo)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_scaled_storage_hundred_steps_at_benchmark_physics(U, storage):
+    """100 steps of the Ma 5 sphere with FP16 / BF16 storage: each step rounds
+    every stored value to eps of its deviation from the reference Maxwellian
+    (at most 0.1 of max |f| here), which moves W by at most that much per step
+    (CFL < 1); accumulated linearly over 100 steps: W within 100 eps 0.1."""
+    mesh, grid, gas, prim = sphere_benchmark_physics_case()
+    Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 100, storage, "scaled", key="ma5_sphere")
+    assert w_err(Wg, Wo) <= 100 * STORAGE_EPS[storage] * 0.1, w_err(Wg, Wo)
 
 
 def test_cavity_config_200_steps_fp64(U):
