@@ -83,6 +83,9 @@ def load():
         lib.orc_heat_flux.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, P, P, P, P, P, P]
         lib.orc_reduced_equilibrium.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, P, P, P, P]
         lib.orc_initial_f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P, P, P]
+        lib.orc_limiter_phi.restype = ctypes.c_double
+        lib.orc_limiter_phi.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double]
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_set_threads.restype = ctypes.c_int
         lib.orc_set_threads.argtypes = [ctypes.c_int]
@@ -194,6 +197,12 @@ def surface(mesh, F: np.ndarray, dt: float, freestream=None):
                         _p(vals), _p(coef))
     assert n == nwall
     return faces[:n], vals[:n], (coef[:n] if fs is not None else None)
+
+
+def limiter_phi(kind: str, d2: float, dmax: float, dmin: float, eps2: float = 0.0) -> float:
+    """The oracle's limiter value for one face increment d2 of a cell whose
+    stencil spans [dmin, dmax] around the cell value (reading R1)."""
+    return float(load().orc_limiter_phi(LIMITERS[kind], float(d2), float(dmax), float(dmin), float(eps2)))
 
 
 def time_coefficients(dt: float, tau: float) -> np.ndarray:

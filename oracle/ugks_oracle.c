@@ -421,6 +421,12 @@ static double limiter_phi(int kind, double d2, double dmax, double dmin, double 
   return num / den;
 }
 
+/* The limiter of one face increment d2 of a cell whose stencil spans
+ * [dmin, dmax] around the cell value, exported for the pin tests. */
+double orc_limiter_phi(int kind, double d2, double dmax, double dmin, double eps2) {
+  return limiter_phi(kind, d2, dmax, dmin, eps2);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Blocked velocity summation (Sec. 2.2.2, Eq. 48-49; Sec. 2.2.6, Eq. 63-64)   */
 /* ------------------------------------------------------------------------ */

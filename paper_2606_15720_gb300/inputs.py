@@ -402,6 +402,25 @@ def sphere_tet_mesh(target_cells: int = 100_000, seed: int = 2, mach: float = 5.
     return _assemble_simplex_mesh(P, simp, keep, 3, classify, bcs, name=f"sphere_tet{int(keep.sum())}")
 
 
+def box_tet_mesh(n_inner: int = 2, seed: int = 7, bcs: Optional[List[BC]] = None) -> Mesh:
+    """Delaunay tetrahedra of the unit cube's corners and ``n_inner`` seeded
+    interior points (a few cells with skewed, non-orthogonal neighbours).
+    Boundary faces: x = 0 -> bc 0, x = 1 -> bc 1, the others -> bc 2
+    (default: far field, outflow, wall)."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(seed)
+    corners = np.array([[x, y, z] for x in (0.0, 1.0) for y in (0.0, 1.0) for z in (0.0, 1.0)])
+    pts = np.vstack([corners, rng.uniform(0.2, 0.8, (n_inner, 3))])
+    tri = Delaunay(pts)
+    if bcs is None:
+        bcs = [BC(BC_FARFIELD, 1.05, (0.25, 0.0, 0.1), 1.1), BC(BC_OUTFLOW), BC(BC_WALL, 1.0, (0.0, 0.1, 0.0), 1.2)]
+
+    def classify(fc):
+        return np.where(fc[:, 0] < 1e-9, 0, np.where(fc[:, 0] > 1.0 - 1e-9, 1, 2))
+    return _assemble_simplex_mesh(pts, tri.simplices, np.ones(len(tri.simplices), bool), 3, classify, bcs,
+                                  name=f"box_tet{len(tri.simplices)}")
+
+
 def cylinder_tri_mesh(target_cells: int = 10_000, seed: int = 4, mach: float = 3.0,
                       T_wall: Optional[float] = None, gamma: float = 5.0 / 3.0, radius: float = 0.5) -> Mesh:
     """Triangle mesh around a cylinder of the given radius in [-4,8] x [-5,5].

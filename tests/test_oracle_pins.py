@@ -735,3 +735,152 @@ def test_steady_state_does_not_depend_on_the_start():
         ends.append(W)
     diff = np.abs(ends[1] - ends[0]).max(axis=0) / np.abs(ends[0]).max(axis=0)
     assert diff.max() < 2e-5, diff
+
+
+# ---------------------------------------------------------------------------
+# Limiter (reading R1), 3-D least squares, far-field ghost
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d2,dmax,dmin,eps2,expect", [
+    # Venkatakrishnan's function of y = dp / d2 at eps = 0: (y^2 + 2y) / (y^2 + y + 2)
+    (1.0, 1.0, -5.0, 0.0, 3.0 / 4.0),        # y = 1
+    (0.5, 1.0, -5.0, 0.0, 1.0),              # y = 2
+    (1.0, 3.0, -5.0, 0.0, 15.0 / 14.0),      # y = 3 (above 1: the caller clips)
+    (2.0, 1.0, -5.0, 0.0, 5.0 / 11.0),       # y = 1/2
+    (1.0, 0.0, -5.0, 0.0, 0.0),              # the face reaches a new extremum with no room
+    (-1.0, 5.0, -1.0, 0.0, 3.0 / 4.0),       # negative increment: measured against dmin
+    (-4.0, 5.0, -1.0, 0.0, (1.0 / 16 + 0.5) / (1.0 / 16 + 0.25 + 2.0)),   # y = 1/4
+    (1.0, 1.0, -5.0, 1.0, 4.0 / 5.0),        # with eps^2 = 1: (1 + 1 + 2) / (1 + 2 + 1 + 1)
+    (0.0, 1.0, -1.0, 0.0, 1.0),              # no increment
+])
+def test_venkatakrishnan_limiter_at_closed_form_points(d2, dmax, dmin, eps2, expect):
+    """The published Venkatakrishnan limiter, psi = (dp^2 + eps^2 + 2 d2 dp) /
+    (dp^2 + 2 d2^2 + dp d2 + eps^2), evaluated by hand at chosen points."""
+    assert O.limiter_phi("venkatakrishnan", d2, dmax, dmin, eps2) == pytest.approx(expect, rel=1e-15)
+
+
+@pytest.mark.parametrize("d2,dmax,dmin,expect", [(2.0, 1.0, -3.0, 0.5), (-4.0, 2.0, -1.0, 0.25),
+                                                 (0.5, 1.0, -1.0, 1.0), (-0.5, 1.0, -1.0, 1.0),
+                                                 (1.0, 0.0, -1.0, 0.0)])
+def test_barth_jespersen_limiter_at_closed_form_points(d2, dmax, dmin, expect):
+    """Barth and Jespersen: min(1, dp / d2), dp the room to the stencil's
+    extremum on the side of the increment."""
+    assert O.limiter_phi("barth_jespersen", d2, dmax, dmin, 0.0) == pytest.approx(expect, rel=1e-15)
+
+
+def _free_transport_error_limited(n, limiter):
+    mesh = I.cartesian_mesh((n,), (0,), (1.0,), {"x-": "periodic", "x+": "periodic"}, [])
+    grid = I.midpoint_grid(8, -2, 2, 1)
+    gas = I.Gas(model="bgk", mu_ref=1e14, limiter=limiter, cfl=0.5)
+    x = mesh.cell_centroid[:, 0]
+    eps = 0.1
+    prim = I.uniform_primitives(mesh)
+    prim[:, 0] = 1 + eps * np.sin(2 * np.pi * x)
+    W, f = _setup(mesh, grid, gas, prim)
+    t_end = 0.25
+    nsteps = int(math.ceil(t_end / O.time_step(mesh, grid, 0.5)))
+    W1, f1, _, _ = O.run(mesh, grid, gas, W, f, nsteps, dt=t_end / nsteps)
+    err = 0.0
+    for k, uk in enumerate(grid.u[:, 0]):
+        exact = (1 + eps * np.sin(2 * np.pi * (x - uk * t_end))) * math.pi ** -0.5 * math.exp(-uk * uk)
+        err = max(err, np.max(np.abs(f1[0, :, k] - exact)))
+    return err
+
+
+@pytest.mark.parametrize("limiter,min_order", [("venkatakrishnan", 1.5), ("barth_jespersen", 1.3)])
+def test_free_molecular_limit_with_the_limiter_on(limiter, min_order):
+    """Free transport of a smooth profile (free-molecular limit) with the
+    limiter on: the error still falls at order >= 1.5 with the default
+    (Venkatakrishnan) limiter, whose constant stops it clipping smooth
+    extrema; Barth-Jespersen clips them and stays above 1.3."""
+    e = [_free_transport_error_limited(n, limiter) for n in (32, 64, 128, 256)]
+    orders = [math.log2(e[i] / e[i + 1]) for i in range(3)]
+    assert min(orders[1:]) >= min_order, (e, orders)
+    if limiter == "venkatakrishnan":
+        assert e[-1] > _free_transport_error(256) * 1.05    # the limiter did act
+
+
+def test_linear_field_is_transported_exactly_on_tetrahedra():
+    """Free-molecular limit (tau -> infinity), limiter off, f_k(x) =
+    g_k (1 + beta . x) linear in x: the 3-D least-squares gradient is exact,
+    the face values are exact, and one step moves every interior cell by
+    exactly -dt u_k . grad f_k (the face-centroid rule integrates a linear
+    flux exactly over planar faces and sum_f S n = 0).  Checked on cells two
+    face rings away from every boundary of a graded tetrahedral mesh."""
+    mesh = I.sphere_tet_mesh(2500, seed=3)
+    grid = I.midpoint_grid(3, -2.0, 2.0, 3)
+    gas = I.Gas(model="bgk", K=0, mu_ref=1e12, limiter="none", cfl=0.5)
+    W = I.prim_to_conservative(I.uniform_primitives(mesh, 1.0, (0.3, -0.2, 0.1), 1.0), 3, 0)
+    f = O.initial_f(mesh, grid, W, 0)
+    beta = np.array([0.03, -0.02, 0.025])
+    x = mesh.cell_centroid
+    f = f * (1.0 + x @ beta)[None, :, None]
+    W1, f1, dt, _ = O.run(mesh, grid, gas, W, f, 1)
+    g = O.initial_f(mesh, grid, W, 0)[0, 0]                      # the uniform Maxwellian g_k
+    expect_change = -dt * (grid.u @ beta) * g                    # -dt u_k . grad f_k
+    # cells whose face neighbours and their neighbours are interior
+    nb = [[] for _ in range(mesh.n_cells)]
+    bnd = np.zeros(mesh.n_cells, bool)
+    for o, n in zip(mesh.face_owner, mesh.face_neighbor):
+        if n >= 0:
+            nb[o].append(n)
+            nb[n].append(o)
+        else:
+            bnd[o] = True
+    ring1 = bnd | np.array([any(bnd[j] for j in nb[i]) for i in range(mesh.n_cells)])
+    ok = ~ring1 & ~np.array([any(ring1[j] for j in nb[i]) for i in range(mesh.n_cells)])
+    assert ok.sum() > 200
+    change = f1[0, ok] - f[0, ok]
+    scale = np.max(np.abs(expect_change))
+    assert np.max(np.abs(change - expect_change[None, :])) <= 1e-10 * scale
+
+
+@pytest.mark.parametrize("model", ["bgk", "shakhov"])
+@pytest.mark.parametrize("dim", [1, 2])
+def test_far_field_of_the_interior_state_preserves_a_drifting_maxwellian(dim, model):
+    """A uniform drifting Maxwellian with far-field boundaries holding the same
+    state on every side stays as it is: the ghost state is that state.  BGK:
+    to round-off.  Shakhov: the discrete Maxwellian carries a quadrature heat
+    flux q_h of ~1e-10 whose interface value is halved at a far-field face
+    (ghost q = 0, reading R7), so W moves by O(dt q_h / dx) there."""
+    if dim == 1:
+        bcs = [I.BC(I.BC_FARFIELD, 1.2, (0.35, 0.0, 0.0), 0.9)]
+        mesh = I.cartesian_mesh((12,), (0,), (1,), {"x-": 0, "x+": 0}, bcs)
+        grid = I.midpoint_grid(24, -5, 5, 1)
+    else:
+        bcs = [I.BC(I.BC_FARFIELD, 1.2, (0.35, -0.2, 0.0), 0.9)]
+        mesh = I.cartesian_mesh((6, 5), (0, 0), (1, 0.8), {"x-": 0, "x+": 0, "y-": 0, "y+": 0}, bcs)
+        grid = I.midpoint_grid(16, -5, 5, 2)
+    gas = I.Gas(model=model, Pr=2 / 3 if model == "shakhov" else 1.0, mu_ref=0.05)
+    bc = bcs[0]
+    W, f = _setup(mesh, grid, gas, I.uniform_primitives(mesh, bc.rho, bc.u, bc.T))
+    W1, f1, _, _ = O.run(mesh, grid, gas, W, f, 5)
+    tol = 1e-13 if model == "bgk" else 1e-8
+    np.testing.assert_allclose(W1, W, rtol=0, atol=tol)
+    np.testing.assert_allclose(f1, f, rtol=0, atol=tol * np.max(f))
+
+
+def test_free_molecular_inflow_through_a_far_field_boundary():
+    """Every discrete velocity moves to +x, the free-molecular limit: the far
+    field at x = 0 is the upwind side of every velocity there and has no
+    slope, so after one step the strip's totals change by the far-field
+    Maxwellian's inflow minus the outflow of the uniform interior,
+    d(sum |Omega| W) = dt sum_k w_k psi_k u_k (g_inf,k - f_in,k), with g_inf the
+    reduced far-field Maxwellian (h = rho (lam/pi)^(1/2) exp(-lam (u-U)^2),
+    b = K_xi/(2 lam) h, K_xi = 2)."""
+    rho_inf, U_inf, T_inf = 1.4, 1.1, 1.3
+    bcs = [I.BC(I.BC_FARFIELD, rho_inf, (U_inf, 0.0, 0.0), T_inf), I.BC(I.BC_OUTFLOW)]
+    mesh = I.cartesian_mesh((10,), (0,), (1,), {"x-": 0, "x+": 1}, bcs)
+    u = 0.5 + np.arange(12) * 0.375
+    grid = I.VelocityGrid(u=u[:, None].copy(), weight=np.full(12, 0.375))
+    gas = I.Gas(model="bgk", mu_ref=1e12, cfl=0.5)
+    W, f = _setup(mesh, grid, gas, I.uniform_primitives(mesh, 1.0, (0.8, 0, 0), 1.0))
+    W1, f1, dt, _ = O.run(mesh, grid, gas, W, f, 1)
+    lam = 1.0 / T_inf
+    h_inf = rho_inf * math.sqrt(lam / math.pi) * np.exp(-lam * (u - U_inf) ** 2)
+    b_inf = h_inf / lam
+    dh, db = h_inf - f[0, 0], b_inf - f[1, 0]
+    w = grid.weight
+    expect = dt * np.array([np.sum(w * u * dh), np.sum(w * u * u * dh), 0.5 * np.sum(w * u * (u * u * dh + db))])
+    got = mesh.cell_volume @ (W1 - W)
+    np.testing.assert_allclose(got, expect, rtol=1e-12)
