@@ -52,7 +52,8 @@ struct ugks_ctx {
   Gas gas{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  std::vector<int64_t> new_of_old, old_of_new;
+  std::vector<int64_t> new_of_old, old_of_new;   // cells
+  std::vector<int64_t> face_old_of_new;            // faces
   std::vector<void*> allocs;
   // cells
   double *d_vol = nullptr, *d_xc = nullptr, *d_W[2] = {nullptr, nullptr}, *d_q[2] = {nullptr, nullptr};
@@ -858,18 +859,34 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
     vol[i] = m->cell_volume[o];
     for (int d = 0; d < D; ++d) xc[i * 3 + d] = m->cell_centroid[o * D + d];
   }
-  // ---- face geometry ----
+  // ---- face renumbering: faces in the order of their lower-numbered cell,
+  // so that the kernels that walk faces and those that walk cells touch the
+  // per-face rows (interface records, the block's face buffer) in the same
+  // spatial order ----
+  std::vector<int64_t>& f_old = ctx->face_old_of_new;
+  f_old.resize(Nf);
+  std::iota(f_old.begin(), f_old.end(), 0);
+  {
+    std::vector<int64_t> fkey(Nf);
+    for (int64_t f = 0; f < Nf; ++f) {
+      const int64_t a = n_of_o[m->face_owner[f]], nb = m->face_neighbor[f];
+      fkey[f] = nb >= 0 ? std::min(a, n_of_o[nb]) : a;
+    }
+    std::stable_sort(f_old.begin(), f_old.end(), [&](int64_t x, int64_t y) { return fkey[x] < fkey[y]; });
+  }
+  // ---- face geometry (new face order) ----
   std::vector<int64_t> fown(Nf), fnei(Nf);
   std::vector<double> fnormal(Nf * 3, 0.0), fcent(Nf * 3, 0.0), fshift(Nf * 3, 0.0);
   std::vector<FaceGeom<double>> fg(Nf);
   for (int64_t f = 0; f < Nf; ++f) {
-    fown[f] = n_of_o[m->face_owner[f]];
-    int64_t nb = m->face_neighbor[f];
+    const int64_t fo = f_old[f];
+    fown[f] = n_of_o[m->face_owner[fo]];
+    int64_t nb = m->face_neighbor[fo];
     fnei[f] = nb >= 0 ? n_of_o[nb] : nb;
     for (int d = 0; d < D; ++d) {
-      fnormal[f * 3 + d] = m->face_normal[f * D + d];
-      fcent[f * 3 + d] = m->face_centroid[f * D + d];
-      fshift[f * 3 + d] = m->face_shift ? m->face_shift[f * D + d] : 0.0;
+      fnormal[f * 3 + d] = m->face_normal[fo * D + d];
+      fcent[f * 3 + d] = m->face_centroid[fo * D + d];
+      fshift[f * 3 + d] = m->face_shift ? m->face_shift[fo * D + d] : 0.0;
     }
     FaceGeom<double>& g = fg[f];
     for (int d = 0; d < 3; ++d) {
@@ -877,15 +894,16 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
       g.rl[d] = d < D ? fcent[f * 3 + d] - xc[fown[f] * 3 + d] : 0.0;
       g.rr[d] = (d < D && fnei[f] >= 0) ? fcent[f * 3 + d] - fshift[f * 3 + d] - xc[fnei[f] * 3 + d] : 0.0;
     }
-    g.area = m->face_area[f];
+    g.area = m->face_area[fo];
     g.own = fown[f];
     g.nei = fnei[f];
     g.bc_type = nb >= 0 ? 0 : m->bc[-nb - 1].type;
     g.pad = 0;
   }
-  // ---- diffuse-wall faces (surface quantities) ----
+  // ---- diffuse-wall faces (surface quantities), in ascending original index ----
   for (int64_t f = 0; f < Nf; ++f)
     if (fg[f].bc_type == UGKS_BC_WALL) ctx->walls.push_back(f);
+  std::sort(ctx->walls.begin(), ctx->walls.end(), [&](int64_t x, int64_t y) { return f_old[x] < f_old[y]; });
 
   // ---- incidence CSR with least-squares weights ----
   std::vector<int64_t> cf_off(Nc + 1, 0);
@@ -906,7 +924,7 @@ ugks_status create_impl(const ugks_mesh* m, const ugks_vgrid* v, const ugks_para
         e.sign = side == 0 ? 1 : -1;
         e.other = side == 0 ? fnei[f] : fown[f];
         e.bc_type = fnei[f] >= 0 ? 0 : m->bc[-fnei[f] - 1].type;
-        e.area = m->face_area[f];
+        e.area = m->face_area[f_old[f]];
         for (int d = 0; d < D; ++d) e.r[d] = fcent[f * 3 + d] - (side == 0 ? 0.0 : fshift[f * 3 + d]) - xc[c * 3 + d];
         cf[fill[c]++] = e;
       }
@@ -1340,7 +1358,7 @@ ugks_status ugks_surface(ugks_ctx* ctx, const double* freestream, int64_t cap, i
   if (freestream)
     CUDA_TRY(ctx, cudaMemcpyAsync(coef, d_coef, nwall * 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  std::copy(ctx->walls.begin(), ctx->walls.end(), faces);
+  for (int64_t i = 0; i < nwall; ++i) faces[i] = ctx->face_old_of_new[ctx->walls[i]];
   return UGKS_OK;
 }
 
