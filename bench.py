@@ -595,6 +595,7 @@ def time_batch(args, cases, workload):
         torch.cuda.synchronize()
         tune_s = time.perf_counter() - t0
         picks = [b.tuning(i)[0] for i in range(len(cases))]
+        shapes = [b.shape(i) for i in range(len(cases))]
         b.step(max(2, args.warmup - args.warmup % 2))   # captures the graph
         torch.cuda.synchronize()
         start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -613,6 +614,50 @@ def time_batch(args, cases, workload):
             s.residual()          # synchronises each case's stream
         seq_ms = 1e3 * (time.perf_counter() - t0) / steps
         finite = all(bool(np.all(np.isfinite(s.moments()))) for s in b.cases)
+        # time to steady: graph launches (two steps each), density residuals
+        # (reading R13) read every `every` steps; per case the first step count
+        # (and batch wall time) at which it fell below each threshold
+        steady = None
+        if args.steady_steps > 0:
+            thresholds = (1e-4, 1e-5, 1e-6)
+            every = 100
+            reached = [[None] * len(thresholds) for _ in cases]
+            failed = [None] * len(cases)      # step at which a case reported a non-physical state
+            done_steps, t_all = 0, 0.0
+            while done_steps < args.steady_steps:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                b.step(every)
+                torch.cuda.synchronize()
+                t_all += time.perf_counter() - t0
+                done_steps += every
+                for i, cs in enumerate(b.cases):
+                    if failed[i] is not None:
+                        continue
+                    try:
+                        r = float(cs.residual()[0])
+                    except U.UGKSError:
+                        failed[i] = done_steps
+                        continue
+                    for t, thr in enumerate(thresholds):
+                        if reached[i][t] is None and r < thr:
+                            reached[i][t] = (done_steps, t_all)
+                if all(x[-1] is not None or failed[i] is not None for i, x in enumerate(reached)):
+                    break
+            steady = {"steps_run": done_steps, "seconds": t_all, "ms_per_step": 1e3 * t_all / done_steps,
+                      "non_physical": [{"case": i, "mach": cases[i][4], "kn": cases[i][5], "cells": int(cases[i][0].n_cells),
+                                        "by_step": failed[i]} for i in range(len(cases)) if failed[i] is not None],
+                      "residual": "density residual R_rho, reading R13",
+                      "reached": {f"{thr:g}": {"cases": sum(1 for x in reached if x[t] is not None),
+                                               "steps_median": (float(np.median([x[t][0] for x in reached
+                                                                                 if x[t] is not None]))
+                                                                if any(x[t] is not None for x in reached) else None),
+                                               "all_cases_seconds": (max(x[t][1] for x in reached)
+                                                                     if all(x[t] is not None for x in reached)
+                                                                     else None)}
+                                  for t, thr in enumerate(thresholds)},
+                      "per_case_steps": [[(x[t][0] if x[t] is not None else None) for t in range(len(thresholds))]
+                                         for x in reached]}
         b.close()
     return {
         "report": "batch", "metric": "phase-space DOF updates/s per batch step", "unit": "DOF/s",
@@ -623,7 +668,14 @@ def time_batch(args, cases, workload):
                   "note": "one CUDA-graph launch per two steps of all cases, cases on forked streams"},
         "sequential": {"value": dof / (seq_ms * 1e-3), "ms_per_step": seq_ms,
                        "note": "ugks_step per case in turn, host wall clock"},
-        "autotune": {"seconds": tune_s, "block_velocities": {str(v): picks.count(v) for v in sorted(set(picks))}},
+        "autotune": {"seconds": tune_s, "block_velocities": {str(v): picks.count(v) for v in sorted(set(picks))},
+                     "fused": sum(1 for sh in shapes if sh["fused"]),
+                     "stage2_chunks": {str(c): sum(1 for sh in shapes if sh["stage2_chunks"] == c)
+                                       for c in sorted(set(sh["stage2_chunks"] for sh in shapes))},
+                     "distinct_shapes": len(set((sh["block_velocities"], sh["fused"], sh["stage2_chunks"])
+                                                for sh in shapes)),
+                     "per_case": shapes},
+        "time_to_steady": steady,
         "setup_seconds": {"create": create_s}, "finite": finite, "steps": steps}
 
 
@@ -669,6 +721,8 @@ def main():
     ap.add_argument("--nv-axis", type=int, default=NV_AXIS, help="velocities per axis (profiling runs only)")
     ap.add_argument("--sweep", default="auto", choices=["auto", "blocked", "blocked_fused", "tiled"])
     ap.add_argument("--block-velocities", type=int, default=0, choices=[0, 32, 64, 128, 256])
+    ap.add_argument("--steady-steps", type=int, default=0,
+                    help="batch report: also step the batch up to this many steps, recording time to steady")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="storage of f (FP16 / BF16: deviations from a per-cell reference Maxwellian)")
     ap.add_argument("--report", default=None, choices=["mixed", "batch", "warmstart"],

@@ -98,11 +98,22 @@ typedef struct {
 
 /* Discrete velocity grid (Sec. 2.1, Eq. 21-22): u[n_v][dim], weight[n_v] >= 0
  * (the velocity-cell volumes omega_k).  The library pads it to a multiple of
- * the velocity block (Sec. 2.2.2, Eq. 47) with zero-weight points. */
+ * the velocity block (Sec. 2.2.2, Eq. 47) with zero-weight points.
+ * Optional tensor-product declaration: tensor_n[d] > 0 for d < dim declares
+ * u[k] = (axis[0][i0], ..., axis[dim-1][i_{dim-1}]) with
+ * k = i0 + tensor_n[0] (i1 + tensor_n[1] i2) (first axis fastest) and
+ * n_v = the product of the tensor_n; the library checks it against u
+ * (UGKS_ERR_VGRID if it does not hold).  All zero: not declared, the library
+ * detects the structure from u.  When the fastest axis has 32 points (one
+ * velocity block per line) the kernels evaluate Maxwellians as a product of
+ * a per-line and a per-point factor (the separable exponentials of a tensor
+ * grid). */
 typedef struct {
   int64_t n_v;
   const double *u;
   const double *weight;
+  int32_t tensor_n[3];
+  const double *axis[3];
 } ugks_vgrid;
 
 /* Gas and scheme parameters.
@@ -283,11 +294,17 @@ ugks_status ugks_batch_create(int32_t n, const ugks_mesh *const *meshes, const u
                               const ugks_params *params, const double *const *W_init, void *cuda_stream,
                               ugks_batch **out);
 
-/* Block-size autotuner: every case not tuned yet runs two steps at each
- * block size of 32, 64, 128 (and 256) velocities that its buffers allow, timed on
- * the device (the second step of each pair), and keeps the fastest.  These
- * steps advance the cases (different block sizes change only the summation
- * order of the moments).  The choice is cached for the process. */
+/* Autotuner of the sweep's shape (Sec. 2.2.2: the velocity block is the
+ * tiling unit): for every case not tuned yet, a coordinate search over the
+ * block size (32, 64, 128 and, where compiled, 256 velocities that its
+ * buffers allow), then the organisation of the fluxes and the first stage
+ * (split kernels or one fused kernel, UGKS_SWEEP_BLOCKED / _FUSED), then the
+ * number of velocity chunks of the second stage (the allocated count and its
+ * halves down to an eighth).  Each shape is timed on the device over the
+ * second of two steps; the fastest is kept.  These steps advance the cases
+ * (shapes differ only in the summation order of the moments).  The choice is
+ * cached for the process per (cells, velocities, dim, reduced distributions,
+ * storage). */
 ugks_status ugks_batch_autotune(ugks_batch *batch);
 
 ugks_status ugks_batch_step(ugks_batch *batch, int32_t n_steps);
@@ -299,6 +316,14 @@ ugks_status ugks_batch_context(ugks_batch *batch, int32_t i, ugks_ctx **ctx);
  * timings, ms_per_step[4]: ms per step at 32, 64, 128, 256 velocities per
  * block (0 = not run). */
 ugks_status ugks_batch_tuning(ugks_batch *batch, int32_t i, int32_t *block_velocities, double *ms_per_step);
+
+/* The shape case i runs with (after ugks_batch_autotune: the tuned one):
+ * velocities per block, fused (1) or split (0) fluxes and first stage,
+ * second-stage velocity chunks, the tuned ms per step (0 if taken from the
+ * process cache or not tuned) and the number of shapes timed.  Any output
+ * pointer may be NULL. */
+ugks_status ugks_batch_shape(ugks_batch *batch, int32_t i, int32_t *block_velocities, int32_t *fused,
+                             int32_t *stage2_chunks, double *ms_per_step, int32_t *trials);
 
 ugks_status ugks_batch_destroy(ugks_batch *batch);
 

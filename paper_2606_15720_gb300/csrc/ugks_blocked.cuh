@@ -19,7 +19,9 @@
 //                                                                  [K3]
 // The only intermediate is one per-face buffer X [face][NR][VB][32]: each
 // velocity's upwind cell writes its lane (the two cells of a face write
-// complementary lanes), the flux kernel overwrites it with the flux.  It is
+// complementary lanes; the owner also writes the lanes with u.n = 0, so every
+// lane of an interior face is written once per block), the flux kernel
+// overwrites it with the flux.  It is
 // rewritten by every block and stays mostly in L2.  After the last block:
 //   k_bwall    face accumulators to FP64 (FP32 sweeps: float pairs) and the
 //              wall density from non-penetration (Eq. 38)
@@ -314,12 +316,15 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon(const BlockedArgs<T>
         rr[d] = in.r[d];
       }
       T* Xf = a.X + size_t(face[i]) * (NR * VB * BV) + lane;
+      const bool owner = in.sarea > T(0);
 #pragma unroll
       for (int j = 0; j < VB; ++j) {
         T un = T(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) un += v.u[j][d] * n[d];
-        if (un > T(0)) {
+        // upwind side; u.n = 0 (padding included) written by the owner, so
+        // that every lane of an interior face is written once per block
+        if (un > T(0) || (un == T(0) && owner)) {
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
             T ff = fc[r][j];
@@ -1094,12 +1099,15 @@ __global__ void __launch_bounds__(kBlockedThreads) k_brecon_p(const BlockedArgs<
         rr[d] = inc[i].r[d];
       }
       T* Xf = a.X + size_t(inc[i].face) * (NR * VB * BV) + lane;
+      const bool owner = inc[i].sarea > T(0);
 #pragma unroll
       for (int j = 0; j < VB; ++j) {
         T un = T(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) un += v.u[j][d] * n[d];
-        if (un > T(0)) {
+        // upwind side; u.n = 0 (padding included) written by the owner, so
+        // that every lane of an interior face is written once per block
+        if (un > T(0) || (un == T(0) && owner)) {
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
             T ff = fc[r][j];
@@ -1578,11 +1586,13 @@ __global__ void __launch_bounds__(kS2Threads, sizeof(T) == 4 && NR == 1 && !WALL
         ++nwall;
       }
   if ((__syncthreads_or(nwall > 0) != 0) != WALL) return;   // CTA-uniform
-  if (threadIdx.x == 0)
+  if (threadIdx.x == 0) {
     for (int st = 0; st < RG::NST; ++st) {
       mbar_init(&full[st], 1);
       mbar_init(&empty[st], kS2Consumers / 32);
     }
+    mbar_init_fence();
+  }
   __syncthreads();
 
   if (producer) {
@@ -1675,8 +1685,6 @@ __global__ void __launch_bounds__(kS2Threads, sizeof(T) == 4 && NR == 1 && !WALL
       x[r] = quad_lds<S>(mine + st * RG::STAGE + r * RG::ROW);
       if constexpr (SCALED) sc[r] = a.sc_next[(size_t(r) * a.M + m) * a.Nc + cc];
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[st]);   // the warp's values are in registers: the stage may be refilled
 
     // row part of the velocities (tensor grids)
     T crow[3] = {T(0), T(0), T(0)}, c2row = T(0), cqrow = T(0), Hrow = pref, Grow = T(0), wrow = T(0);
@@ -1777,6 +1785,13 @@ __global__ void __launch_bounds__(kS2Threads, sizeof(T) == 4 && NR == 1 && !WALL
         if (NR == 2) ft[j][NR - 1] -= wf.kap * out;
       }
     }
+    // The stage is released for refilling only after the decode above has
+    // consumed the values read from it, behind a proxy fence: a release issued
+    // right after the shared-memory loads let the bulk copy of row i + NST
+    // overwrite the stage before those loads had returned.
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
     if constexpr (WALL) {
       // further wall faces of the cell (rare): records re-read per row
       if (nwall > 1) {

@@ -264,6 +264,27 @@ ugks_status validate(const ugks_mesh* m, const ugks_vgrid* v, const ugks_params*
     for (int d = 0; d < D; ++d)
       if (!std::isfinite(v->u[k * D + d])) return fail(nullptr, UGKS_ERR_VGRID, "velocity %lld: non-finite", (long long)k);
   }
+  if (v->tensor_n[0] != 0 || v->tensor_n[1] != 0 || v->tensor_n[2] != 0) {
+    // declared tensor product: the axes must reproduce u, first axis fastest
+    int64_t prod = 1;
+    for (int d = 0; d < D; ++d) {
+      if (v->tensor_n[d] <= 0 || !v->axis[d])
+        return fail(nullptr, UGKS_ERR_VGRID, "tensor grid: tensor_n[%d] and axis[%d] needed", d, d);
+      prod *= v->tensor_n[d];
+    }
+    for (int d = D; d < 3; ++d)
+      if (v->tensor_n[d] != 0) return fail(nullptr, UGKS_ERR_VGRID, "tensor grid: tensor_n[%d] beyond dim", d);
+    if (prod != v->n_v) return fail(nullptr, UGKS_ERR_VGRID, "tensor grid: product of tensor_n != n_v");
+    for (int64_t k = 0; k < v->n_v; ++k) {
+      int64_t rem = k;
+      for (int d = 0; d < D; ++d) {
+        const int64_t i = rem % v->tensor_n[d];
+        rem /= v->tensor_n[d];
+        if (v->u[k * D + d] != v->axis[d][i])
+          return fail(nullptr, UGKS_ERR_VGRID, "tensor grid: velocity %lld does not match the axes", (long long)k);
+      }
+    }
+  }
   if (p->model != UGKS_MODEL_BGK && p->model != UGKS_MODEL_SHAKHOV)
     return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "unknown model");
   if (p->K < 0) return fail(nullptr, UGKS_ERR_INVALID_ARGUMENT, "K must be >= 0");
@@ -492,6 +513,7 @@ ugks_status build_typed(ugks_ctx* ctx, const std::vector<int64_t>& cf_off, const
     ctx->d_ell = de;
     T* X;
     CUDA_TRY(ctx, dalloc(ctx, &X, blocked_X_bytes<T>(ctx)));
+    CUDA_TRY(ctx, cudaMemsetAsync(X, 0, blocked_X_bytes<T>(ctx), ctx->stream));
     ctx->d_X = X;
     CUDA_TRY(ctx, dalloc(ctx, &ctx->d_Facc_b, blocked_Facc_bytes(ctx)));
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_Facc_b, 0, blocked_Facc_bytes(ctx), ctx->stream));
@@ -1670,15 +1692,23 @@ struct ugks_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<int> tuned_bv;                 // velocities per block chosen by the autotuner (0: not tuned)
-  std::vector<std::vector<double>> tune_ms;  // ms per step of each candidate (32, 64, 128, 256 velocities)
+  std::vector<std::vector<double>> tune_ms;  // ms per step of each block-size candidate (32, 64, 128, 256)
+  std::vector<int> tuned_fused, tuned_chunks;  // organisation and second-stage chunks chosen with it
+  std::vector<double> tuned_best_ms;           // ms per step of the chosen shape
+  std::vector<int> tune_trials;                // shapes timed for the case (0: from the cache)
   std::string err;
 };
 
 namespace {
 
 using TuneKey = std::tuple<int64_t, int64_t, int, int, int>;  // cells, velocities, dim, reduced, storage
+struct TuneShape {
+  int vb;        // velocities per block lane (1, 2, 4 or 8)
+  int fused;     // fluxes evaluated per cell in the first-stage kernel
+  int nchunk;    // velocity chunks of the second stage
+};
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune_cache;                            // -> velocities per block lane (1, 2 or 4)
+std::map<TuneKey, TuneShape> g_tune_cache;
 
 ugks_status bfail(ugks_batch* b, ugks_status st, const char* fmt, ...) {
   char buf[512];
@@ -1823,9 +1853,17 @@ ugks_status ugks_batch_create(int32_t n, const ugks_mesh* const* meshes, const u
     auto it = g_tune_cache.find(TuneKey(c->Nc, c->nv, c->D, c->NR, c->storage));
     b->tuned_bv.push_back(0);
     b->tune_ms.push_back(std::vector<double>(4, 0.0));
-    if (it != g_tune_cache.end() && it->second <= c->vb_max) {
-      c->vb = it->second;
-      b->tuned_bv.back() = it->second * BV;
+    b->tuned_fused.push_back(c->fused ? 1 : 0);
+    b->tuned_chunks.push_back(c->nchunk);
+    b->tuned_best_ms.push_back(0.0);
+    b->tune_trials.push_back(0);
+    if (it != g_tune_cache.end() && it->second.vb <= c->vb_max && it->second.nchunk <= c->nchunk) {
+      c->vb = it->second.vb;
+      c->fused = it->second.fused != 0;
+      c->nchunk = it->second.nchunk;
+      b->tuned_bv.back() = it->second.vb * BV;
+      b->tuned_fused.back() = it->second.fused;
+      b->tuned_chunks.back() = it->second.nchunk;
     }
   }
   *out = b;
@@ -1845,33 +1883,77 @@ ugks_status ugks_batch_autotune(ugks_batch* b) {
   if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
     return bfail(b, UGKS_ERR_CUDA, "autotune: event creation failed");
   ugks_status st = UGKS_OK;
+  // ms of the second of two steps at the case's current shape (the first
+  // takes any set-up outside the timing)
+  auto time_shape = [&](ugks_ctx* c, double& ms_out) -> ugks_status {
+    ugks_status s2 = ctx_step(c);
+    if (s2 != UGKS_OK) return s2;
+    cudaEventRecord(t0, c->stream);
+    s2 = ctx_step(c);
+    cudaEventRecord(t1, c->stream);
+    if (s2 != UGKS_OK) return s2;
+    float ms = 0.f;
+    if (cudaEventSynchronize(t1) != cudaSuccess || cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess)
+      return bfail(b, UGKS_ERR_CUDA, "autotune: timing failed");
+    ms_out = ms;
+    return UGKS_OK;
+  };
   for (size_t i = 0; st == UGKS_OK && i < b->cases.size(); ++i) {
     ugks_ctx* c = b->cases[i];
     if (b->tuned_bv[i]) continue;
-    int best = c->vb;
+    // coordinate search: block size (split form, all chunks), then the
+    // organisation (split / fused), then the second stage's chunk count
+    const int chunks_max = c->nchunk;
+    int trials = 0;
+    TuneShape best{c->vb, 0, chunks_max};
     double best_ms = 1e300;
+    c->fused = false;
     for (int v = 1, slot = 0; v <= c->vb_max && st == UGKS_OK; v *= 2, ++slot) {
       c->vb = v;
-      st = ctx_step(c);  // first use of this block size: set-up outside the timing
+      double ms = 0.0;
+      st = time_shape(c, ms);
       if (st != UGKS_OK) break;
-      cudaEventRecord(t0, c->stream);
-      st = ctx_step(c);
-      cudaEventRecord(t1, c->stream);
-      if (st != UGKS_OK) break;
-      float ms = 0.f;
-      if (cudaEventSynchronize(t1) != cudaSuccess || cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) {
-        st = bfail(b, UGKS_ERR_CUDA, "autotune: timing failed");
-        break;
-      }
+      ++trials;
       b->tune_ms[i][slot] = ms;
       if (ms < best_ms) {
         best_ms = ms;
-        best = v;
+        best.vb = v;
       }
     }
     if (st != UGKS_OK) break;
-    c->vb = best;
-    b->tuned_bv[i] = best * BV;
+    c->vb = best.vb;
+    c->fused = true;
+    {
+      double ms = 0.0;
+      st = time_shape(c, ms);
+      if (st != UGKS_OK) break;
+      ++trials;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best.fused = 1;
+      }
+    }
+    c->fused = best.fused != 0;
+    for (int ch = chunks_max / 2; ch >= 1 && ch >= chunks_max / 8; ch /= 2) {
+      c->nchunk = ch;
+      double ms = 0.0;
+      st = time_shape(c, ms);
+      if (st != UGKS_OK) break;
+      ++trials;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best.nchunk = ch;
+      }
+    }
+    if (st != UGKS_OK) break;
+    c->vb = best.vb;
+    c->fused = best.fused != 0;
+    c->nchunk = best.nchunk;
+    b->tuned_bv[i] = best.vb * BV;
+    b->tuned_fused[i] = best.fused;
+    b->tuned_chunks[i] = best.nchunk;
+    b->tuned_best_ms[i] = best_ms;
+    b->tune_trials[i] = trials;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[TuneKey(c->Nc, c->nv, c->D, c->NR, c->storage)] = best;
   }
@@ -1917,6 +1999,19 @@ ugks_status ugks_batch_tuning(ugks_batch* b, int32_t i, int32_t* block_velocitie
   if (block_velocities) *block_velocities = b->tuned_bv[i] ? b->tuned_bv[i] : b->cases[i]->vb * BV;
   if (ms_per_step)
     for (int k = 0; k < 4; ++k) ms_per_step[k] = b->tune_ms[i][k];
+  return UGKS_OK;
+}
+
+ugks_status ugks_batch_shape(ugks_batch* b, int32_t i, int32_t* block_velocities, int32_t* fused,
+                             int32_t* stage2_chunks, double* ms_per_step, int32_t* trials) {
+  if (!b || i < 0 || i >= int32_t(b->cases.size()))
+    return bfail(b, UGKS_ERR_INVALID_ARGUMENT, "no case %d in this batch", i);
+  const ugks_ctx* c = b->cases[i];
+  if (block_velocities) *block_velocities = c->vb * BV;
+  if (fused) *fused = c->fused ? 1 : 0;
+  if (stage2_chunks) *stage2_chunks = c->nchunk;
+  if (ms_per_step) *ms_per_step = b->tuned_best_ms[i];
+  if (trials) *trials = b->tune_trials[i];
   return UGKS_OK;
 }
 

@@ -47,7 +47,8 @@ class ugks_mesh(ctypes.Structure):
 
 
 class ugks_vgrid(ctypes.Structure):
-    _fields_ = [("n_v", ctypes.c_int64), ("u", ctypes.c_void_p), ("weight", ctypes.c_void_p)]
+    _fields_ = [("n_v", ctypes.c_int64), ("u", ctypes.c_void_p), ("weight", ctypes.c_void_p),
+                ("tensor_n", ctypes.c_int32 * 3), ("axis", ctypes.c_void_p * 3)]
 
 
 class ugks_params(ctypes.Structure):
@@ -93,6 +94,7 @@ def load(build_if_missing: bool = True):
         "ugks_batch_step": [P, I32],
         "ugks_batch_context": [P, I32, P],
         "ugks_batch_tuning": [P, I32, P, P],
+        "ugks_batch_shape": [P, I32, P, P, P, P, P],
         "ugks_batch_destroy": [P],
         "ugks_destroy": [P],
         "ugks_mesh_sizes": [P, P, P, P],
@@ -150,6 +152,11 @@ class _MeshArgs:
             self.u = f64(grid.u)
             self.w = f64(grid.weight)
             self.grid = ugks_vgrid(grid.n_v, _ptr(self.u), _ptr(self.w))
+            if grid.axes is not None:   # declare the tensor product (checked by the library)
+                self.axes = [f64(a) for a in grid.axes]
+                for d, ax in enumerate(self.axes):
+                    self.grid.tensor_n[d] = int(ax.size)
+                    self.grid.axis[d] = _ptr(ax)
 
 
 def make_params(gas: Gas, storage: str = "f32", tile_cells: int = 0, sweep: str = "auto",
@@ -358,6 +365,15 @@ class Batch:
 
     def step(self, n: int = 1) -> None:
         self._c(self._lib.ugks_batch_step(self._b, int(n)))
+
+    def shape(self, i: int) -> dict:
+        """ugks_batch_shape: the (tuned) shape of case i."""
+        bv, fu, ch, tr = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        ms = ctypes.c_double()
+        self._c(self._lib.ugks_batch_shape(self._b, int(i), ctypes.byref(bv), ctypes.byref(fu), ctypes.byref(ch),
+                                           ctypes.byref(ms), ctypes.byref(tr)))
+        return {"block_velocities": bv.value, "fused": bool(fu.value), "stage2_chunks": ch.value,
+                "ms_per_step": ms.value, "trials": tr.value}
 
     def tuning(self, i: int):
         bv = ctypes.c_int32()

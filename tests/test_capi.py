@@ -102,3 +102,18 @@ def test_warm_start_network_validates_its_arguments_on_the_host(lib):
     assert lib.ugks_mlp_train(None, None, None, 1, 1, 1, ctypes.c_float(1e-3), 0, None) == 1
     assert lib.ugks_mlp_predict(None, None, 1, None) == 1
     assert lib.ugks_mlp_destroy(None) == 0
+
+
+def test_declared_tensor_grid_is_checked_against_the_velocities(lib):
+    """ugks_vgrid.tensor_n / axis declare a tensor-product grid (first axis
+    fastest); a declaration that does not reproduce u is refused on the host."""
+    mesh = I.cavity_mesh(4)
+    gas = I.Gas()
+    grid = I.midpoint_grid([32, 5], -4, 4, 2)
+    assert grid.axes is not None
+    wrong = I.VelocityGrid(u=grid.u, weight=grid.weight, axes=[grid.axes[1], grid.axes[0]])   # axes swapped
+    st, msg = _status_of(mesh, wrong, gas)
+    assert st == 3 and "tensor" in msg                                 # UGKS_ERR_VGRID
+    shifted = I.VelocityGrid(u=grid.u, weight=grid.weight, axes=[grid.axes[0] + 1e-9, grid.axes[1]])
+    st, msg = _status_of(mesh, shifted, gas)
+    assert st == 3 and "match the axes" in msg

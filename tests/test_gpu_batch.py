@@ -73,3 +73,52 @@ def test_autotuner_picks_an_allowed_block_size_and_caches_it():
             bv2, ms2 = b2.tuning(i)
             assert bv2 == bv and np.all(ms2 == 0.0)
             np.testing.assert_array_equal(b2.cases[i].moments(), cases[i][3])
+
+
+def test_autotuner_shapes_are_allowed_and_keep_the_cases_physical():
+    """The shape search (block size, split or fused fluxes and first stage,
+    second-stage chunks) returns an allowed shape per case, and stepping with
+    it matches a case stepped with the same block size and organisation to
+    FP32 rounding (the chunk count changes only the heat flux's summation
+    order)."""
+    from paper_2606_15720_gb300 import ugks as U
+    cases = _cases()
+    args = ([c[0] for c in cases], [c[1] for c in cases], [c[2] for c in cases], [c[3] for c in cases])
+    with U.Batch(*args, storage="f32") as b:
+        b.autotune()
+        shapes = [b.shape(i) for i in range(len(cases))]
+        states = [s.get_state() for s in b.cases]
+        b.step(2)
+        W_after = [s.moments() for s in b.cases]
+    for (mesh, grid, gas, W0), sh, (Ws, fs, k), Wa in zip(cases, shapes, states, W_after):
+        assert sh["block_velocities"] in (32, 64, 128, 256)
+        assert sh["stage2_chunks"] >= 1
+        # tuned here (at least the block sizes, the organisation and one chunk count), or reused from the
+        # process cache when an earlier batch tuned the same case shape
+        assert (sh["trials"] >= 3 and sh["ms_per_step"] > 0.0) or (sh["trials"] == 0 and sh["ms_per_step"] == 0.0)
+        with U.Solver(mesh, grid, gas, W0, storage="f32", block_velocities=sh["block_velocities"],
+                      sweep="blocked_fused" if sh["fused"] else "blocked") as s:
+            s.set_state(Ws, fs, k)
+            s.step(2)
+            assert w_err(Wa, s.moments()) <= 1e-6, w_err(Wa, s.moments())
+
+
+def test_autotuned_batch_of_cylinders_stays_physical_after_memory_reuse():
+    """Eight cases of the cylinder batch workload (5k-40k triangles, padded
+    velocity grids): a first batch is created, stepped and freed, so that a
+    second one reuses its device memory; the second is autotuned (its shapes
+    include the fused flux + first-stage kernel, which reads every lane of the
+    per-face buffer: lanes with u.n = 0, padding included, must be written by
+    the reconstruction each block) and stepped; every case stays physical."""
+    import bench
+    from paper_2606_15720_gb300 import ugks as U
+    cases = bench.batch_cases(n=8)
+    args = ([c[0] for c in cases], [c[1] for c in cases], [c[2] for c in cases], [c[3] for c in cases])
+    with U.Batch(*args, storage="f32") as b:
+        b.step(4)
+    with U.Batch(*args, storage="f32") as b:
+        b.autotune()
+        b.step(6)
+        for s in b.cases:
+            s.residual()                                   # raises on a non-physical state
+            assert np.all(np.isfinite(s.moments()))
