@@ -397,6 +397,10 @@ def sphere_tet_mesh(target_cells: int = 100_000, seed: int = 2, mach: float = 5.
         out = np.full(fc.shape[0], 1, dtype=np.int64)
         out[np.linalg.norm(fc, axis=1) < 1.5] = 0
         out[np.abs(fc[:, 0] - hi[0]) < 1e-9] = 2
+        if lateral == "outflow":
+            out[(np.abs(fc[:, 1] - lo[1]) < 1e-9) | (np.abs(fc[:, 1] - hi[1]) < 1e-9)] = 2
+        elif lateral != "farfield":
+            raise ValueError("lateral must be 'outflow' or 'farfield'")
         return out
 
     return _assemble_simplex_mesh(P, simp, keep, 3, classify, bcs, name=f"sphere_tet{int(keep.sum())}")
@@ -422,12 +426,18 @@ def box_tet_mesh(n_inner: int = 2, seed: int = 7, bcs: Optional[List[BC]] = None
 
 
 def cylinder_tri_mesh(target_cells: int = 10_000, seed: int = 4, mach: float = 3.0,
-                      T_wall: Optional[float] = None, gamma: float = 5.0 / 3.0, radius: float = 0.5) -> Mesh:
+                      T_wall: Optional[float] = None, gamma: float = 5.0 / 3.0, radius: float = 0.5,
+                      lateral: str = "outflow") -> Mesh:
     """Triangle mesh around a cylinder of the given radius in [-4,8] x [-5,5].
 
     Graded circular rings (spacing proportional to 0.02 + 0.1 (r - R)), lattices
     on the box edges, Delaunay, triangles inside r < R removed.  bc 0 wall,
-    bc 1 far field, bc 2 outflow at x = 8."""
+    bc 1 far field (the inflow edge x = -4, and the edges y = +-5 when
+    ``lateral`` is "farfield"), bc 2 outflow at x = 8 and, by default, at
+    y = +-5: the bow shock of a supersonic stream leaves through the lateral
+    edges, and a free-stream ghost state there holds the post-shock gas
+    against the free stream (above Ma ~7 on these meshes the cells where the
+    shock meets the edges went to T ~ 0)."""
     from scipy.spatial import Delaunay
     lo = np.array([-4.0, -5.0])
     hi = np.array([8.0, 5.0])
@@ -474,6 +484,10 @@ def cylinder_tri_mesh(target_cells: int = 10_000, seed: int = 4, mach: float = 3
         out = np.full(fc.shape[0], 1, dtype=np.int64)
         out[np.linalg.norm(fc, axis=1) < radius + 0.5 * (radius * 0.2 + 0.05)] = 0
         out[np.abs(fc[:, 0] - hi[0]) < 1e-9] = 2
+        if lateral == "outflow":
+            out[(np.abs(fc[:, 1] - lo[1]) < 1e-9) | (np.abs(fc[:, 1] - hi[1]) < 1e-9)] = 2
+        elif lateral != "farfield":
+            raise ValueError("lateral must be 'outflow' or 'farfield'")
         return out
 
     return _assemble_simplex_mesh(P, simp, keep, 2, classify, bcs, name=f"cylinder_tri{int(keep.sum())}")
@@ -488,6 +502,33 @@ def uniform_primitives(mesh: Mesh, rho: float = 1.0, U=(0.0, 0.0, 0.0), T: float
     out = np.zeros((mesh.n_cells, mesh.dim + 2))
     out[:, 0] = rho
     out[:, 1:1 + mesh.dim] = np.asarray(U, dtype=np.float64)[:mesh.dim]
+    out[:, -1] = T
+    return out
+
+
+def cylinder_potential_primitives(mesh: Mesh, u_inf: float, radius: float = 0.5, rho: float = 1.0,
+                                  T: float = 1.0) -> np.ndarray:
+    """Start-up field for a cylinder of the given radius at the origin in a
+    stream u_inf along x: the velocity of incompressible potential flow,
+    u - i v = u_inf (1 - R^2 / z^2), scaled down wherever its speed exceeds
+    u_inf (so that it stays inside a velocity grid sized for the free
+    stream), with uniform rho and T.  It is tangential at the wall and zero at
+    both stagnation points, so, unlike a uniform free stream, it does not pull
+    the gas away from the rear of the body at the first step (a uniform start
+    empties the cells behind the cylinder to ~1e-6 of the free-stream
+    density)."""
+    x = mesh.cell_centroid[:, 0]
+    y = mesh.cell_centroid[:, 1]
+    r2 = x * x + y * y
+    R2 = radius * radius
+    u = u_inf * (1.0 - R2 * (x * x - y * y) / (r2 * r2))
+    v = -u_inf * 2.0 * R2 * x * y / (r2 * r2)
+    speed = np.sqrt(u * u + v * v)
+    scale = np.minimum(1.0, u_inf / np.maximum(speed, 1e-300))
+    out = np.zeros((mesh.n_cells, mesh.dim + 2))
+    out[:, 0] = rho
+    out[:, 1] = u * scale
+    out[:, 2] = v * scale
     out[:, -1] = T
     return out
 

@@ -93,3 +93,43 @@ def test_launch_count_of_the_blocked_sweep(bench):
              "conserve": (1.0, 3), "stage2": (1.0, 3), "residual": (1.0, 3)}
     # per step: 1 + 1 + 1 + 2 x 128 + 2 + 3 + 1 = 265 launches
     assert bench.count_launches(fused) == 3 * 265
+
+
+def test_batch_workload_inputs(bench):
+    """The cylinder batch: Ma in [2, 8], Kn in [1e-3, 1], 5k-40k cells,
+    20^2-48^2 velocities of spacing <= 0.7, BGK, and the potential-flow start:
+    uniform rho and T, speed at most u_inf, tangential to the wall, near zero
+    at the rear stagnation point and u_inf far upstream."""
+    from paper_2606_15720_gb300 import inputs as I
+    cases = bench.batch_cases(n=3)
+    for mesh, grid, gas, W0, mach, kn in cases:
+        assert 2.0 <= mach <= 8.0 and 1e-3 <= kn <= 1.0
+        assert 4500 <= mesh.n_cells <= 44000
+        nvx = int(round(np.sqrt(grid.n_v)))
+        assert nvx * nvx == grid.n_v and 20 <= nvx <= 48
+        assert grid.u[1, 0] - grid.u[0, 0] <= 0.7 + 1e-12 or nvx == 48
+        assert gas.model == "bgk"
+        u_inf = mesh.bc[1].u[0]
+        prim = I.cylinder_potential_primitives(mesh, u_inf)
+        np.testing.assert_allclose(W0, I.prim_to_conservative(prim, 2, 0))
+        assert np.all(prim[:, 0] == 1.0) and np.all(prim[:, 3] == 1.0)
+        speed = np.linalg.norm(prim[:, 1:3], axis=1)
+        assert np.max(speed) <= u_inf * (1 + 1e-12)
+        x = mesh.cell_centroid
+        r = np.linalg.norm(x, axis=1)
+        near = r < 0.56
+        un = np.abs(np.sum(prim[near, 1:3] * x[near], axis=1) / r[near])
+        assert np.max(un / u_inf) < 0.25                   # O(r - R) next to the wall
+        rear = np.argmin(np.linalg.norm(x - np.array([0.5, 0.0]), axis=1))
+        assert speed[rear] < 0.2 * u_inf
+        far = np.argmin(x[:, 0])
+        assert speed[far] == pytest.approx(u_inf, rel=0.02)
+    # lateral edges are outflow, the inflow edge far field
+    mesh = cases[0][0]
+    nb = mesh.face_neighbor
+    bnd = nb < 0
+    bc = -(nb[bnd] + 1)
+    yc = mesh.face_centroid[bnd, 1]
+    xc = mesh.face_centroid[bnd, 0]
+    assert np.all(bc[np.abs(np.abs(yc) - 5.0) < 1e-9] == 2)
+    assert np.all(bc[np.abs(xc + 4.0) < 1e-9] == 1)

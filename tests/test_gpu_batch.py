@@ -106,10 +106,13 @@ def test_autotuner_shapes_are_allowed_and_keep_the_cases_physical():
 def test_autotuned_batch_of_cylinders_stays_physical_after_memory_reuse():
     """Eight cases of the cylinder batch workload (5k-40k triangles, padded
     velocity grids): a first batch is created, stepped and freed, so that a
-    second one reuses its device memory; the second is autotuned (its shapes
-    include the fused flux + first-stage kernel, which reads every lane of the
-    per-face buffer: lanes with u.n = 0, padding included, must be written by
-    the reconstruction each block) and stepped; every case stays physical."""
+    second one reuses its device memory; the second is autotuned and stepped;
+    every case stays physical.  Its shapes include the fused flux +
+    first-stage kernel, which reads every lane of the per-face buffer (lanes
+    with u.n = 0, padding included, must be written by the reconstruction
+    each block), and second-stage chunk counts of 1-4, where one CTA streams
+    many velocity rows through its ring of shared-memory stages (a stage must
+    not be refilled before the rows read from it have been used)."""
     import bench
     from paper_2606_15720_gb300 import ugks as U
     cases = bench.batch_cases(n=8)

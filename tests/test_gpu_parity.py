@@ -255,6 +255,31 @@ def test_scaled_storage_hundred_steps_at_benchmark_physics(U, storage):
     assert w_err(Wg, Wo) <= 100 * STORAGE_EPS[storage] * 0.1, w_err(Wg, Wo)
 
 
+def cylinder_hypersonic_case(mach=7.5, kn=0.005, cells=1500):
+    """The upper end of the cylinder batch workload, reduced: Ma 7.5,
+    Kn 0.005, BGK with K_v = 1, diffuse wall at the stagnation temperature,
+    the potential-flow start, 45^2 velocities of spacing 0.7 on
+    [-15.6, 15.6]^2 (the batch's grid rule), 1500 triangles."""
+    mesh = I.cylinder_tri_mesh(cells, seed=11, mach=mach)
+    u_inf = mesh.bc[1].u[0]
+    vmax = max(u_inf + 4.0, 3.5 * np.sqrt(1.0 + mach * mach / 3.0))
+    nvx = int(min(48, max(20, np.ceil(2.0 * vmax / 0.7))))
+    grid = I.midpoint_grid(nvx, -vmax, vmax, 2)
+    gas = I.Gas(model="bgk", K=0, Pr=1.0, omega=0.81, mu_ref=I.mu_ref_from_kn(kn, 0.81), cfl=0.8, venkat_K=1.0)
+    return mesh, grid, gas, I.cylinder_potential_primitives(mesh, u_inf)
+
+
+@pytest.mark.parametrize("storage,bound", [("f64", 1e-11), ("f32", 1e-4)])
+def test_hypersonic_cylinder_hundred_steps(U, storage, bound):
+    """100 steps of the Ma 7.5 cylinder against the FP64 oracle: FP64 to
+    round-off, FP32 within the benchmark spec's bound; the wake's density falls
+    below 1e-2 of the free stream and stays positive."""
+    mesh, grid, gas, prim = cylinder_hypersonic_case()
+    Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 100, storage, "blocked128", key="ma75_cylinder")
+    assert w_err(Wg, Wo) <= bound, w_err(Wg, Wo)
+    assert np.min(Wo[:, 0]) > 0.0 and np.min(Wo[:, 0]) < 0.05
+
+
 def test_cavity_config_200_steps_fp64(U):
     """32x32 cavity, 24x24 grid, Kn 0.075, FP64, 200 steps (the correctness workload)."""
     mesh = I.cavity_mesh(32)
