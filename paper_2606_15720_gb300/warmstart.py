@@ -67,11 +67,13 @@ def freestream_fields(mesh) -> np.ndarray:
 
 def cylinder_case(mach: float, kn: float, cells: int, nvx: int, seed: int):
     """2-D cylinder in a Shakhov gas (Pr 2/3, omega 0.81) started from the
-    freestream: a triangle mesh of about ``cells`` cells and an nvx^2 midpoint
-    velocity grid on [-v, v]^2, v = max(U_inf + 4, 3.5 sqrt(T_stag))."""
+    freestream: a triangle mesh of about ``cells`` cells with far-field
+    lateral edges (this family's flows, Ma <= 3, keep the bow shock clear of
+    them) and an nvx^2 midpoint velocity grid on [-v, v]^2,
+    v = max(U_inf + 4, 3.5 sqrt(T_stag))."""
     import math
     from . import inputs as I
-    mesh = I.cylinder_tri_mesh(cells, seed=seed, mach=mach)
+    mesh = I.cylinder_tri_mesh(cells, seed=seed, mach=mach, lateral="farfield")
     u_inf = mesh.bc[1].u[0]
     vmax = max(u_inf + 4.0, 3.5 * math.sqrt(1.0 + mach * mach / 3.0))
     grid = I.midpoint_grid(nvx, -vmax, vmax, 2)
