@@ -397,10 +397,6 @@ def sphere_tet_mesh(target_cells: int = 100_000, seed: int = 2, mach: float = 5.
         out = np.full(fc.shape[0], 1, dtype=np.int64)
         out[np.linalg.norm(fc, axis=1) < 1.5] = 0
         out[np.abs(fc[:, 0] - hi[0]) < 1e-9] = 2
-        if lateral == "outflow":
-            out[(np.abs(fc[:, 1] - lo[1]) < 1e-9) | (np.abs(fc[:, 1] - hi[1]) < 1e-9)] = 2
-        elif lateral != "farfield":
-            raise ValueError("lateral must be 'outflow' or 'farfield'")
         return out
 
     return _assemble_simplex_mesh(P, simp, keep, 3, classify, bcs, name=f"sphere_tet{int(keep.sum())}")
