@@ -110,7 +110,7 @@ BYTES_STAGE_SCALED = 2 * (2 + 4 / 32)   # FP16 / BF16 value + its row's FP32 sca
 
 def sweep_source_hash():
     h = hashlib.sha256()
-    for fn in ("ugks_blocked.cuh", "ugks_internal.cuh", "ugks_kernels.cuh", "ugks_device.cuh"):
+    for fn in ("ugks_blocked.cuh", "ugks_bulk.cuh", "ugks_internal.cuh", "ugks_kernels.cuh", "ugks_device.cuh"):
         with open(os.path.join(ROOT, "paper_2606_15720_gb300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
