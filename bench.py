@@ -42,9 +42,10 @@ MESH_SEED = 2
 NV_AXIS = 32
 
 
-def build_workload(cells=MESH_CELLS, nv_axis=NV_AXIS):
+def build_workload(cells=MESH_CELLS, nv_axis=NV_AXIS, nv_cross=0):
     mesh = I.sphere_tet_mesh(cells, seed=MESH_SEED)
-    grid = I.midpoint_grid(nv_axis, -12.0, 12.0, 3)
+    n = [nv_axis, nv_cross, nv_cross] if nv_cross > 0 else nv_axis
+    grid = I.midpoint_grid(n, -12.0, 12.0, 3)
     gas = I.Gas(model="shakhov", K=0, Pr=2.0 / 3.0, omega=0.81, mu_ref=I.mu_ref_from_kn(0.05, 0.81), cfl=0.8)
     prim = I.uniform_primitives(mesh, 1.0, mesh.bc[1].u, 1.0)   # freestream start
     W0 = I.prim_to_conservative(prim, 3, 0)
@@ -381,7 +382,7 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2606_15720_gb300 import ugks as U
 
-    mesh, grid, gas, W0 = build_workload(args.cells, args.nv_axis)
+    mesh, grid, gas, W0 = build_workload(args.cells, args.nv_axis, args.nv_cross)
     stream = torch.cuda.Stream()
     n_reduced = 1
     dof = mesh.n_cells * grid.n_v * n_reduced
@@ -454,10 +455,13 @@ def run_gpu(args):
             dist.destroy_process_group()
         return 0
     cpu = None
-    if world == 1 and not args.no_cpu_baseline and (args.cells, args.nv_axis) == (MESH_CELLS, NV_AXIS):
+    full = (args.cells, args.nv_axis, args.nv_cross) == (MESH_CELLS, NV_AXIS, 0)
+    if world == 1 and not args.no_cpu_baseline and full:
         cpu = cpu_baseline(mesh, grid, gas, W0, dt_run)
-    workload = WORKLOAD if (args.cells, args.nv_axis) == (MESH_CELLS, NV_AXIS) else \
-        f"sphere_tet{args.cells // 1000}k_v{args.nv_axis}cube_shakhov_fp32 (reduced size for profiling)"
+    workload = WORKLOAD if full else \
+        (f"sphere_tet{args.cells // 1000}k_v{args.nv_axis}x{args.nv_cross}x{args.nv_cross}_shakhov_fp32"
+         if args.nv_cross > 0 else f"sphere_tet{args.cells // 1000}k_v{args.nv_axis}cube_shakhov_fp32") + \
+        " (reduced size for profiling)"
     if args.storage != "f32":
         workload = workload.replace("fp32", args.storage + "_scaled_storage")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -726,6 +730,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cells", type=int, default=MESH_CELLS, help="mesh size (profiling runs only)")
     ap.add_argument("--nv-axis", type=int, default=NV_AXIS, help="velocities per axis (profiling runs only)")
+    ap.add_argument("--nv-cross", type=int, default=0,
+                    help="velocities along the two cross-flow axes, 0 = as --nv-axis (profiling runs only)")
     ap.add_argument("--sweep", default="auto", choices=["auto", "blocked", "blocked_fused", "tiled"])
     ap.add_argument("--block-velocities", type=int, default=0, choices=[0, 32, 64, 128, 256])
     ap.add_argument("--steady-steps", type=int, default=0,
