@@ -699,6 +699,28 @@ def warm_held_out(n=16, seed=5):
             for _ in range(n)]
 
 
+WARM_TRAIN_BATCH = [(2.0, 1e-3), (2.0, 1e-2), (2.0, 0.1), (2.0, 1.0), (3.5, 1e-3), (3.5, 1e-2), (3.5, 0.1),
+                    (3.5, 1.0), (5.0, 0.03), (5.0, 0.1), (5.0, 1.0), (6.5, 0.05), (6.5, 0.15), (6.5, 1.0),
+                    (8.0, 0.05), (8.0, 0.15), (8.0, 1.0)]
+
+
+def warm_held_out_batch(n=8, seed=6):
+    """Held-out (Ma, Kn) of the wide warm-start family: Ma ~ U[2.3, 7.7],
+    Kn log-uniform in [1.5e-3, 0.7], redrawn where Ma > 4.5 and Kn < 0.05
+    (the continuum corner whose strong shocks do not stay physical on
+    2000-triangle meshes: Ma 5-8 at Kn 1e-3-1e-2 went non-physical within
+    1500-3500 steps there)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        ma = float(rng.uniform(2.3, 7.7))
+        kn = float(10 ** rng.uniform(math.log10(1.5e-3), math.log10(0.7)))
+        if ma > 4.5 and kn < 0.05:
+            continue
+        out.append((round(ma, 3), round(kn, 4)))
+    return out
+
+
 def run_warm_report(args):
     """Learned warm start: 12 converged cylinder cases (Ma 1.5-3, Kn 0.05-0.5,
     about 2000 triangles, 28^2 velocities, Shakhov) train the 6x256 network;
@@ -709,10 +731,15 @@ def run_warm_report(args):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU (the CUDA library has no CPU path)")
     from paper_2606_15720_gb300 import warmstart as WS
-    res = WS.experiment(WARM_TRAIN, warm_held_out(), cells=2000, nvx=28, ref_tol=1e-8,
-                        log=lambda m: print(m, file=sys.stderr, flush=True))
+    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    if args.family == "batch":
+        res = WS.experiment(WARM_TRAIN_BATCH, warm_held_out_batch(), cells=2000, nvx=None, ref_tol=1e-8,
+                            max_steps=60_000, family="batch", log=log)
+        res["workload"] = "cylinder_warmstart_ma2-8_kn1e-3-1_tri2k_v20-48sq_bgk_potential_start_fp32"
+    else:
+        res = WS.experiment(WARM_TRAIN, warm_held_out(), cells=2000, nvx=28, ref_tol=1e-8, log=log)
+        res["workload"] = "cylinder_warmstart_ma1.5-3_kn0.05-0.5_tri2k_v28sq_shakhov_fp32"
     ratios = [c["time_ratio"] for c in res["cases"] if "time_ratio" in c]
-    res["workload"] = "cylinder_warmstart_ma1.5-3_kn0.05-0.5_tri2k_v28sq_shakhov_fp32"
     res["metric"] = "time_to_residual_1e-6_speedup"
     res["value"] = float(np.exp(np.mean(np.log(ratios)))) if ratios else None
     res["unit"] = "x (geometric mean over held-out cases, freestream seconds / warm-start seconds)"
@@ -736,6 +763,9 @@ def main():
     ap.add_argument("--block-velocities", type=int, default=0, choices=[0, 32, 64, 128, 256])
     ap.add_argument("--steady-steps", type=int, default=0,
                     help="batch report: also step the batch up to this many steps, recording time to steady")
+    ap.add_argument("--family", default="shakhov", choices=["shakhov", "batch"],
+                    help="warmstart report: the Ma 1.5-3 Shakhov family, or cases of the batch workload's "
+                         "kind (Ma 2-8, Kn 1e-3-1, BGK, potential-flow start)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="storage of f (FP16 / BF16: deviations from a per-cell reference Maxwellian)")
     ap.add_argument("--report", default=None, choices=["mixed", "batch", "warmstart"],

@@ -398,7 +398,10 @@ ugks_status ugks_mlp_features(ugks_mlp *net, const ugks_mesh *mesh, double mach,
 
 /* Warm start of a context: predicts the thirteen-moment fields of
  * every cell from its features and resets the context to their
- * Chapman-Enskog distribution (ugks_init_moments13).  Freestream fallback:
+ * Chapman-Enskog distribution (ugks_init_moments13).  The predicted stress
+ * and heat flux of a cell are scaled by one factor in (0, 1] where needed so
+ * that |sigma_ij| <= p/2 and |q| <= p sqrt(T)/2 (p = rho T / 2): bounded
+ * Grad corrections keep f positive at thermal speeds.  Freestream fallback:
  * a cell whose prediction is not finite or has rho <= 0 or T <= 0 gets the
  * fields of freestream = (rho, U[dim], T) with zero stress and heat flux;
  * *n_fallback (if not NULL) receives their number.  mesh must be the mesh the

@@ -889,6 +889,18 @@ ugks_status ugks_mlp_warm_start(ugks_mlp* n, ugks_ctx* ctx, const ugks_mesh* mes
     double* o = fields.data() + i * n13;
     if (ok) {
       for (int j = 0; j < n13; ++j) o[j] = y[j];
+      // bounded non-equilibrium: stress and heat flux scaled by one factor so
+      // that |sigma_ij| <= p/2 and |q| <= p sqrt(T)/2 (p = rho T / 2), where the
+      // Grad correction stays above -1/2 at thermal speeds and f stays positive
+      const double p = 0.5 * o[0] * o[D + 1];
+      double smax = 0.0, q2 = 0.0;
+      for (int j = D + 2; j < D + 2 + D * (D + 1) / 2; ++j) smax = std::max(smax, std::fabs(o[j]));
+      for (int j = D + 2 + D * (D + 1) / 2; j < n13; ++j) q2 += o[j] * o[j];
+      double alpha = 1.0;
+      if (smax > 0.5 * p) alpha = std::min(alpha, 0.5 * p / smax);
+      const double qb = 0.5 * p * std::sqrt(o[D + 1]);
+      if (q2 > qb * qb) alpha = std::min(alpha, qb / std::sqrt(q2));
+      for (int j = D + 2; j < n13; ++j) o[j] *= alpha;
     } else {
       ++nf;
       for (int j = 0; j < n13; ++j) o[j] = j < D + 2 ? freestream[j] : 0.0;

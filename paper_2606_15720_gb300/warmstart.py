@@ -22,22 +22,29 @@ def converge(solvers: Sequence["U.Solver"], tol: float = 1e-6, max_steps: int = 
              batch: Optional["U.Batch"] = None):
     """Steps until the density residual R_rho of every case is below tol
     (checked every ``check_every`` steps).  Returns the steps each case took
-    (None where max_steps was reached first).  With ``batch`` the cases are
-    stepped together by its graph launches; converged cases keep stepping
-    until all are done (their fields no longer change at that tolerance)."""
+    (None where max_steps was reached first or the case became non-physical,
+    which ends its stepping).  With ``batch`` the cases are stepped together
+    by its graph launches; converged cases keep stepping until all are done
+    (their fields no longer change at that tolerance)."""
     steps = [None] * len(solvers)
+    failed = [False] * len(solvers)
     done = 0
-    while done < max_steps and any(s is None for s in steps):
+    while done < max_steps and any(s is None and not f for s, f in zip(steps, failed)):
         if batch is not None:
             batch.step(check_every)
         else:
             for i, s in enumerate(solvers):
-                if steps[i] is None:
+                if steps[i] is None and not failed[i]:
                     s.step(check_every)
         done += check_every
         for i, s in enumerate(solvers):
-            if steps[i] is None and s.residual()[0] < tol:
-                steps[i] = done
+            if steps[i] is not None or failed[i]:
+                continue
+            try:
+                if s.residual()[0] < tol:
+                    steps[i] = done
+            except U.UGKSError:
+                failed[i] = True
     return steps
 
 
@@ -65,20 +72,35 @@ def freestream_fields(mesh) -> np.ndarray:
     return np.array([b.rho, *b.u[:mesh.dim], b.T], dtype=np.float64)
 
 
-def cylinder_case(mach: float, kn: float, cells: int, nvx: int, seed: int):
-    """2-D cylinder in a Shakhov gas (Pr 2/3, omega 0.81) started from the
-    freestream: a triangle mesh of about ``cells`` cells with far-field
-    lateral edges (this family's flows, Ma <= 3, keep the bow shock clear of
-    them) and an nvx^2 midpoint velocity grid on [-v, v]^2,
-    v = max(U_inf + 4, 3.5 sqrt(T_stag))."""
+def cylinder_case(mach: float, kn: float, cells: int, nvx: Optional[int], seed: int, family: str = "shakhov"):
+    """One cylinder case of a warm-start family.
+
+    family "shakhov": a Shakhov gas (Pr 2/3, omega 0.81) started from the
+    freestream, far-field lateral edges (this family's flows, Ma <= 3, keep
+    the bow shock clear of them) and an nvx^2 midpoint velocity grid on
+    [-v, v]^2, v = max(U_inf + 4, 3.5 sqrt(T_stag)).
+
+    family "batch": a case of the cylinder batch workload's kind (Ma 2-8):
+    BGK (omega 0.81) with Venkatakrishnan's K_v = 1, outflow lateral edges,
+    the potential-flow start, and (nvx None) the batch's grid rule, nvx =
+    clip(ceil(2 v / 0.7), 20, 48)."""
     import math
     from . import inputs as I
-    mesh = I.cylinder_tri_mesh(cells, seed=seed, mach=mach, lateral="farfield")
-    u_inf = mesh.bc[1].u[0]
+    u_inf = mach * math.sqrt(5.0 / 6.0)
     vmax = max(u_inf + 4.0, 3.5 * math.sqrt(1.0 + mach * mach / 3.0))
-    grid = I.midpoint_grid(nvx, -vmax, vmax, 2)
-    gas = I.Gas(model="shakhov", K=0, Pr=2.0 / 3.0, omega=0.81, mu_ref=I.mu_ref_from_kn(kn, 0.81), cfl=0.8)
-    W0 = I.prim_to_conservative(I.uniform_primitives(mesh, 1.0, mesh.bc[1].u, 1.0), 2, 0)
+    if family == "shakhov":
+        mesh = I.cylinder_tri_mesh(cells, seed=seed, mach=mach, lateral="farfield")
+        grid = I.midpoint_grid(nvx, -vmax, vmax, 2)
+        gas = I.Gas(model="shakhov", K=0, Pr=2.0 / 3.0, omega=0.81, mu_ref=I.mu_ref_from_kn(kn, 0.81), cfl=0.8)
+        W0 = I.prim_to_conservative(I.uniform_primitives(mesh, 1.0, mesh.bc[1].u, 1.0), 2, 0)
+    elif family == "batch":
+        mesh = I.cylinder_tri_mesh(cells, seed=seed, mach=mach)
+        n = nvx if nvx else int(min(48, max(20, math.ceil(2.0 * vmax / 0.7))))
+        grid = I.midpoint_grid(n, -vmax, vmax, 2)
+        gas = I.Gas(model="bgk", K=0, Pr=1.0, omega=0.81, mu_ref=I.mu_ref_from_kn(kn, 0.81), cfl=0.8, venkat_K=1.0)
+        W0 = I.prim_to_conservative(I.cylinder_potential_primitives(mesh, mesh.bc[1].u[0]), 2, 0)
+    else:
+        raise ValueError("family must be 'shakhov' or 'batch'")
     return mesh, grid, gas, W0
 
 
@@ -87,10 +109,10 @@ def rel_linf(W, W_ref):
     return (np.abs(W - W_ref).max(0) / np.maximum(np.abs(W_ref).max(0), 1e-300)).tolist()
 
 
-def experiment(train, held_out, cells: int, nvx: int, width: int = 256, hidden_layers: int = 6,
+def experiment(train, held_out, cells: int, nvx: Optional[int], width: int = 256, hidden_layers: int = 6,
                schedule=((200, 1e-3), (200, 3e-4), (100, 1e-4)), batch: int = 512, tol: float = 1e-6,
                ref_tol: Optional[float] = None, check_every: int = 200, max_steps: int = 200_000, seed: int = 0,
-               log=None) -> dict:
+               log=None, family: str = "shakhov") -> dict:
     """Trains the warm start on converged cases and measures what it gains.
 
     train, held_out: sequences of (Mach, Kn).  The training cases run together
@@ -103,14 +125,17 @@ def experiment(train, held_out, cells: int, nvx: int, width: int = 256, hidden_l
     both starting states are compared with it (per-field relative L-inf), and
     the warm solve also records when every field is at least as close to the
     reference as the freestream solve was at R_rho < tol (equal accuracy).
-    The warm solve's checks then also read W every check_every steps."""
+    The warm solve's checks then also read W every check_every steps.
+    family selects the kind of case (cylinder_case); training cases that do
+    not reach tol within max_steps are left out of the training set."""
     def say(*a):
         if log:
             log(" ".join(str(x) for x in a))
 
     out = {"train": [list(t) for t in train], "held_out": [list(t) for t in held_out], "cells": cells,
-           "nvx": nvx, "tol": tol, "ref_tol": ref_tol, "network": f"{hidden_layers}x{width} tanh, BF16/FP32-acc"}
-    cases = [cylinder_case(ma, kn, cells, nvx, seed=1000 + i) for i, (ma, kn) in enumerate(train)]
+           "nvx": nvx, "family": family, "tol": tol, "ref_tol": ref_tol,
+           "network": f"{hidden_layers}x{width} tanh, BF16/FP32-acc"}
+    cases = [cylinder_case(ma, kn, cells, nvx, seed=1000 + i, family=family) for i, (ma, kn) in enumerate(train)]
     t0 = time.perf_counter()
     with U.Batch([c[0] for c in cases], [c[1] for c in cases], [c[2] for c in cases], [c[3] for c in cases],
                  storage="f32") as b:
@@ -119,7 +144,9 @@ def experiment(train, held_out, cells: int, nvx: int, width: int = 256, hidden_l
         say("training cases converged", steps, round(time.perf_counter() - t0, 1), "s")
         D = cases[0][0].dim
         net = U.WarmStartNet(6, 2 * D + 2 + D * (D + 1) // 2, width=width, hidden_layers=hidden_layers, seed=seed)
-        X, Y = training_set(net, b.cases, [c[0] for c in cases], [t[0] for t in train], [t[1] for t in train])
+        keep = [i for i, n in enumerate(steps) if n is not None]
+        X, Y = training_set(net, [b.cases[i] for i in keep], [cases[i][0] for i in keep],
+                            [train[i][0] for i in keep], [train[i][1] for i in keep])
     net.fit_scaling(X, Y)
     t0 = time.perf_counter()
     losses = []
@@ -139,18 +166,27 @@ def experiment(train, held_out, cells: int, nvx: int, width: int = 256, hidden_l
                        "gemm_tflops": flops / secs / 1e12}
     out["cases"] = []
     for j, (ma, kn) in enumerate(held_out):
-        mesh, grid, gas, W0 = cylinder_case(ma, kn, cells, nvx, seed=5000 + j)
+        mesh, grid, gas, W0 = cylinder_case(ma, kn, cells, nvx, seed=5000 + j, family=family)
         rec = {"mach": ma, "kn": kn, "n_cells": int(mesh.n_cells)}
         W_ref = None
         with U.Solver(mesh, grid, gas, W0, storage="f32") as s:
             W_free = s.moments()
             n, sec = time_to_steady(s, tol, max_steps, check_every)
-            W_plain = s.moments()
             rec["freestream"] = {"steps": n, "seconds": sec}
+            if n is None:
+                # non-physical or not converged within max_steps: no reference to compare with
+                say("held-out", ma, kn, "plain start did not reach tol")
+                out["cases"].append(rec)
+                continue
+            W_plain = s.moments()
             if ref_tol:
-                converge([s], ref_tol, max_steps, check_every)
-                W_ref = s.moments()
-                e_plain = rel_linf(W_plain, W_ref)
+                if converge([s], ref_tol, max_steps, check_every)[0] is None:
+                    rec["reference_not_reached"] = True
+                try:
+                    W_ref = s.moments()
+                    e_plain = rel_linf(W_plain, W_ref)
+                except U.UGKSError:
+                    W_ref = None
         with U.Solver(mesh, grid, gas, W0, storage="f32") as s:
             t0 = time.perf_counter()
             nf = net.warm_start(s, mesh, ma, kn, freestream_fields(mesh))
@@ -161,13 +197,30 @@ def experiment(train, held_out, cells: int, nvx: int, width: int = 256, hidden_l
             while done < max_steps and (n_res is None or (W_ref is not None and n_acc is None)):
                 s.step(check_every)
                 done += check_every
-                if n_res is None and s.residual()[0] < tol:
+                try:
+                    r = s.residual()[0]
+                except U.UGKSError:
+                    rec["warm_non_physical_by_step"] = done
+                    break
+
+                if n_res is None and r < tol:
                     n_res, sec_res, W_warm = done, time.perf_counter() - t0 + setup, s.moments()
                 if W_ref is not None and n_acc is None:
                     e = rel_linf(s.moments(), W_ref)
                     if all(a <= b for a, b in zip(e, e_plain)):
                         n_acc, sec_acc = done, time.perf_counter() - t0 + setup
             rec["warm"] = {"steps": n_res, "seconds": sec_res, "setup_seconds": setup, "fallback_cells": nf}
+        if "warm_non_physical_by_step" in rec:
+            # fallback: the plain start, after the steps and seconds lost on the warm one
+            lost_steps, lost_sec = rec["warm_non_physical_by_step"], time.perf_counter() - t0 + setup
+            with U.Solver(mesh, grid, gas, W0, storage="f32") as s:
+                n, sec = time_to_steady(s, tol, max_steps, check_every)
+                W_warm = s.moments() if n is not None else None
+            n_res = lost_steps + n if n is not None else None
+            sec_res = lost_sec + sec if n is not None else None
+            rec["warm"] = {"steps": n_res, "seconds": sec_res, "setup_seconds": setup, "fallback_cells": nf,
+                           "restarted_from_plain_start": True}
+            n_acc, sec_acc = n_res, sec_res     # the plain solve's own accuracy
         if rec["freestream"]["steps"] and n_res:
             rec["step_ratio"] = rec["freestream"]["steps"] / n_res
             rec["time_ratio"] = rec["freestream"]["seconds"] / sec_res

@@ -154,8 +154,9 @@ def _cavity_solver(U):
 def test_warm_start_sets_the_predicted_fields_and_falls_back_to_freestream():
     """A network with zero weights predicts its last bias everywhere; the warm
     start sets the Chapman-Enskog state of those fields (its moments give them
-    back up to the grid's quadrature error) and replaces non-physical
-    predictions by the freestream."""
+    back up to the grid's quadrature error), scales stress and heat flux
+    above the bound down, and replaces non-physical predictions by the
+    freestream."""
     from paper_2606_15720_gb300 import ugks as U
     mesh, s = _cavity_solver(U)
     sizes = [6, 32, 32, 9]
@@ -170,6 +171,17 @@ def test_warm_start_sets_the_predicted_fields_and_falls_back_to_freestream():
     m13 = s.moments13()
     np.testing.assert_allclose(m13[:, :4], np.broadcast_to(fields[:4], (mesh.n_cells, 4)), rtol=0, atol=2e-4)
     np.testing.assert_allclose(m13[:, 4:], np.broadcast_to(fields[4:], (mesh.n_cells, 5)), rtol=0, atol=2e-3)
+    # stress above p/2 (p = rho T / 2 = 0.66): stress and heat flux scaled by 0.33 / 1.32
+    big = fields.copy()
+    big[4] = 1.32
+    p[-9:] = big
+    net.set_params(p)
+    assert net.warm_start(s, mesh, 0.16, 0.075, fs) == 0
+    m13 = s.moments13()
+    alpha = 0.5 * 0.66 / 1.32
+    np.testing.assert_allclose(m13[:, :4], np.broadcast_to(big[:4], (mesh.n_cells, 4)), rtol=0, atol=2e-4)
+    np.testing.assert_allclose(m13[:, 4:], np.broadcast_to(alpha * big[4:], (mesh.n_cells, 5)), rtol=0, atol=2e-3)
+    p[-9:] = fields
     p[-9] = -1.0                                   # rho < 0: every cell falls back
     net.set_params(p)
     nf = net.warm_start(s, mesh, 0.16, 0.075, fs)
