@@ -283,7 +283,7 @@ def rooflines(stats, mesh, grid, dof, steps, ms_per_step, bytes_stage=BYTES_STAG
     events on the stream the kernels run on).
 
     roofline (the headline): the whole step against HBM on its algorithmic
-    bytes (SURVEY 8(d)): 4 s bytes per phase-space DOF (s = bytes per stored
+    bytes: 4 s bytes per phase-space DOF (s = bytes per stored
     value: the first stage reads f^n and writes f~, the second reads f~ and
     writes f^{n+1}), achieved = 4 s x DOF / (ms_per_step), so the fraction
     reproduces from ms_per_step.  traffic = the step's DRAM bytes from the

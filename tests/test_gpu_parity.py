@@ -237,7 +237,7 @@ def sphere_benchmark_physics_case():
 @pytest.mark.parametrize("sweep", ["blocked64", "blocked256"])
 def test_fp32_hundred_steps_at_benchmark_physics(U, sweep):
     """100 FP32 steps of the Ma 5 sphere on [-12, 12]^3 against the FP64
-    oracle: W within the benchmark spec's bound 1e-4."""
+    oracle: W within the FP32 bound of 1e-4 after 100 steps."""
     mesh, grid, gas, prim = sphere_benchmark_physics_case()
     Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 100, "f32", sweep, key="ma5_sphere")
     assert np.all(np.isfinite(Wg))
@@ -272,7 +272,7 @@ def cylinder_hypersonic_case(mach=7.5, kn=0.005, cells=1500):
 @pytest.mark.parametrize("storage,bound", [("f64", 1e-11), ("f32", 1e-4)])
 def test_hypersonic_cylinder_hundred_steps(U, storage, bound):
     """100 steps of the Ma 7.5 cylinder against the FP64 oracle: FP64 to
-    round-off, FP32 within the benchmark spec's bound; the wake's density falls
+    round-off, FP32 within 1e-4 (the FP32 bound after 100 steps); the wake's density falls
     below 1e-2 of the free stream and stays positive."""
     mesh, grid, gas, prim = cylinder_hypersonic_case()
     Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 100, storage, "blocked128", key="ma75_cylinder")
