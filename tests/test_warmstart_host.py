@@ -35,6 +35,46 @@ def test_converge_gives_none_when_the_step_budget_runs_out():
     assert WS.converge([s], tol=1e-6, max_steps=1000, check_every=100) == [None]
 
 
+class FailingSolver(FakeSolver):
+    """Raises the library's non-physical error from step ``fail_at`` on."""
+
+    def __init__(self, fail_at):
+        super().__init__(1.0, 1.0)
+        self.fail_at = fail_at
+
+    def residual(self):
+        from paper_2606_15720_gb300 import ugks as U
+        if self.n >= self.fail_at:
+            raise U.UGKSError(6, "non-physical state")
+        return super().residual()
+
+
+def test_converge_stops_stepping_a_case_that_became_non_physical():
+    ok, bad = FakeSolver(1e-3, 0.995), FailingSolver(300)
+    steps = WS.converge([ok, bad], tol=1e-6, max_steps=20_000, check_every=100)
+    assert steps[0] == 100 * math.ceil(3 * math.log(10) / -math.log(0.995) / 100)
+    assert steps[1] is None
+    assert bad.n == 300                       # not stepped after its failure was seen
+
+
+def test_batch_family_cases_use_the_batch_workload_recipe():
+    mesh, grid, gas, W0 = WS.cylinder_case(6.0, 0.05, 400, None, seed=3, family="batch")
+    assert gas.model == "bgk" and gas.venkat_K == 1.0
+    u_inf = 6.0 * math.sqrt(5.0 / 6.0)
+    vmax = max(u_inf + 4.0, 3.5 * math.sqrt(1.0 + 36.0 / 3.0))
+    n = int(round(math.sqrt(grid.n_v)))
+    assert n == min(48, max(20, math.ceil(2 * vmax / 0.7)))
+    np.testing.assert_allclose(W0, I.prim_to_conservative(I.cylinder_potential_primitives(mesh, u_inf), 2, 0))
+    nb = mesh.face_neighbor
+    yc = mesh.face_centroid[nb < 0, 1]
+    assert np.all(-(nb[nb < 0][np.abs(np.abs(yc) - 5.0) < 1e-9] + 1) == 2)     # outflow lateral edges
+    mesh_s, _, gas_s, _ = WS.cylinder_case(2.0, 0.1, 400, 24, seed=3)
+    nb = mesh_s.face_neighbor
+    yc = mesh_s.face_centroid[nb < 0, 1]
+    assert gas_s.model == "shakhov"
+    assert np.all(-(nb[nb < 0][np.abs(np.abs(yc) - 5.0) < 1e-9] + 1) == 1)   # far-field lateral edges
+
+
 def test_rel_linf_is_per_field_and_relative_to_the_reference_magnitude():
     ref = np.array([[1.0, -2.0], [0.5, 4.0]])
     w = ref + np.array([[0.1, 0.0], [0.0, -0.2]])
