@@ -1138,12 +1138,18 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage1_p(const BlockedArgs
   const size_t sj = size_t(a.Nc) * BV, sr = size_t(a.M) * sj;
   const int stride = gridDim.x * nwarps;
   const int cbeg = blockIdx.x * nwarps + warp;
+  // Cells are visited from the last to the first (item i is cell Nc - 1 - i):
+  // the flux kernel writes the per-face buffer in increasing face order, so
+  // the rows it wrote last, still in L2, are read first.
+  auto cell_of = [&](int i) { return a.Nc - 1 - i; };
 
-  auto issueA = [&](int c, unsigned char* dst) {
+  auto issueA = [&](int item, unsigned char* dst) {
+    const int c = cell_of(item);
     stage_bytes(dst, a.ell + size_t(c) * W, W * CS::INC, lane);
     stage_bytes(dst + W * CS::INC, a.ceq0 + c, int(sizeof(CellEq<T>)), lane);
   };
-  auto issueB = [&](int c, const unsigned char* A, unsigned char* dst) {
+  auto issueB = [&](int item, const unsigned char* A, unsigned char* dst) {
+    const int c = cell_of(item);
     const IncT<T>* inc = reinterpret_cast<const IncT<T>*>(A);
     for (int i = 0; i < W; ++i) {
       if (inc[i].flags & 2) continue;
@@ -1160,13 +1166,14 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage1_p(const BlockedArgs
   if (cbeg + stride < a.Nc) issueA(cbeg + stride, As + AB);
   cp_async_commit();
   int it = 0;
-  for (int c = cbeg; c < a.Nc; c += stride, ++it) {
+  for (int ci = cbeg; ci < a.Nc; ci += stride, ++it) {
     cp_async_wait<0>();
     __syncwarp();
-    const int cn = c + stride, cnn = c + 2 * stride;
+    const int cn = ci + stride, cnn = ci + 2 * stride;
     if (cn < a.Nc) issueB(cn, As + ((it + 1) % 3) * AB, Bs + ((it + 1) & 1) * BB);
     if (cnn < a.Nc) issueA(cnn, As + ((it + 2) % 3) * AB);
     cp_async_commit();
+    const int c = cell_of(ci);
 
     const unsigned char* A = As + (it % 3) * AB;
     const unsigned char* B = Bs + (it & 1) * BB;
