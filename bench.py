@@ -576,10 +576,11 @@ def batch_cases(n=64, seed=4, cells_range=(5e3, 4e4), nv_range=(20, 48), mach_ra
 
 def run_batch_report(args):
     """Batch workload: 64 uneven 2-D cylinder cases advanced by one CUDA-graph
-    launch per two steps after the block-size autotuner, against the same
-    cases stepped one after another with ordinary launches; also 64 small
-    cases (Ma 1.5-3, 300-1500 cells, 20^2-24^2 velocities), where launch
-    overhead and idle SMs matter."""
+    launch per two steps after the shape autotuner, against the same cases
+    stepped with ordinary launches (in turn without waiting, each case on its
+    own stream, and one case at a time); also 64 small cases (Ma 1.5-3,
+    300-1500 cells, 20^2-24^2 velocities), where launch overhead and idle SMs
+    matter."""
     import torch
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU (the CUDA library has no CPU path)")
@@ -624,6 +625,15 @@ def time_batch(args, cases, workload):
         for s in b.cases:
             s.residual()          # synchronises each case's stream
         seq_ms = 1e3 * (time.perf_counter() - t0) / steps
+        # one case at a time: each case's step has finished before the next
+        # case's is enqueued (no overlap between cases)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            for s in b.cases:
+                s.step(1)
+                s.residual()
+        one_ms = 1e3 * (time.perf_counter() - t0) / steps
         finite = all(bool(np.all(np.isfinite(s.moments()))) for s in b.cases)
         # time to steady: graph launches (two steps each), density residuals
         # (reading R13) read every `every` steps; per case the first step count
@@ -678,7 +688,11 @@ def time_batch(args, cases, workload):
         "graph": {"value": dof / (graph_ms * 1e-3), "ms_per_step": graph_ms,
                   "note": "one CUDA-graph launch per two steps of all cases, cases on forked streams"},
         "sequential": {"value": dof / (seq_ms * 1e-3), "ms_per_step": seq_ms,
-                       "note": "ugks_step per case in turn, host wall clock"},
+                       "note": "ugks_step per case in turn without waiting: every case has its own stream, so "
+                               "the GPU overlaps the cases; host wall clock"},
+        "one_case_at_a_time": {"value": dof / (one_ms * 1e-3), "ms_per_step": one_ms,
+                               "note": "ugks_step per case in turn, each waited for before the next case; "
+                                       "host wall clock"},
         "autotune": {"seconds": tune_s, "block_velocities": {str(v): picks.count(v) for v in sorted(set(picks))},
                      "fused": sum(1 for sh in shapes if sh["fused"]),
                      "stage2_chunks": {str(c): sum(1 for sh in shapes if sh["stage2_chunks"] == c)
