@@ -289,7 +289,7 @@ typedef struct ugks_batch ugks_batch;
 /* Creates n contexts from meshes[i], vgrids[i], params[i] and W_init[i]
  * (W_init or W_init[i] may be NULL as in ugks_create).  A case whose
  * (cells, velocities, dim, reduced distributions, storage) was tuned earlier
- * in this process reuses that block size. */
+ * in this process reuses that shape (ugks_batch_autotune). */
 ugks_status ugks_batch_create(int32_t n, const ugks_mesh *const *meshes, const ugks_vgrid *const *vgrids,
                               const ugks_params *params, const double *const *W_init, void *cuda_stream,
                               ugks_batch **out);
