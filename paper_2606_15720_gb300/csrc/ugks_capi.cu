@@ -84,6 +84,7 @@ struct ugks_ctx {
   // sweep organisation: 1 tiled, 2 blocked; velocities per lane of the blocked sweep
   int variant = 2, vb = 1, vb_max = 1;  // vb_max: the block size the per-face buffer was sized for
   bool fused = false;                    // blocked sweep: fluxes and first stage in one kernel per block
+  bool fused_used = false;               // the last blocked step ran the fused kernel (its stages fit)
   // blocked sweep: 32-bit incidence records, per-block scratch
   int32_t* d_cf_off32 = nullptr;
   void* d_inc = nullptr;
@@ -625,6 +626,7 @@ ugks_status sweep_blocked(ugks_ctx* ctx, int cur, void* X, double* Facc, double*
     // the fused flux + first-stage kernel where requested and its stages
     // fit, else the flux kernel (fluxes into X) and the first stage
     const bool fused = ctx->fused && bstage1f_supported<T, S>(a, vb);
+    if (pass == 0) ctx->fused_used = fused;
     for (; m0 + vb <= M; m0 += vb) {
       record_start(ctx, kTGrad, &ev);
       LAUNCH_TRY(ctx, (launch_brecon<T, S>(s, a, m0, vb)));
@@ -1928,7 +1930,7 @@ ugks_status ugks_batch_autotune(ugks_batch* b) {
       st = time_shape(c, ms);
       if (st != UGKS_OK) break;
       ++trials;
-      if (ms < best_ms) {
+      if (ms < best_ms && c->fused_used) {   // only where the fused kernel's stages fit
         best_ms = ms;
         best.fused = 1;
       }
