@@ -52,6 +52,18 @@ def build_workload(cells=MESH_CELLS, nv_axis=NV_AXIS, nv_cross=0):
     return mesh, grid, gas, W0
 
 
+def workload_config(mesh, grid, gas, world, workload=WORKLOAD, sweep="auto", storage="f32", block_velocities=0):
+    """The benchmark's config entry, the same for the CUDA arm and the
+    reference (oracle) arm: the workload and its sizes."""
+    n_reduced = 2 if gas.K + 3 - mesh.dim > 0 else 1
+    dof = mesh.n_cells * grid.n_v * n_reduced
+    return {"workload": workload, "n_cells": mesh.n_cells, "n_faces": mesh.n_faces, "n_v": grid.n_v,
+            "n_reduced": n_reduced, "dof_per_step": dof, "parallelism": f"replicas x{world}",
+            "sweep": sweep, "storage": storage,
+            "block_velocities": block_velocities or (256 if mesh.dim == 3 and gas.K == 0 else 128),
+            "l2": "inputs larger than L2 (two %.1f GB distribution buffers)" % (dof * 4 / 1e9)}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -266,11 +278,12 @@ def run_reference(args):
         W, f, _, _ = O.run(pm, grid, gas, W, f, 1, dt=dt)
     el = time.perf_counter() - t0
     value = dof * args.steps / el
-    sample = f"each step: one oracle step of a {pm.n_cells}-cell patch of the workload mesh x {grid.n_v} velocities"
+    sample = (f"each step: one oracle step of a {pm.n_cells}-cell face-connected patch of the {mesh.n_cells}-cell "
+              f"workload mesh x {grid.n_v} velocities; value = the patch's DOF updates per second")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_cells": pm.n_cells, "n_v": grid.n_v, "sampled_from_cells": mesh.n_cells},
+            "config": workload_config(mesh, grid, gas, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "cpu_model": cpu_model(),
                              "nproc": os.cpu_count(), "kind": "oracle", "dt": dt, "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -468,13 +481,9 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "fp32" if args.storage == "f32" else f"fp32 arithmetic, {args.storage} storage",
             "data": "synthetic",
-            "config": {"workload": workload, "n_cells": mesh.n_cells, "n_faces": mesh.n_faces, "n_v": grid.n_v,
-                       "n_reduced": n_reduced, "dof_per_step": dof, "parallelism": f"replicas x{world}",
-                       "sweep": args.sweep, "storage": args.storage,
-                       "block_velocities": args.block_velocities or (256 if mesh.dim == 3 and gas.K == 0 else 128),
-                       "l2": "inputs larger than L2 (two %.1f GB distribution buffers)" % (dof * 4 / 1e9),
-                       "state_after": {"residual": [float(x) for x in res],
-                                       "finite": bool(np.all(np.isfinite(W_end)))}},
+            "config": workload_config(mesh, grid, gas, world, workload, args.sweep, args.storage,
+                                      args.block_velocities),
+            "state_after": {"residual": [float(x) for x in res], "finite": bool(np.all(np.isfinite(W_end)))},
             "roofline": roofline, "kernels": kernels, "step_roofline": step_views,
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": count_launches(stats),
