@@ -129,6 +129,62 @@ def strip1d_case():
     return mesh, grid, gas, prim
 
 
+def wheel_mesh(n=10, radii=(0.5, 1.0, 1.6, 2.4)):
+    """2-D polygonal mesh: a regular n-gon at the centre (n faces, more than
+    the 8 of the pipelined kernels' incidence table) inside rings of n quads
+    each; far-field outer edge.  Built here, face by face (shoelace areas and
+    centroids), for the kernels that such cells take."""
+    th = 2 * np.pi * (np.arange(n) + 0.25) / n
+    pts = [np.stack([r * np.cos(th), r * np.sin(th)], 1) for r in radii]
+    cells = [pts[0]]                                    # the n-gon
+    for k in range(len(radii) - 1):
+        for i in range(n):
+            j = (i + 1) % n
+            cells.append(np.array([pts[k][i], pts[k + 1][i], pts[k + 1][j], pts[k][j]]))
+
+    def area_centroid(P):
+        x, y = P[:, 0], P[:, 1]
+        xn, yn = np.roll(x, -1), np.roll(y, -1)
+        cr = x * yn - xn * y
+        A = 0.5 * cr.sum()
+        return abs(A), np.array([((x + xn) * cr).sum(), ((y + yn) * cr).sum()]) / (6 * A)
+
+    vol, cen = zip(*(area_centroid(P) for P in cells))
+    edges = {}
+    for c, P in enumerate(cells):
+        for a in range(len(P)):
+            key = tuple(sorted((tuple(np.round(P[a], 12)), tuple(np.round(P[(a + 1) % len(P)], 12)))))
+            edges.setdefault(key, []).append(c)
+    own, nei, area, nrm, fcen = [], [], [], [], []
+    for (pa, pb), cs in edges.items():
+        pa, pb = np.array(pa), np.array(pb)
+        mid = 0.5 * (pa + pb)
+        t = pb - pa
+        nv = np.array([t[1], -t[0]]) / np.linalg.norm(t)
+        o = cs[0]
+        if np.dot(nv, mid - cen[o]) < 0:
+            nv = -nv
+        own.append(o)
+        nei.append(cs[1] if len(cs) == 2 else -1)
+        area.append(np.linalg.norm(t))
+        nrm.append(nv)
+        fcen.append(mid)
+    nf = len(own)
+    return I.Mesh(dim=2, cell_volume=np.array(vol), cell_centroid=np.array(cen),
+                  face_owner=np.array(own, dtype=np.int64), face_neighbor=np.array(nei, dtype=np.int64),
+                  face_area=np.array(area), face_normal=np.array(nrm), face_centroid=np.array(fcen),
+                  face_shift=np.zeros((nf, 2)), bc=[I.BC(I.BC_FARFIELD, 1.0, (0.3, 0.1, 0.0), 1.1)],
+                  name=f"wheel{n}")
+
+
+def wheel_case():
+    mesh = wheel_mesh()
+    grid = I.midpoint_grid(14, -5, 5, 2)                # 196 velocities: 6 blocks of 32 + a ragged tail
+    gas = I.Gas(model="shakhov", Pr=2 / 3, omega=0.81, mu_ref=0.05, cfl=0.8)
+    prim = I.smooth_random_primitives(mesh, seed=6, amp=0.1, U0=(0.3, 0.1, 0.0), length=(5, 5))
+    return mesh, grid, gas, prim
+
+
 def sphere_case(cells=2500, nvx=11, mach=2.0, vmax=6.0):
     # the velocity grid must resolve the gas (spacing ~ thermal speed): 11^3 on [-6, 6]^3
     mesh = I.sphere_tet_mesh(cells, seed=3, mach=mach)
@@ -278,6 +334,23 @@ def test_hypersonic_cylinder_hundred_steps(U, storage, bound):
     Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 100, storage, "blocked128", key="ma75_cylinder")
     assert w_err(Wg, Wo) <= bound, w_err(Wg, Wo)
     assert np.min(Wo[:, 0]) > 0.0 and np.min(Wo[:, 0]) < 0.05
+
+
+@pytest.mark.parametrize("storage,steps,bound", [("f64", 3, 1e-11), ("f32", 1, 1e-5)])
+def test_cells_with_more_than_eight_faces(U, storage, steps, bound):
+    """A ten-sided cell sends the reconstruction and first stage to their
+    non-pipelined kernels: W and f against the oracle (FP64 to round-off,
+    FP32 within the one-step bound).  Scaled FP16 storage, which needs the
+    pipelined kernels, is refused."""
+    mesh, grid, gas, prim = wheel_case()
+    assert mesh.closure_residual() < 1e-13
+    assert np.max(np.bincount(np.concatenate([mesh.face_owner, mesh.face_neighbor[mesh.face_neighbor >= 0]]))) == 10
+    Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, steps, storage, "blocked64")
+    assert w_err(Wg, Wo) <= bound, w_err(Wg, Wo)
+    for r in range(fo.shape[0]):
+        assert rel_linf(fg[r], fo[r], None) <= bound
+    with pytest.raises(U.UGKSError):
+        U.Solver(mesh, grid, gas, I.prim_to_conservative(prim, 2, gas.K), storage="f16")
 
 
 def test_cavity_config_200_steps_fp64(U):
