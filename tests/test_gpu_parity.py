@@ -66,6 +66,7 @@ SWEEPS = {
     "blocked_fused64": dict(sweep="blocked_fused", block_velocities=64),   # fluxes evaluated per cell with stage 1
     "tiled": dict(sweep="tiled", tile_cells=48),
     "scaled": dict(sweep="blocked"),   # the storage argument selects FP16 / BF16
+    "scaled_fused": dict(sweep="blocked_fused"),
 }
 _oracle_cache = {}
 
@@ -241,7 +242,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("sweep", sorted(k for k in SWEEPS if k != "scaled"))
+@pytest.mark.parametrize("sweep", sorted(k for k in SWEEPS if not k.startswith("scaled")))
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_fp64_matches_oracle(U, name, sweep):
     mesh, grid, gas, prim = CASES[name]()
@@ -251,7 +252,7 @@ def test_fp64_matches_oracle(U, name, sweep):
     np.testing.assert_allclose(res, diag[-1, :mesh.dim + 2], rtol=1e-9, atol=1e-300)
 
 
-@pytest.mark.parametrize("sweep", sorted(k for k in SWEEPS if k != "scaled"))
+@pytest.mark.parametrize("sweep", sorted(k for k in SWEEPS if not k.startswith("scaled")))
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_fp32_one_step_matches_oracle(U, name, sweep):
     mesh, grid, gas, prim = CASES[name]()
@@ -503,18 +504,20 @@ def _deviation_ratio(mesh, grid, gas, W, f):
     return np.array([np.max(np.abs(f[r] - g[r])) / np.max(np.abs(f[r])) for r in range(f.shape[0])])
 
 
+@pytest.mark.parametrize("sweep", ["scaled", "scaled_fused"])
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_scaled_storage_one_step_matches_oracle(U, name, storage):
+def test_scaled_storage_one_step_matches_oracle(U, name, storage, sweep):
     """FP16 / BF16 deviations from a per-cell reference Maxwellian, FP32
     arithmetic.  f^0 is its own reference (zero deviations), so W after one step
     carries FP32 rounding only (<= 1e-5).  f^1 carries two storage roundings,
     each at most eps of the value's deviation from its reference (f~ against the
     Maxwellian of W^0, f^1 against that of W^1): per reduced distribution the
     error is within 1e-5 + 2 eps (D0 + D1) of max |f|, D0 and D1 the oracle's
-    largest deviations from the two references."""
+    largest deviations from the two references.  Both organisations of the
+    fluxes and first stage (split kernels, fused kernel)."""
     mesh, grid, gas, prim = CASES[name]()
-    Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 1, storage, "scaled", key=name)
+    Wg, fg, res, Wo, fo, diag, dt, _ = run_pair(U, mesh, grid, gas, prim, 1, storage, sweep, key=name)
     W0 = I.prim_to_conservative(prim, mesh.dim, gas.K)
     assert w_err(Wg, Wo) <= 1e-5, w_err(Wg, Wo)
     dev = _deviation_ratio(mesh, grid, gas, W0, fo) + _deviation_ratio(mesh, grid, gas, Wo, fo)
