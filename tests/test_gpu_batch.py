@@ -25,17 +25,18 @@ def _cases():
     return out
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
 @pytest.mark.parametrize("nsteps", [4, 3])
-def test_batch_graph_steps_equal_single_case_steps(nsteps):
+def test_batch_graph_steps_equal_single_case_steps(nsteps, storage):
     from paper_2606_15720_gb300 import ugks as U
     cases = _cases()
     with U.Batch([c[0] for c in cases], [c[1] for c in cases], [c[2] for c in cases], [c[3] for c in cases],
-                 storage="f32", block_velocities=64) as b:
+                 storage=storage, block_velocities=64) as b:
         b.step(nsteps)
         Wb = [s.moments() for s in b.cases]
         rb = [s.residual() for s in b.cases]
     for (mesh, grid, gas, W0), W, r in zip(cases, Wb, rb):
-        with U.Solver(mesh, grid, gas, W0, storage="f32", sweep="blocked", block_velocities=64) as s:
+        with U.Solver(mesh, grid, gas, W0, storage=storage, sweep="blocked", block_velocities=64) as s:
             s.step(nsteps)
             np.testing.assert_array_equal(W, s.moments())
             # the residual's cross-CTA sum uses atomics: equal up to summation order
