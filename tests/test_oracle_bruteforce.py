@@ -49,6 +49,7 @@ CASES = {
     "tets3d_shakhov_venkatakrishnan": (tets3d, "shakhov", 0, "venkatakrishnan"),
     "tets3d_shakhov_barth_jespersen": (tets3d, "shakhov", 0, "barth_jespersen"),
     "tets3d_bgk_no_limiter": (tets3d, "bgk", 0, "none"),
+    "tets3d_bgk_K2_venkatakrishnan": (tets3d, "bgk", 2, "venkatakrishnan"),
 }
 # (mu_ref, dt): dt / tau about 0.03 (collisionless-ish) and about 1
 REGIMES = {"dt_small": (0.2, 0.01), "dt_tau": (0.01, 0.02)}
