@@ -877,7 +877,7 @@ __host__ __device__ constexpr int recon_warp_bytes(int W) {
 template <int NR, int VB, typename T, typename S>
 __host__ __device__ constexpr int stage1_warp_bytes(int W) {
   return 3 * (W * CellStage<NR, VB, T>::INC + int(sizeof(CellEq<T>))) +
-         2 * (W * CellStage<NR, VB, T>::ROW + CellSlot<NR, VB, S>::BYTES);
+         2 * (W * CellStage<NR, VB, T>::ROW + CellSlot<NR, VB, S>::BYTES) + 16;   // + two mbarriers
 }
 
 // byte offset of the 16-byte chunk of a FacePoly that holds G0 and G1
@@ -1148,29 +1148,73 @@ __global__ void __launch_bounds__(kBlockedThreads) k_bstage1_p(const BlockedArgs
     stage_bytes(dst, a.ell + size_t(c) * W, W * CS::INC, lane);
     stage_bytes(dst + W * CS::INC, a.ceq0 + c, int(sizeof(CellEq<T>)), lane);
   };
-  auto issueB = [&](int item, const unsigned char* A, unsigned char* dst) {
+  // The rows of a cell's slot arrive by 1-D bulk copies, one per lane: the
+  // block of each face in X (one contiguous CS::ROW segment) and each of the
+  // cell's NR x VB rows of f^n (one 32-velocity segment each), completing in
+  // bytes on the slot's mbarrier; records and the scaled-storage extras come
+  // by cp.async.
+  uint64_t* const bars = reinterpret_cast<uint64_t*>(Bs + 2 * BB);
+  if (lane == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  const S* const fs = reinterpret_cast<const S*>(a.f_cur);
+  constexpr unsigned kRowBytes = BV * unsigned(sizeof(S));
+  static_assert(CS::ROW % 16 == 0 && kRowBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+  static_assert((WT * CS::INC + sizeof(CellEq<T>)) % 16 == 0 && (WT * CS::ROW + SL::BYTES) % 16 == 0,
+                "16-byte aligned slots");
+  static_assert(WT + NR * VB <= 32, "one copy per lane");
+  auto issueB = [&](int item, const unsigned char* A, unsigned char* dst, uint64_t* bar) {
     const int c = cell_of(item);
     const IncT<T>* inc = reinterpret_cast<const IncT<T>*>(A);
-    for (int i = 0; i < W; ++i) {
-      if (inc[i].flags & 2) continue;
-      stage_bytes(dst + i * CS::ROW, a.X + size_t(inc[i].face) * (NR * VB * BV), CS::ROW, lane);
+    unsigned bytes = NR * VB * kRowBytes;
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+      if (!(inc[i].flags & 2)) bytes += CS::ROW;
+    // this lane's reads of the slot (two items ago) before the copies' writes;
+    // the slot's bytes announced before any copy is issued
+    fence_proxy_async_smem();
+    if (lane == 0) mbar_arrive_expect_tx(bar, bytes);
+    __syncwarp();
+    if (lane < W) {
+      if (!(inc[lane].flags & 2))
+        bulk_load(dst + lane * CS::ROW, a.X + size_t(inc[lane].face) * (NR * VB * BV), CS::ROW, bar);
+    } else if (lane < W + NR * VB) {
+      const int q = lane - W, r = q / VB, j = q % VB;
+      bulk_load(dst + W * CS::ROW + q * kRowBytes, fs + r * sr + (size_t(m0) + j) * sj + size_t(c) * BV,
+                kRowBytes, bar);
     }
-    stage_cell<NR, VB, T, S>(dst + W * CS::ROW, a, m0, c, lane);
+    if constexpr (SL::SCALED) {
+      unsigned char* cs = dst + W * CS::ROW;
+      for (int q = lane; q < NR * VB; q += 32) {
+        const int r = q / VB, j = q % VB;
+        cp_async_small<4>(cs + SL::ROWS + q * 4, a.sc_cur + (size_t(r) * a.M + m0 + j) * a.Nc + c);
+      }
+      if (lane < 2)
+        cp_async16(cs + SL::ROWS + SL::SCL + lane * 16, reinterpret_cast<const unsigned char*>(a.ref_cur + c) + lane * 16);
+    }
   };
 
   if (cbeg < a.Nc) issueA(cbeg, As);
   cp_async_commit();
   cp_async_wait<0>();
   __syncwarp();
-  if (cbeg < a.Nc) issueB(cbeg, As, Bs);
+  if (cbeg < a.Nc) issueB(cbeg, As, Bs, &bars[0]);
   if (cbeg + stride < a.Nc) issueA(cbeg + stride, As + AB);
   cp_async_commit();
   int it = 0;
   for (int ci = cbeg; ci < a.Nc; ci += stride, ++it) {
     cp_async_wait<0>();
+    // slot it & 1 is used for the (it >> 1)-th time: that phase of its barrier
+    if (!mbar_wait(&bars[it & 1], unsigned(it >> 1) & 1u, a.status)) {
+      mbar_wait(&bars[it & 1], unsigned(it >> 1) & 1u, a.status);   // its copies may still be in flight
+      break;
+    }
     __syncwarp();
     const int cn = ci + stride, cnn = ci + 2 * stride;
-    if (cn < a.Nc) issueB(cn, As + ((it + 1) % 3) * AB, Bs + ((it + 1) & 1) * BB);
+    if (cn < a.Nc) issueB(cn, As + ((it + 1) % 3) * AB, Bs + ((it + 1) & 1) * BB, &bars[(it + 1) & 1]);
     if (cnn < a.Nc) issueA(cnn, As + ((it + 2) % 3) * AB);
     cp_async_commit();
     const int c = cell_of(ci);
